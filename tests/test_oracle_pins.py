@@ -1,0 +1,817 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-derives the oracle's formulas: each checks a closed form,
+an invariant, a special case or a value printed in the paper, chosen so
+that a dropped term, a wrong sign or a swapped index in the oracle fails
+one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import orc
+from oracle.drive import oracle_from_workload
+from oracle.orc import Oracle
+from paper_1202_0442_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    return vals
+
+
+# --------------------------------------------------------------------------
+# equilibrium, Eq. (2) and the fluids-command generalisation
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.3, 0.05, -0.02),
+                                       (0.2, -0.1, 0.07), (24.0, 0.01, 0.0)])
+@pytest.mark.parametrize("alpha", [4.0 / 9.0, 0.8, 0.0])
+def test_feq_moments(rho, ux, uy, alpha):
+    """sum f_eq = rho, sum f_eq e = rho u, sum f_eq e e = rho c_s^2 I + rho u u
+    with c_s^2 = (3/5)(1 - alpha) (fluids command; 1/3 at alpha = 4/9)."""
+    f = orc.feq(rho, ux, uy, alpha)
+    cs2 = 0.6 * (1.0 - alpha)
+    assert np.isclose(f.sum(), rho, rtol=1e-14, atol=0)
+    assert np.isclose((f * EX).sum(), rho * ux, rtol=0, atol=1e-15 * rho)
+    assert np.isclose((f * EY).sum(), rho * uy, rtol=0, atol=1e-15 * rho)
+    assert np.isclose((f * EX * EX).sum(), rho * cs2 + rho * ux * ux, rtol=1e-13, atol=1e-16)
+    assert np.isclose((f * EY * EY).sum(), rho * cs2 + rho * uy * uy, rtol=1e-13, atol=1e-16)
+    assert np.isclose((f * EX * EY).sum(), rho * ux * uy, rtol=1e-13, atol=1e-16)
+
+
+def test_feq_rest_weights():
+    """At u = 0 and alpha = 4/9 the equilibrium is rho w_i (Eq. (2) text)."""
+    f = orc.feq(1.0, 0.0, 0.0)
+    assert np.allclose(f, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, rtol=1e-15)
+
+
+def test_feq_is_a_fixed_point():
+    """collide(f_eq(rho, u)) = f_eq when no force acts; on a 1x1 periodic
+    lattice streaming is the identity, so one iteration is one collision."""
+    for tau in (0.6, 1.0, 1.7):
+        o = Oracle(1, 1)
+        o.set_tau(tau)
+        o.set_equilibrium(1.1, 0.03, -0.04)
+        f0 = o.f().copy()
+        o.step(3)
+        assert np.allclose(o.f(), f0, rtol=1e-14, atol=1e-16)
+
+
+def test_single_node_collision_moments():
+    """BGK keeps rho; with the velocity-shift force it adds exactly F to the
+    momentum; the second moment relaxes by 1/tau toward rho/3 I + rho u u."""
+    rng = np.random.default_rng(7)
+    for tau in (0.55, 0.9, 1.0, 2.0):
+        f = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) * (1 + 0.3 * rng.uniform(-1, 1, 9))
+        F = np.array([1e-3, -2e-3])
+        o = Oracle(1, 1)
+        o.set_tau(tau)
+        o.set_aveforce(*F)
+        o.set_f(f.reshape(9, 1, 1))
+        o.step()
+        fs = o.f().ravel()
+        rho = f.sum()
+        j = np.array([(f * EX).sum(), (f * EY).sum()])
+        assert np.isclose(fs.sum(), rho, rtol=1e-14)
+        assert np.allclose([(fs * EX).sum(), (fs * EY).sum()], j + F, rtol=0, atol=1e-15)
+        ueq = (j + tau * F) / rho
+        for (a, b) in ((EX, EX), (EY, EY), (EX, EY)):
+            pi = (f * a * b).sum()
+            ua = ueq[0] if a is EX else ueq[1]
+            ub = ueq[0] if b is EX else ueq[1]
+            pieq = rho * ua * ub + (rho / 3 if a is b else 0.0)
+            assert np.isclose((fs * a * b).sum(), pi - (pi - pieq) / tau, rtol=1e-12, atol=1e-15)
+        # physical momentum reported for the step is j + F/2 (Eq. (4))
+        r, px, py, req = o.fields()
+        o2 = Oracle(1, 1)
+        o2.set_tau(tau)
+        o2.set_aveforce(*F)
+        o2.set_f(f.reshape(9, 1, 1))
+        o2.step()
+        r, px, py, req = o2.fields()
+        assert np.isclose(px[0, 0], j[0] + F[0] / 2, atol=1e-15)
+        assert np.isclose(py[0, 0], j[1] + F[1] / 2, atol=1e-15)
+        assert np.isclose(req[0, 0], rho, rtol=1e-14)
+
+
+def test_two_component_collision_conservation():
+    """Two components: each mass is kept, the mixture momentum changes by
+    exactly the total force (common velocity of the fluids command)."""
+    rng = np.random.default_rng(3)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    o = Oracle(1, 1, 2)
+    o.set_tau(0.7, 0)
+    o.set_tau(1.6, 1)
+    F1, F2 = np.array([2e-3, 1e-3]), np.array([-5e-4, 3e-3])
+    o.set_aveforce(*F1, comp=0)
+    o.set_aveforce(*F2, comp=1)
+    f1 = 1.2 * w * (1 + 0.2 * rng.uniform(-1, 1, 9))
+    f2 = 0.3 * w * (1 + 0.2 * rng.uniform(-1, 1, 9))
+    o.set_f(f1.reshape(9, 1, 1), 0)
+    o.set_f(f2.reshape(9, 1, 1), 1)
+    o.step()
+    g1, g2 = o.f(0).ravel(), o.f(1).ravel()
+    assert np.isclose(g1.sum(), f1.sum(), rtol=1e-14)
+    assert np.isclose(g2.sum(), f2.sum(), rtol=1e-14)
+    jb = np.array([((f1 + f2) * EX).sum(), ((f1 + f2) * EY).sum()])
+    ja = np.array([((g1 + g2) * EX).sum(), ((g1 + g2) * EY).sum()])
+    assert np.allclose(ja, jb + F1 + F2, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# streaming, bounce-back, forcing: invariants and exact results
+# --------------------------------------------------------------------------
+
+def test_mass_conserved_with_obstacles():
+    """Periodic box, random solid mask, random non-equilibrium populations:
+    streaming with half-way bounce-back plus BGK keeps sum f exactly."""
+    nx, ny = 23, 17
+    mask = synth.random_mask(nx, ny, 5, 0.25)
+    w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    f = synth.random_populations(9, nx, ny, 11, w, 0.4, mask)
+    o = Oracle(nx, ny)
+    o.set_tau(0.73)
+    o.set_aveforce(1e-4, -3e-4)
+    o.set_solid(mask)
+    o.set_f(f)
+    m0 = f.sum()
+    o.step(200)
+    assert abs(o.f().sum() - m0) / m0 < 1e-13
+    th = o.thermo()
+    assert abs(th["mass1"] - m0) / m0 < 1e-13
+    assert abs(th["mass_eq1"] - m0) / m0 < 1e-13
+    assert th["nsolid"] == mask.sum() and th["nfluid"] == nx * ny - mask.sum()
+
+
+def test_rest_state_is_invariant_next_to_any_mask():
+    """A fluid at rest with uniform density stays at rest beside any solid
+    arrangement (bounce-back of an isotropic state)."""
+    nx, ny = 19, 13
+    mask = synth.random_mask(nx, ny, 9, 0.35)
+    o = Oracle(nx, ny)
+    o.set_tau(0.8)
+    o.set_solid(mask)
+    o.set_equilibrium(np.where(mask, 0.0, 1.0))
+    f0 = o.f().copy()
+    o.step(50)
+    assert np.allclose(o.f(), f0, rtol=0, atol=1e-15)
+
+
+def test_uniform_force_momentum_is_exact():
+    """Periodic box at rest with a constant force per node F: after n
+    iterations the reported momentum (j + F/2, Eq. (4)) is N F (n - 1/2)."""
+    nx, ny, F = 6, 5, np.array([3e-5, -1e-5])
+    o = Oracle(nx, ny)
+    o.set_tau(0.9)
+    o.set_aveforce(*F)
+    o.set_equilibrium(1.0)
+    for n in range(1, 8):
+        o.step()
+        th = o.thermo()
+        assert np.isclose(th["momx"], nx * ny * F[0] * (n - 0.5), rtol=1e-12)
+        assert np.isclose(th["momy"], nx * ny * F[1] * (n - 0.5), rtol=1e-12)
+
+
+def test_acceleration_scales_with_density():
+    """aveacceleration gives the force rho a: a heavier fluid at rest
+    gains proportionally more momentum."""
+    for rho in (1.0, 24.0):
+        o = Oracle(3, 3)
+        o.set_aveacceleration(2e-5, 0.0)
+        o.set_equilibrium(rho)
+        o.step()
+        assert np.isclose(o.thermo()["momx"], 9 * rho * 2e-5 * 0.5, rtol=1e-12)
+
+
+def _channel_profile(nx, ny, g, tau, steps, accel=False):
+    w = synth.channel(nx, ny, tau=tau, gx=g, steps=steps)
+    o = oracle_from_workload(w)
+    if accel:
+        o.set_aveforce(0.0, 0.0)
+        o.set_aveacceleration(g, 0.0)
+    o.step(steps)
+    r, px, py, _ = o.fields()
+    u = np.where(r > 0, px / np.where(r > 0, r, 1), 0.0)
+    return u, o
+
+
+def test_poiseuille_transient_series():
+    """64 x 32 channel, walls y = 0 and 31, tau = 1, g = 1e-6, 2000
+    iterations against the start-up series of plane Poiseuille flow,
+    u = u_ss - sum_odd 4gH^2/(nu n^3 pi^3) sin(n pi y'/H) exp(-n^2 pi^2 nu t/H^2)
+    with H = 30, y' = y - 1/2, nu = (tau - 1/2)/3 and t = n - 1/2."""
+    nx, ny, g, tau, steps = 64, 32, 1e-6, 1.0, 2000
+    u, _ = _channel_profile(nx, ny, g, tau, steps)
+    H, nu = ny - 2, (tau - 0.5) / 3
+    y = np.arange(ny) - 0.5
+    t = steps - 0.5
+    ua = g / (2 * nu) * y * (H - y)
+    for n in range(1, 400, 2):
+        ua -= (4 * g * H * H / (nu * n ** 3 * np.pi ** 3) * np.sin(n * np.pi * y / H)
+               * np.exp(-n * n * np.pi ** 2 * nu * t / H ** 2))
+    sl = slice(1, ny - 1)
+    prof = u[sl, :]
+    assert np.allclose(prof, prof[:, :1], rtol=0, atol=1e-15)   # uniform along x
+    err = np.max(np.abs(prof[:, 0] - ua[sl])) / np.max(ua[sl])
+    assert err < 1e-3, err
+    # symmetric about the channel centre
+    assert np.allclose(u[sl, 0], u[sl, 0][::-1], rtol=1e-12)
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 1.5])
+def test_poiseuille_steady_second_order(tau):
+    """Steady profile g/(2 nu) y'(H - y') (Eq. (5)) is approached at second
+    order in H: the relative error times H^2 is the same for H = 15 and 30
+    (half-way bounce-back)."""
+    errs = []
+    for H in (15, 30):
+        ny = H + 2
+        nu = (tau - 0.5) / 3
+        steps = int(12 * H * H / (np.pi ** 2 * nu)) + 200
+        u, _ = _channel_profile(3, ny, 1e-6, tau, steps)
+        y = np.arange(ny) - 0.5
+        ua = 1e-6 / (2 * nu) * y * (H - y)
+        sl = slice(1, ny - 1)
+        errs.append(np.max(np.abs(u[sl, 0] - ua[sl])) / np.max(ua[sl]) * H * H)
+    assert abs(errs[0] / errs[1] - 1) < 0.02, errs
+    assert errs[1] < 5.0, errs
+
+
+def test_poiseuille_paper_worked_example():
+    """Sec. Poiseuille flow and its script: N_x = 60, N_y = 30 (61 x 31
+    nodes), solid rows y = 0 and y = N_y, populations 4 (rest and slow
+    modes) and 1 (fast modes), aveacceleration g = 1.11e-4, tau = 1, 10000
+    iterations: the paper gives u_max = 0.07 for this g, from
+    g = (4/3) u_max (2 tau - 1)/(N_y - 1)^2."""
+    gold = read_golden("poiseuille_x1.txt")
+    Nx, Ny = int(gold["Nx"]), int(gold["Ny"])
+    g, tau, umax = float(gold["g"]), float(gold["tau"]), float(gold["u_max"])
+    assert np.isclose(4 / 3 * umax * (2 * tau - 1) / (Ny - 1) ** 2, g, rtol=2e-3)
+    nx, ny = Nx + 1, Ny + 1
+    o = Oracle(nx, ny)
+    o.set_tau(tau)
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0, :] = 1
+    mask[Ny, :] = 1
+    o.set_solid(mask)
+    f = np.zeros((9, ny, nx))
+    f[0:5, 1:Ny, :] = 4.0
+    f[5:9, 1:Ny, :] = 1.0
+    o.set_f(f)
+    o.set_aveacceleration(g, 0.0)
+    o.step(int(gold["steps"]))
+    r, px, _, _ = o.fields()
+    u = px[:, 0] / np.where(r[:, 0] > 0, r[:, 0], 1)
+    assert np.isclose(r[Ny // 2, 0], 24.0, rtol=1e-12)
+    assert abs(u.max() - umax) / umax < 2e-3, u.max()
+    # the profile of Eq. (5) at y = 1..N_y-1
+    y = np.arange(1, Ny)
+    ua = 3 * g / (2 * tau - 1) * (((Ny - 1) / 2) ** 2 - (y - Ny / 2) ** 2)
+    assert np.max(np.abs(u[1:Ny] - ua)) / ua.max() < 2e-3
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0])
+def test_taylor_green_decay(tau):
+    """Periodic Taylor-Green vortex: the amplitude decays as
+    exp(-2 nu k^2 t) with nu = (tau - 1/2)/3; the relative rate error falls
+    fourfold per doubling of N (second order)."""
+    errs = []
+    for N in (16, 32):
+        o = Oracle(N, N)
+        o.set_tau(tau)
+        k = 2 * np.pi / N
+        y, x = np.mgrid[0:N, 0:N].astype(float)
+        U = 1e-4
+        ux = -U * np.cos(k * x) * np.sin(k * y)
+        uy = U * np.sin(k * x) * np.cos(k * y)
+        o.set_equilibrium(1.0, ux, uy)
+        nu = (tau - 0.5) / 3
+        T = int(0.5 / (2 * nu * k * k))
+        amps = []
+        for _ in range(T):
+            o.step()
+            r, px, py, _ = o.fields()
+            amps.append(np.sum(px * ux + py * uy) / np.sum(ux * ux + uy * uy))
+        tt = np.arange(1, T + 1) - 0.5
+        rate = -np.polyfit(tt[T // 4:], np.log(np.array(amps[T // 4:])), 1)[0]
+        errs.append(abs(rate / (2 * nu * k * k) - 1))
+    assert errs[1] < 4e-3, errs
+    assert 3.4 < errs[0] / errs[1] < 4.6, errs
+
+
+# --------------------------------------------------------------------------
+# inlet/outlet openings (inlet_momentum/outlet_momentum, App. A)
+# --------------------------------------------------------------------------
+
+WALL_NORMAL = {"xlo": (1, 0), "xhi": (-1, 0), "ylo": (0, 1), "yhi": (0, -1)}
+
+
+@pytest.mark.parametrize("wall", ["xlo", "xhi", "ylo", "yhi"])
+@pytest.mark.parametrize("kind", ["inlet", "outlet"])
+def test_velocity_opening_moments(wall, kind):
+    """After the rule the node moves at speed v along the inward normal for
+    an inlet (outward for an outlet), with no tangential velocity; the
+    three rewritten modes are exactly those that crossed the wall."""
+    rng = np.random.default_rng(1)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    nvec = np.array(WALL_NORMAL[wall])
+    for v in (0.0, 0.03, 0.1):
+        f = w * (1 + 0.2 * rng.uniform(-1, 1, 9))
+        g, rho, _ = orc.zouhe(wall, kind, "uniform", f, v=v)
+        crossed = (EX * nvec[0] + EY * nvec[1]) > 0
+        assert np.array_equal(g[~crossed], f[~crossed])
+        assert np.isclose(g.sum(), rho, rtol=1e-14)
+        j = np.array([(g * EX).sum(), (g * EY).sum()])
+        sign = 1.0 if kind == "inlet" else -1.0
+        assert np.allclose(j, sign * rho * v * nvec, atol=1e-15)
+
+
+@pytest.mark.parametrize("wall", ["xlo", "xhi", "ylo", "yhi"])
+def test_dirichlet_opening_moments(wall):
+    """dirichlet keeps the imposed density and returns the normal velocity
+    component; tangential velocity is zero."""
+    rng = np.random.default_rng(2)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    nvec = np.array(WALL_NORMAL[wall])
+    for rho_b in (1.0, 1.001, 0.7):
+        f = w * (1 + 0.2 * rng.uniform(-1, 1, 9))
+        for kind in ("inlet", "outlet"):
+            g, rho, v = orc.zouhe(wall, kind, "dirichlet", f, rho=rho_b)
+            assert rho == rho_b
+            assert np.isclose(g.sum(), rho_b, rtol=1e-14)
+            j = np.array([(g * EX).sum(), (g * EY).sum()])
+            axis = 0 if wall in ("xlo", "xhi") else 1
+            assert np.isclose(j[axis], rho_b * v, atol=1e-15)
+            assert np.isclose(j[1 - axis], 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("wall", ["xlo", "xhi", "ylo", "yhi"])
+def test_zero_velocity_inlet_is_bounce_back(wall):
+    """At v = 0 and no tangential imbalance the velocity rule reduces to
+    bounce-back of the crossing modes (special case of the Zou-He rule)."""
+    nvec = np.array(WALL_NORMAL[wall])
+    f = np.array([0.44, 0.11, 0.12, 0.105, 0.115, 0.03, 0.026, 0.029, 0.027])
+    if wall in ("xlo", "xhi"):
+        f[4] = f[2]
+    else:
+        f[3] = f[1]
+    g, _, _ = orc.zouhe(wall, "inlet", "uniform", f, v=0.0)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    crossed = (EX * nvec[0] + EY * nvec[1]) > 0
+    for i in np.nonzero(crossed)[0]:
+        assert np.isclose(g[i], f[opp[i]], rtol=0, atol=1e-16)
+
+
+def test_poiseuille_opening_profile():
+    """The poiseuille style's profile is the parabola through the half-way
+    points y0 - 1/2 and y1 + 1/2 with maximum vmax on the opening centre."""
+    vmax, a0, a1 = 0.07, 3, 21
+    v = np.array([orc.poiseuille_v(vmax, a0, a1, y) for y in range(a0, a1 + 1)])
+    ys = np.arange(a0, a1 + 1)
+    L = a1 - a0 + 1
+    par = np.polyfit(ys, v, 2)
+    roots = np.sort(np.roots(par).real)
+    assert np.allclose(roots, [a0 - 0.5, a1 + 0.5], atol=1e-9)
+    assert np.isclose(v.max(), vmax * (1 - 1 / L ** 2) if L % 2 == 0 else vmax, rtol=1e-12)
+
+
+def test_pressure_driven_channel():
+    """dirichlet inlet/outlet on a walled channel: at steady state the mass
+    flux is the same through every column, the profile is parabolic and the
+    density falls linearly between the openings."""
+    nx, ny = 40, 13
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    w = synth.Workload(name="pchan", nx=nx, ny=ny, solid=solid,
+                       rho=[np.where(solid, 0.0, 1.0)], tau=(0.9,),
+                       openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("dirichlet", 0, 1.002)]),
+                                 synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0, 1.0)])])
+    o = oracle_from_workload(w)
+    o.step(6000)
+    r, px, py, _ = o.fields()
+    o.step()
+    r2, px2, _, _ = o.fields()
+    # the openings excite the lattice's period-2 staggered mode (momentum
+    # alternating in sign between neighbouring columns and successive
+    # steps, which BGK does not damp); the two-step average removes it
+    r, px = 0.5 * (r + r2), 0.5 * (px + px2)
+    flux = px[1:-1, :].sum(axis=0)
+    assert flux.min() > 0
+    assert np.allclose(flux, flux.mean(), rtol=1e-6), flux
+    ux = px[1:-1, nx // 2]
+    y = np.arange(1, ny - 1)
+    fit = np.polyfit(y, ux, 2)
+    assert np.max(np.abs(np.polyval(fit, y) - ux)) / ux.max() < 5e-3
+    rm = r[ny // 2, :]
+    lin = np.polyfit(np.arange(nx), rm, 1)
+    assert np.max(np.abs(np.polyval(lin, np.arange(nx)) - rm)) < 2e-5
+    assert np.isclose(r[ny // 2, 0], 1.002, rtol=1e-14) and np.isclose(r[ny // 2, -1], 1.0, rtol=1e-14)
+    assert np.isclose(r2[ny // 2, 0], 1.002, rtol=1e-14)
+
+
+def test_velocity_inlet_delivers_the_flux():
+    """uniform inlet at xlo with v and dirichlet outlet: at steady state the
+    mass flux through every column equals the inlet's (sum rho v)."""
+    nx, ny, v = 30, 11, 0.01
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    w = synth.Workload(name="vchan", nx=nx, ny=ny, solid=solid,
+                       rho=[np.where(solid, 0.0, 1.0)], tau=(0.8,),
+                       openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("uniform", v, 1.0)]),
+                                 synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0, 1.0)])])
+    o = oracle_from_workload(w)
+    o.step(5000)
+    r, px, _, _ = o.fields()
+    assert np.allclose(px[1:-1, 0], r[1:-1, 0] * v, rtol=1e-12)
+    o.step()
+    r2, px2, _, _ = o.fields()
+    r, px = 0.5 * (r + r2), 0.5 * (px + px2)    # two-step average (staggered mode)
+    inflow = (r[1:-1, 0] * v).sum()
+    assert np.allclose(px[1:-1, :].sum(axis=0), inflow, rtol=1e-6)
+
+
+def test_gradient_outlet_extrapolates():
+    """gradient style: after collision f_i(N_x) = 2 f_i(N_x - 1) - f_i(N_x - 2)."""
+    nx, ny = 20, 9
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    w = synth.Workload(name="gchan", nx=nx, ny=ny, solid=solid,
+                       rho=[np.where(solid, 0.0, 1.0)], tau=(0.8,),
+                       openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("uniform", 0.02, 1.0)]),
+                                 synth.Opening("xhi", 1, ny - 2, "outlet", [("gradient", 0, 1.0)])])
+    o = oracle_from_workload(w)
+    o.step(40)
+    f = o.f()
+    assert np.allclose(f[:, 1:-1, -1], 2 * f[:, 1:-1, -2] - f[:, 1:-1, -3], rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Shan-Chen interforce and adhesiveforce
+# --------------------------------------------------------------------------
+
+def test_single_component_sc_flat_interface():
+    """interforce(-120, 4, 200) (Sec. Phase separation's parameters) on a
+    liquid slab: the phases separate and the bulk pressure
+    p = rho/3 + G psi^2/6 is the same in liquid and vapour."""
+    nx, ny = 128, 4
+    o = Oracle(nx, ny)
+    o.set_interforce(-120.0, 4.0, 200.0)
+    x = np.arange(nx)
+    rho = np.broadcast_to(np.where((x > nx // 4) & (x < 3 * nx // 4), 500.0, 100.0), (ny, nx))
+    o.set_equilibrium(rho)
+    m0 = rho.sum()
+    o.step(8000)
+    r = o.fields()[0][0]
+    psi = 4 * np.exp(-200 / r)
+    p = r / 3 - 120 * psi ** 2 / 6
+    assert r[nx // 2] / r[2] > 5
+    assert abs(p[nx // 2] - p[2]) / p[2] < 1e-2
+    assert abs(o.thermo()["mass1"] - m0) / m0 < 1e-11
+
+
+def test_two_component_sc_flat_interface():
+    """Two components with interforce G: masses are conserved exactly and
+    p = (rho1 + rho2)/3 + G rho1 rho2 / 3 balances across the interface."""
+    nx, ny, G = 128, 4, 1.5
+    o = Oracle(nx, ny, 2)
+    o.set_interforce(G)
+    x = np.arange(nx)
+    one = (x > nx // 4) & (x < 3 * nx // 4)
+    r1 = np.broadcast_to(np.where(one, 2.0, 0.1), (ny, nx))
+    r2 = np.broadcast_to(np.where(one, 0.1, 2.0), (ny, nx))
+    o.set_equilibrium(r1, comp=0)
+    o.set_equilibrium(r2, comp=1)
+    o.step(6000)
+    a, b = o.fields(0)[0][0], o.fields(1)[0][0]
+    p = (a + b) / 3 + G * a * b / 3
+    assert a[nx // 2] / a[2] > 20 and b[2] / b[nx // 2] > 20
+    assert abs(p[nx // 2] - p[2]) / p[2] < 1e-4
+    th = o.thermo()
+    assert abs(th["mass1"] - r1.sum()) / r1.sum() < 1e-12
+    assert abs(th["mass2"] - r2.sum()) / r2.sum() < 1e-12
+
+
+def test_sc_force_is_cohesive_for_negative_G():
+    """A single dense node in a uniform field: with G < 0 (cohesive, Sec.
+    Phase separation) its neighbours are pulled toward it; G > 0 pushes.
+    At the first step j does not depend on the force, so the difference of
+    the reported momentum j + F/2 with and without interforce is F/2."""
+    n = 7
+    rho = np.full((n, n), 200.0)
+    rho[3, 3] = 400.0
+
+    def run(G):
+        o = Oracle(n, n)
+        o.set_interforce(G, 4.0, 200.0)
+        o.set_equilibrium(rho)
+        o.step()
+        _, px, py, _ = o.fields()
+        return px, py
+
+    px0, py0 = run(0.0)
+    for G, sign in ((-120.0, 1.0), (120.0, -1.0)):
+        px, py = run(G)
+        Fx, Fy = 2 * (px - px0), 2 * (py - py0)
+        assert sign * Fx[3, 2] > 0 and sign * Fx[3, 4] < 0   # toward (3,3)
+        assert sign * Fy[2, 3] > 0 and sign * Fy[4, 3] < 0
+        assert np.isclose(Fx[3, 2], -Fx[3, 4], rtol=1e-12)
+        assert np.isclose(Fx[3, 2], Fy[2, 3], rtol=1e-12)
+        assert abs(Fx.sum()) < 1e-9 and abs(Fy.sum()) < 1e-9
+
+
+def test_adhesion_acts_normal_to_a_wall():
+    """adhesiveforce next to a straight solid row: the force is normal to
+    the wall, attractive for G < 0 (hydrophilic, Sec. Contact angles I),
+    mirror-symmetric on the two sides, and zero beyond the first row."""
+    nx, ny = 5, 9
+    for G in (-250.0, 70.0):
+        o = Oracle(nx, ny)
+        mask = np.zeros((ny, nx), np.uint8)
+        mask[4, :] = 1
+        o.set_solid(mask)
+        o.set_adhesiveforce(G, 4.0, 200.0)
+        o.set_equilibrium(np.where(mask, 0.0, 200.0))
+        o.step()
+        _, px, py, _ = o.fields()
+        assert np.allclose(px, 0, atol=1e-13)
+        toward = -np.sign(G)
+        assert toward * py[5, 0] < 0 and toward * py[3, 0] > 0   # toward row 4
+        assert np.isclose(py[5, 0], -py[3, 0], rtol=1e-12)
+        assert np.allclose(py[[1, 2, 6, 7], :], 0, atol=1e-13)
+
+
+def test_two_component_adhesion_sign():
+    """Two components: adhesiveforce G_s with rho_s; G > 0 repels the
+    component from the wall, G < 0 attracts it."""
+    nx, ny = 4, 7
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[3, :] = 1
+    o = Oracle(nx, ny, 2)
+    o.set_solid(mask)
+    o.set_adhesiveforce(0.2, comp=0)
+    o.set_adhesiveforce(-0.2, comp=1)
+    o.set_equilibrium(np.where(mask, 0, 1.0), comp=0)
+    o.set_equilibrium(np.where(mask, 0, 1.0), comp=1)
+    o.step()
+    p1 = o.fields(0)[2]
+    p2 = o.fields(1)[2]
+    assert p1[4, 0] > 0 and p1[2, 0] < 0      # pushed away from row 3
+    assert p2[4, 0] < 0 and p2[2, 0] > 0      # pulled toward row 3
+
+
+# --------------------------------------------------------------------------
+# solute transport (solute command, Eq. (3), Eq. (4))
+# --------------------------------------------------------------------------
+
+def _pulse(q, taus, N, s0, T, u=(0.0, 0.0)):
+    o = Oracle(N, N, 1, q)
+    o.set_taus(taus)
+    y, x = np.mgrid[0:N, 0:N].astype(float)
+    c = N / 2
+    C = np.exp(-((x - c) ** 2 + (y - c) ** 2) / (2 * s0 * s0))
+    o.set_equilibrium(1.0, u[0], u[1])
+    o.set_solute_equilibrium(C, u[0], u[1])
+    o.step(T)
+    return C, o.solute_C(), x, y, c
+
+
+@pytest.mark.parametrize("q", [4, 9])
+@pytest.mark.parametrize("taus", [0.7, 1.0])
+def test_gaussian_pulse_diffusion(q, taus):
+    """Pure diffusion of a Gaussian: mass kept to rounding, variance grows
+    at 2D per axis with D = (tau_s - 1/2)/2 on D2Q4 (solute command) and
+    (tau_s - 1/2)/3 on D2Q9, and the field matches the analytic solution
+    M/(4 pi D (t + t0)) exp(-r^2/(4 D (t + t0)))."""
+    N, s0, T = 96, 4.0, 300
+    C0, C, x, y, c = _pulse(q, taus, N, s0, T)
+    D = (taus - 0.5) / (2 if q == 4 else 3)
+    M0 = C0.sum()
+    assert abs(C.sum() - M0) / M0 < 1e-13
+    var0 = (((x - c) ** 2) * C0).sum() / M0
+    var = (((x - c) ** 2) * C).sum() / M0
+    assert abs((var - var0) / (2 * T) / D - 1) < 1e-2
+    t0 = s0 * s0 / (2 * D)
+    Ca = M0 / (4 * np.pi * D * (T + t0)) * np.exp(-((x - c) ** 2 + (y - c) ** 2) / (4 * D * (T + t0)))
+    assert np.max(np.abs(C - Ca)) / Ca.max() < 1e-2
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_solute_uniform_advection_is_exact(q):
+    """With the solvent at uniform velocity u and the solute started at
+    g_eq(C, u), the centre of mass moves by exactly u per iteration."""
+    N, T, u = 128, 200, (0.02, -0.01)
+    C0, C, x, y, c = _pulse(q, 0.7, N, 3.0, T, u)
+    M = C.sum()
+    X = ((x - c) * C).sum() / M
+    Y = ((y - c) * C).sum() / M
+    assert abs(X - u[0] * T) < 1e-9 and abs(Y - u[1] * T) < 1e-9
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_solute_conserved_with_bounce_back(q):
+    """Periodic box with obstacles, no reaction: sum C is kept exactly."""
+    nx, ny = 21, 15
+    mask = synth.random_mask(nx, ny, 4, 0.3)
+    o = Oracle(nx, ny, 1, q)
+    o.set_solid(mask)
+    o.set_taus(0.8)
+    o.set_equilibrium(np.where(mask, 0, 1.0), synth.noise_field(nx, ny, 1, -0.03, 0.03),
+                      synth.noise_field(nx, ny, 2, -0.03, 0.03))
+    Cin = np.where(mask, 0, synth.noise_field(nx, ny, 3, 0.5, 1.5))
+    o.set_solute_equilibrium(Cin)
+    o.step(100)
+    assert abs(o.solute_C().sum() - Cin.sum()) / Cin.sum() < 1e-13
+    assert abs(o.thermo()["solute"] - Cin.sum()) / Cin.sum() < 1e-13
+
+
+def test_solute_dirichlet_and_adiabatic_openings():
+    """Dirichlet holds C = Cbar on its nodes after streaming; adiabatic
+    makes the crossing mode equal to the outgoing one (g3 = g1 on xhi), so
+    pure diffusion from a dirichlet inlet fills a closed-ended channel up
+    to Cbar."""
+    nx, ny = 24, 6
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    for q in (4, 9):
+        w = synth.Workload(name="sol", nx=nx, ny=ny, solid=solid,
+                           rho=[np.where(solid, 0.0, 1.0)], tau=(1.0,),
+                           openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("dirichlet", 0, 1.0)],
+                                                   solute=("dirichlet", 1.0)),
+                                     synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0, 1.0)],
+                                                   solute=("adiabatic", 0.0))],
+                           solute_q=q, taus=1.0, C=np.zeros((ny, nx)))
+        o = oracle_from_workload(w)
+        o.step(20000)
+        C = o.solute_C()
+        assert np.allclose(C[1:-1, :], 1.0, atol=1e-6), C[ny // 2]
+
+
+# --------------------------------------------------------------------------
+# surface reaction, precipitation, growth (surface_reaction, App. C)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("q,i", [(4, 0), (4, 3), (9, 1), (9, 6)])
+def test_reaction_link_limits_and_flux(q, i):
+    """k_r = 0 is bounce-back; k_r -> infinity pins the link concentration
+    to C_s; in general the link removes exactly k_r (C_i - C_s), the
+    macroscopic rule D dC/dn = k_r (C - C_s) of the surface_reaction
+    command."""
+    for g_out in (0.0, 0.2, 0.37):
+        Ci, gin = orc.reaction_link(q, i, g_out, 0.0, 0.5)
+        assert gin == g_out
+        Ci, gin = orc.reaction_link(q, i, g_out, 1e14, 0.5)
+        assert abs(Ci - 0.5) < 1e-12
+        for kr in (1e-3, 0.25, 3.0):
+            for Cs in (0.0, 0.5):
+                Ci, gin = orc.reaction_link(q, i, g_out, kr, Cs)
+                assert np.isclose(g_out - gin, kr * (Ci - Cs), rtol=1e-12, atol=1e-16)
+
+
+def test_reaction_at_zero_rate_is_bounce_back():
+    """surface_reaction with k_r = 0 reproduces the bounce-back run bit for
+    bit (no deposit, since dB = 0 is not > 0)."""
+    nx, ny = 17, 13
+    mask = synth.random_mask(nx, ny, 8, 0.2)
+    runs = []
+    for react in (False, True):
+        o = Oracle(nx, ny, 1, 4)
+        o.set_solid(mask)
+        o.set_taus(0.9)
+        o.set_equilibrium(np.where(mask, 0, 1.0), 0.01, 0.0)
+        o.set_solute_equilibrium(np.where(mask, 0, synth.noise_field(nx, ny, 5, 0.5, 1.5)))
+        if react:
+            o.set_reaction(0.0, 0.3, 0.5, 1e9, 1)
+            o.set_b(np.where(mask, 0.5, 0.0))
+        o.step(60)
+        runs.append((o.g(), o.b()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[1][1], np.where(mask, 0.5, 0.0))
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_precipitation_bookkeeping(q):
+    """One solid node in a uniform solute at rest: every reactive link is
+    alone on its fluid node, so the deposit dB equals the link's reaction
+    flux; the solid gains sum dB while the fluid loses the reaction flux
+    plus the deposit (the precipitation of the surface_reaction command is
+    taken from the incoming modes after the reactive rule), a ratio -2."""
+    n = 7
+    mask = np.zeros((n, n), np.uint8)
+    mask[3, 3] = 1
+    o = Oracle(n, n, 1, q)
+    o.set_solid(mask)
+    o.set_taus(1.0)
+    o.set_equilibrium(np.where(mask, 0, 1.0))
+    C0 = np.where(mask, 0, 1.5)
+    o.set_solute_equilibrium(C0)
+    o.set_reaction(0.05, 0.5, 0.5, 1e9, 1)
+    o.set_b(np.where(mask, 0.5, 0.0))
+    o.step()
+    dC = o.solute_C().sum() - C0.sum()
+    dB = o.b()[3, 3] - 0.5
+    assert dB > 0
+    assert np.isclose(dC / dB, -2.0, rtol=1e-12)
+    th = o.thermo()
+    assert np.isclose(th["bsum"], 0.5 + dB, rtol=1e-14)
+    # the neighbours are equivalent by symmetry
+    C = o.solute_C()
+    assert np.isclose(C[3, 2], C[3, 4], rtol=1e-14) and np.isclose(C[2, 3], C[4, 3], rtol=1e-14)
+    assert np.isclose(C[3, 2], C[2, 3], rtol=1e-14)
+
+
+def test_no_precipitation_when_undersaturated():
+    """dB = k_r (C - C_s) is applied only when positive (dissolution does
+    not reduce b)."""
+    n = 5
+    mask = np.zeros((n, n), np.uint8)
+    mask[2, 2] = 1
+    o = Oracle(n, n, 1, 4)
+    o.set_solid(mask)
+    o.set_equilibrium(np.where(mask, 0, 1.0))
+    o.set_solute_equilibrium(np.where(mask, 0, 0.2))
+    o.set_reaction(0.1, 0.5, 0.5, 1e9, 1)
+    o.set_b(np.where(mask, 0.5, 0.0))
+    o.step(5)
+    assert o.b()[2, 2] == 0.5
+
+
+def test_splitmix64_published_vectors():
+    """SplitMix64 started from state 0 yields the published sequence."""
+    gold = read_golden("splitmix64.txt")
+    gamma = 0x9E3779B97F4A7C15
+    for k in range(3):
+        assert orc.splitmix64((k * gamma) & 0xFFFFFFFFFFFFFFFF) == int(gold[f"out{k}"], 16)
+
+
+def _growth_case(seed, block=()):
+    n = 5
+    mask = np.zeros((n, n), np.uint8)
+    mask[2, 2] = 1
+    for (yy, xx) in block:
+        mask[yy, xx] = 1
+    o = Oracle(n, n, 1, 4)
+    o.set_solid(mask)
+    o.set_equilibrium(np.where(mask, 0, 1.0))
+    o.set_solute_equilibrium(np.where(mask, 0, 0.5))
+    o.set_reaction(0.1, 0.5, 0.25, 1.0, seed)     # C = C_s: no deposit
+    o.set_b(np.where(mask, 0.25, 0.0) + np.where(np.arange(n * n).reshape(n, n) == 12, 1.0, 0.0))
+    return o, mask
+
+
+def test_growth_single_trigger():
+    """A solid node with b > b_max turns exactly one fluid 4-neighbour to
+    solid; its own b is reset to 0 (App. C rule 5); the new solid starts at
+    b0; the removed fluid and solute mass are booked."""
+    o, mask = _growth_case(seed=42)
+    f_before = o.f()
+    g_before = o.g()
+    o.step()
+    flips = o.flips()
+    assert len(flips) == 1
+    k = int(flips[0])
+    yy, xx = divmod(k, 5)
+    assert (abs(yy - 2) + abs(xx - 2)) == 1
+    solid = o.solid()
+    assert solid[yy, xx] == 1 and solid.sum() == 2
+    b = o.b()
+    assert b[2, 2] == 0.0 and b[yy, xx] == 0.25
+    th = o.thermo()
+    assert th["removed1"] > 0 and th["removed_solute"] > 0
+    assert np.isclose(th["mass1"] + th["removed1"], f_before.sum(), rtol=1e-13)
+    assert np.isclose(th["solute"] + th["removed_solute"], g_before.sum(), rtol=1e-13)
+
+
+def test_growth_choice_is_equiprobable():
+    """Every fluid 4-neighbour is equally likely (surface_reaction command;
+    App. C rule 3): over 2000 seeds each of 4 candidates, and each of 2
+    when the others are solid, is chosen within 4 sigma of uniform; solid
+    neighbours are never chosen."""
+    for block, ncand in (((), 4), (((2, 3), (1, 2)), 2)):
+        counts = {}
+        S = 2000
+        for seed in range(S):
+            o, mask = _growth_case(seed, block)
+            o.step()
+            fl = o.flips()
+            assert len(fl) == 1
+            counts[int(fl[0])] = counts.get(int(fl[0]), 0) + 1
+        assert len(counts) == ncand
+        p = 1 / ncand
+        sd = np.sqrt(S * p * (1 - p))
+        for c in counts.values():
+            assert abs(c - S * p) < 4 * sd, counts
+        for (yy, xx) in block:
+            assert yy * 5 + xx not in counts
