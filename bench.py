@@ -1,0 +1,335 @@
+"""Benchmark of the lattice Boltzmann hot path on GB300.
+
+Workload: the porous-medium lattice of the paper's method (1024 x 1024,
+random discs at porosity 0.7, Zou-He density inlet 1.001 / outlet 1.0,
+tau = 0.8, periodic in y), FP32 population storage.  A step is one
+iteration of the update through the C ABI (lb_iteration(ctx, 1)); thermo
+runs every 100 iterations as in the paper's scripts.
+
+value: MLUPS over all nodes, whole job, inputs resident in HBM; the L2 is
+flushed (a write of a buffer twice its size, then a read of another) before
+every timed step and each step is timed by CUDA events on the library's
+stream.  e2e: the same metric through the public API with host buffers:
+every step uploads the state snapshot from pinned memory, iterates once
+and downloads density and velocity to pinned memory.
+--impl reference times the FP64 CPU oracle on the same workload.
+
+Multi-GPU (torchrun): every rank advances its own replica of the lattice
+(independent units, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 MLUPS and % of HBM roofline; 16-bit-storage & batched vs plain FP32 at ≤1e-5"
+WORKLOAD = "porous 1024x1024 (random discs r 8-24 seed 1, porosity 0.7, Zou-He rho 1.001/1.0, tau 0.8)"
+BYTES_PER_FLUID_NODE = {"fp32": 72, "fp16": 36, "bf16": 36}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("k_fluid.cu", "lbdev.cuh", "lbint.h"):
+        with open(os.path.join(ROOT, "paper_1202_0442_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, storage: str, units: int):
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu
+    summary, scaled to this launch's fluid nodes; None when the summary was
+    taken on different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    e = d.get(f"{kernel}/{storage}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_fluid_node"] * units
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        return world, rank, local, dist
+    return 1, 0, 0, None
+
+
+def max_over_ranks(x: float, dist, world: int) -> float:
+    if dist is None or world == 1:
+        return x
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else torch.device("cpu")
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(w, seconds: float, max_steps: int):
+    """Time the FP64 oracle on workload w: single-threaded MLUPS."""
+    from oracle.drive import oracle_from_workload
+    o = oracle_from_workload(w)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, seconds / max(one, 1e-9))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    return w.nodes * n / dt / 1e6, n, dt
+
+
+def run_reference(args, world, rank, dist):
+    from paper_1202_0442_gb300 import synth
+    if rank != 0:
+        return 0
+    w = synth.porous()
+    from oracle.drive import oracle_from_workload
+    o = oracle_from_workload(w)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = w.nodes * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (single thread)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"full 1024x1024 lattice, {args.steps} timed iterations"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args, world, rank, local, dist):
+    import torch
+    from paper_1202_0442_gb300 import build, lb2d, synth
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    if local == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    w = synth.porous()
+    storage = args.storage
+    lt = lb2d.from_workload(w, storage, h_max=2e-3, device=local, stream=stream.cuda_stream)
+    lt.thermo(100)
+    nodes, fluid = w.nodes, w.fluid_nodes
+
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush_w = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
+    flush_r = torch.ones(2 * l2 // 4, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_w.fill_(1.0)
+        sink.add_(flush_r.sum())
+
+    for _ in range(args.warmup):
+        flush()
+        lt.iteration(1)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    thermo_step = []
+    sampler = ClockSampler(local) if local == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    launches0 = lt.launch_count()
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        flush()
+        ev[k][0].record(stream)
+        lt.iteration(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_start
+    launches = lt.launch_count() - launches0
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    for k in range(args.steps):
+        step_no = args.warmup + k + 1
+        thermo_step.append(step_no % 100 == 0)
+    times = np.array([a.elapsed_time(b) for a, b in ev])
+    ms_step = float(times.mean())
+    plain = times[~np.array(thermo_step)] if (~np.array(thermo_step)).any() else times
+    kernel_ms = float(np.median(plain))
+    ms_step = max_over_ranks(ms_step, dist, world)
+    value = world * nodes / (ms_step * 1e-3) / 1e6
+
+    # e2e through the public API with pinned host buffers
+    size = lt.state_size()
+    snap = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+    lt.save_state(snap)
+    outs = tuple(torch.empty((w.ny, w.nx), dtype=torch.float32, pin_memory=True) for _ in range(3))
+    lt.thermo(0)  # every call ends with thermo and fresh node fields
+    for _ in range(2):
+        lt.load_state(snap)
+        lt.iteration(1)
+        lt.velocity_f32(outs)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ke = max(3, min(args.steps, 20))
+    t0e = time.perf_counter()
+    for _ in range(ke):
+        lt.load_state(snap)
+        lt.iteration(1)
+        lt.velocity_f32(outs)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0e) / ke, dist, world)
+    e2e = {"value": world * nodes / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(size),
+           "d2h_bytes_per_step": int(3 * 4 * nodes)}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    alg_bytes = BYTES_PER_FLUID_NODE[storage] * fluid
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    traffic = recorded_traffic("k_fluid_local", storage, fluid)
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": nodes, "fluid_nodes": fluid,
+                   "porosity": w.info["porosity"], "storage": storage,
+                   "l2": "flushed before every timed step (write 2xL2, read 2xL2)",
+                   "thermo_every": 100, "parallelism": f"replicas x{world}"},
+        "mflups": world * fluid / (ms_step * 1e-3) / 1e6,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_fluid_local", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "wall_s_timed_region": wall,
+    }
+    if clocks:
+        line["clocks"] = clocks
+    if world == 1 and not args.no_cpu_baseline:
+        v, n, dt = oracle_rate(w, args.cpu_seconds, 2000)
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"full 1024x1024 lattice, {n} iterations ({dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local, dist = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank, dist)
+        return run_gb300(args, world, rank, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

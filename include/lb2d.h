@@ -1,0 +1,298 @@
+/*
+ * lb2d.h -- C ABI of the GB300 lattice Boltzmann library.
+ *
+ * One call per command of the paper's command set (arXiv:1202.0442,
+ * "Introduction to Perl module lb2d.pm 0.1", Sec. Commands): set up a
+ * lattice with lb_lattice, geometry, openings, forces and initial state,
+ * then advance it with lb_iteration and read the thermo record and fields.
+ * All per-iteration work runs in the library's CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *   - Every call returns int: LB_OK (0) or a negative LB_E_* code;
+ *     lb_last_error() gives the message of the last failure on a context.
+ *   - Nodes are (x, y), 0 <= x < nx, 0 <= y < ny.  A paper script's
+ *     lattice(N_x, N_y) has nx = N_x + 1, ny = N_y + 1 (lattice command:
+ *     "sites are numbered from 0 to N_x").  Node arrays passed in or out
+ *     are dense row-major [ny][nx] (x fastest); population arrays are
+ *     [q][ny][nx] with the D2Q9 numbering e0=(0,0) e1=(1,0) e2=(0,1)
+ *     e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1) and the
+ *     D2Q4 numbering g1..g4 = +x,+y,-x,-y at index 0..3.
+ *   - Host pointers are borrowed for the duration of the call; the library
+ *     copies what it needs.  Pinned host memory makes the copies faster
+ *     but is not required.  All device memory is owned by the library and
+ *     released by lb_destroy.
+ *   - Calls on one context run on the CUDA stream given to lb_create, in
+ *     order; calls that return host data synchronise that stream.  A
+ *     context is not thread safe.
+ *   - Fluid components are numbered 1 and 2 as in the paper's commands
+ *     (the "fluid" argument); 1 is the only one of a single-component run.
+ */
+#ifndef LB2D_H
+#define LB2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LB_OK 0
+#define LB_E_ORDER (-1)       /* command out of the required order */
+#define LB_E_ARG (-2)         /* invalid argument or inconsistent setup */
+#define LB_E_UNSUPPORTED (-3) /* valid in the paper, not built here */
+#define LB_E_CUDA (-4)        /* CUDA runtime error (message has details) */
+#define LB_E_NAN (-5)         /* thermo found a non-finite sum */
+#define LB_E_NOMEM (-6)       /* device or host allocation failed */
+
+/* population storage (lb_set_storage) */
+#define LB_FP32 0 /* f_i - w_i rho_ref in FP32 */
+#define LB_FP16 1 /* (f_i - w_i rho_ref) * 2^s in IEEE binary16 */
+#define LB_BF16 2 /* f_i - w_i rho_ref in bfloat16 */
+/* OR'd into LB_FP16 / LB_BF16: round stores stochastically (a dither drawn
+ * from a hash of node, direction and iteration; reproducible) instead of
+ * to nearest even */
+#define LB_STOCHASTIC_ROUNDING 0x100
+
+typedef struct lb_ctx lb_ctx;
+typedef struct lb_batch lb_batch;
+
+/* thermo record (thermo command): FP64 sums over the state at the end of
+ * the last iteration.  mass = sum of rho over fluid nodes; mom = sum of
+ * the physical momentum j + F/2 (Eq. (4)); mass_eq = sum of the
+ * equilibrium densities; solute = sum of C over fluid nodes; bsum = sum of
+ * the precipitate b over solid nodes; removed* = fluid and solute mass of
+ * nodes that surface growth turned solid. */
+typedef struct {
+  int64_t step;
+  double mass[2];
+  double mom[2];       /* x, y: mixture */
+  double mom_comp[2][2];
+  double mass_eq[2];
+  double solute;
+  double bsum;
+  double removed[2];
+  double removed_solute;
+  int64_t nsolid;
+  int64_t nfluid;
+  int64_t flips; /* growth events since the start */
+} lb_thermo_t;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, issuing all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream stays owned by the caller and must outlive the context. */
+int lb_create(int device, void *cuda_stream, lb_ctx **out);
+/* Free every device and host buffer of the context. */
+int lb_destroy(lb_ctx *ctx);
+/* Message of the last failing call on ctx (never NULL). */
+const char *lb_last_error(const lb_ctx *ctx);
+/* Number of kernels the context has launched so far (graph replays count
+ * their kernel nodes). */
+int lb_launch_count(const lb_ctx *ctx, uint64_t *out);
+
+/* ---- initialization commands ---------------------------------------- */
+
+/* lattice command: style "d2q9", nx x ny nodes, relaxation time tau > 1/2.
+ * Must come first.  Boundaries are periodic until openings or obstacles
+ * say otherwise. */
+int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau);
+
+/* processors command: accepted after lb_lattice and ignored (one GPU runs
+ * the whole lattice, like the serial module); before lb_lattice it fails
+ * with LB_E_ORDER as in the paper. */
+int lb_processors(lb_ctx *ctx, int px, int py);
+
+/* fluids command: two components with relaxation times tau1, tau2 and
+ * density-ratio parameters alpha1, alpha2 (pass 4/9 for the plain
+ * equilibrium of Eq. (2); other values give LB_E_UNSUPPORTED).  Must follow
+ * lb_lattice and precede openings, initial state and forces. */
+int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1,
+              double alpha2);
+
+/* solute command: one solute on a D2Q4 (q = 4, the paper's lattice) or
+ * D2Q9 (q = 9) lattice with relaxation time taus > 1/2; D = (taus-1/2)/2
+ * on D2Q4, (taus-1/2)/3 on D2Q9. */
+int lb_solute(lb_ctx *ctx, double taus, int q);
+
+/* Population storage: LB_FP32, LB_FP16 or LB_BF16 (the 16-bit ones
+ * optionally | LB_STOCHASTIC_ROUNDING).  Populations are kept
+ * as deviations f_i - w_i rho_ref[c] from the rest state of reference
+ * density rho_ref[c] (one per component; NULL = 1.0); FP16 stores them
+ * multiplied by the power of two 2^s with s the largest integer such that
+ * h_max * 2^s <= 2^14, h_max being the largest |f_i - w_i rho_ref| the
+ * run will see (<= 0 picks 0.25 * max rho_ref).  Arithmetic is FP32 in all
+ * three.  Before the first lb_iteration only. */
+int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref,
+                   double h_max);
+
+/* boundary_style command: "noslip" (half-way bounce-back).  "slip",
+ * "mixed" and "hybrid" give LB_E_UNSUPPORTED.  Must precede obstacles. */
+int lb_boundary_style(lb_ctx *ctx, const char *style);
+
+/* obstacle command: mark nodes solid.  Rectangle with inclusive bounds;
+ * circle (x-xc)^2 + (y-yc)^2 <= r^2 with periodic distance; mask: nx*ny
+ * bytes, nonzero = solid (for generated media).  After lb_boundary_style
+ * (LB_E_ORDER otherwise).  Solid overrides openings and initial state. */
+int lb_obstacle_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1);
+int lb_obstacle_circle(lb_ctx *ctx, int xc, int yc, int r);
+int lb_obstacle_mask(lb_ctx *ctx, const uint8_t *mask);
+
+/* inlet/outlet commands: an opening on wall "xlo", "xhi", "ylo" or "yhi"
+ * spanning a0..a1 along it (y for x-walls, x for y-walls).  label1 names
+ * it for fluid 1 (and the solute), label2 for fluid 2 (NULL with one
+ * component).  Openings on one wall may not overlap; two walls may not
+ * both have an opening on a shared corner node. */
+int lb_inlet(lb_ctx *ctx, const char *wall, int a0, int a1,
+             const char *label1, const char *label2);
+int lb_outlet(lb_ctx *ctx, const char *wall, int a0, int a1,
+              const char *label1, const char *label2);
+
+/* inlet_momentum/outlet_momentum commands (App. A): style "poiseuille"
+ * (v = v_max of the profile), "uniform" (v = speed, into the domain for
+ * an inlet and out of it for an outlet), "dirichlet" (rho held), or
+ * "gradient" (extrapolation after collision).  rho is the opening's
+ * density (held by dirichlet; initial value for the others).  |v| < 1. */
+int lb_inlet_momentum(lb_ctx *ctx, const char *label, const char *style,
+                      double v, double rho);
+int lb_outlet_momentum(lb_ctx *ctx, const char *label, const char *style,
+                       double v, double rho);
+
+/* inlet_solute/outlet_solute commands (App. B): "dirichlet" (C held at C)
+ * or "adiabatic" (zero flux; C is the initial value).  "flux" gives
+ * LB_E_UNSUPPORTED.  Every opening needs a solute style when a solute is
+ * on. */
+int lb_inlet_solute(lb_ctx *ctx, const char *label, const char *style,
+                    double C);
+int lb_outlet_solute(lb_ctx *ctx, const char *label, const char *style,
+                     double C);
+
+/* surface_reaction command: rate kr >= 0, saturation Cs, style "growth",
+ * initial deposit b0 on every solid node, growth threshold bmax.  seed
+ * selects the growth choices (SplitMix64 of seed ^ (t*nx*ny + node)).
+ * After lb_solute. */
+int lb_surface_reaction(lb_ctx *ctx, double kr, double Cs,
+                        const char *style, double b0, double bmax,
+                        uint64_t seed);
+
+/* position0 command: select the region the next momentum0 /
+ * concentration0 calls fill (rectangle inclusive, circle as obstacle). */
+int lb_position0_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1);
+int lb_position0_circle(lb_ctx *ctx, int xc, int yc, int r);
+
+/* momentum0 command: add value to population `mode` (0..8) of fluid
+ * `fluid` on the fluid nodes of the last position0 region (values of
+ * repeated calls add up; negative values subtract).  LB_E_ORDER without a
+ * preceding position0. */
+int lb_momentum0(lb_ctx *ctx, int mode, double value, int fluid);
+
+/* concentration0 command: add value to the concentration of the last
+ * position0 region (populations at equilibrium with the fluid at rest). */
+int lb_concentration0(lb_ctx *ctx, double value);
+
+/* read_data "equilibrium" analogue: populations of fluid `fluid` become
+ * f_eq(rho, u) of Eq. (2) on fluid nodes.  rho, ux, uy: host [ny][nx]
+ * FP64 (ux/uy may be NULL = 0).  Allowed before or after iterations. */
+int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho,
+                       const double *ux, const double *uy);
+/* Same for the solute: g = g_eq(C, u) of Eq. (3) (D2Q9: w_i C(1+3e.u)). */
+int lb_set_solute_equilibrium(lb_ctx *ctx, const double *C,
+                              const double *ux, const double *uy);
+/* Set every population of fluid `fluid` (host [9][ny][nx] FP64). */
+int lb_set_populations(lb_ctx *ctx, int fluid, const double *f);
+/* Set every solute population (host [q][ny][nx] FP64). */
+int lb_set_solute_populations(lb_ctx *ctx, const double *g);
+/* Set the precipitate b of every node (host [ny][nx] FP64; only solid
+ * nodes' values are used). */
+int lb_set_precipitate(lb_ctx *ctx, const double *b);
+
+/* ---- force fields ---------------------------------------------------- */
+
+/* aveforce / aveacceleration commands: add value * e_mode (mode 0..8) to
+ * the force per fluid node (or acceleration; force = rho a) of `fluid`.
+ * The _xy forms add (fx, fy) directly. */
+int lb_aveforce(lb_ctx *ctx, int mode, double value, int fluid);
+int lb_aveforce_xy(lb_ctx *ctx, double fx, double fy, int fluid);
+int lb_aveacceleration(lb_ctx *ctx, int mode, double value, int fluid);
+int lb_aveacceleration_xy(lb_ctx *ctx, double ax, double ay, int fluid);
+
+/* interforce command: one component F = -G psi(x) sum_i w_i psi(x+e_i) e_i
+ * with psi = psi0 exp(-rho0/rho); two components F_s = -G rho_s(x)
+ * sum_i w_i rho_sbar(x+e_i) e_i (psi0, rho0 ignored).  psi = 0 on solid
+ * nodes.  Not combined with inlet/outlet openings (LB_E_UNSUPPORTED). */
+int lb_interforce(lb_ctx *ctx, double G, double psi0, double rho0);
+
+/* adhesiveforce command: F = -G psi(x) sum_i w_i s(x+e_i) e_i, s = 1 on
+ * solid nodes; one component psi = psi0 exp(-rho0/rho), two components
+ * psi = rho_fluid. */
+int lb_adhesiveforce(lb_ctx *ctx, double G, double psi0, double rho0,
+                     int fluid);
+
+/* ---- output and action ----------------------------------------------- */
+
+/* thermo command: evaluate the thermo record and the node fields every Nf
+ * iterations (Nf > 0), or at the end of every lb_iteration call (Nf = 0,
+ * the default).  Evaluating them reads the record back to the host, so it
+ * synchronises the stream. */
+int lb_thermo(lb_ctx *ctx, int Nf);
+
+/* iteration command: advance Nt iterations.  The first call validates the
+ * setup (LB_E_ARG with a message if it is inconsistent) and moves the
+ * state to the GPU.  Returns LB_E_NAN if a thermo sum is not finite. */
+int lb_iteration(lb_ctx *ctx, int Nt);
+
+/* Thermo record of the last thermo evaluation. */
+int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out);
+
+/* Node fields of the last thermo evaluation for fluid `fluid` (host
+ * [ny][nx] FP64, any pointer may be NULL): density, physical momentum
+ * density j + F/2 and equilibrium density; zero on solid nodes. */
+int lb_get_fields(lb_ctx *ctx, int fluid, double *rho, double *px,
+                  double *py, double *rho_eq);
+/* Total density and solvent velocity u = sum(j + F/2)/sum(rho) (Eq. (4))
+ * of the last thermo evaluation as FP32 host [ny][nx] arrays. */
+int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy);
+/* Current populations of fluid `fluid` (host [9][ny][nx] FP64). */
+int lb_get_populations(lb_ctx *ctx, int fluid, double *f);
+/* Current solute populations (host [q][ny][nx]), concentration of the
+ * last thermo evaluation and current precipitate (host [ny][nx]); NULL
+ * skips. */
+int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b);
+/* Solid mask (host [ny][nx] bytes, 1 = solid). */
+int lb_get_mask(lb_ctx *ctx, uint8_t *mask);
+
+/* Raw state snapshot (checkpoint/resume): populations in their storage
+ * format, mask, solute, precipitate, removed-mass tallies and step
+ * counter.  lb_state_size gives the byte count; save/load copy to/from a
+ * host buffer of that size (pinned memory gives full copy bandwidth).
+ * Loading a snapshot of the same setup resumes bit for bit. */
+int lb_state_size(lb_ctx *ctx, size_t *bytes);
+int lb_save_state(lb_ctx *ctx, void *host, size_t bytes);
+int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes);
+
+/* ---- batched lattices ------------------------------------------------ */
+
+/* Group n committed single-component contexts of one device and stream
+ * (periodic, no openings, no solute, same storage) so that lb_batch_iteration
+ * advances all of them with one kernel launch per iteration.  The contexts
+ * stay owned by the caller and must outlive the batch. */
+int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out);
+int lb_batch_destroy(lb_batch *b);
+/* Advance every lattice of the batch Nt iterations; use_graph != 0
+ * captures the launches in a CUDA graph and replays it. */
+int lb_batch_iteration(lb_batch *b, int Nt, int use_graph);
+/* Time the candidate tile shapes and work schedules and keep the fastest;
+ * cache_json (may be NULL) is a file that stores the choice keyed by
+ * device, shapes and storage. */
+int lb_batch_autotune(lb_batch *b, const char *cache_json);
+const char *lb_batch_last_error(const lb_batch *b);
+/* Number of kernels the batch has launched (graph replays count their
+ * kernel nodes). */
+int lb_batch_launch_count(const lb_batch *b, uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

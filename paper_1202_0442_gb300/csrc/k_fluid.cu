@@ -1,0 +1,441 @@
+// k_fluid.cu -- one iteration of the D2Q9 fluid lattice(s).
+//
+// k_fluid_local: pull streaming with half-way bounce-back (Fig. 1 and the
+//   noslip boundary_style of the paper), Zou-He inlet/outlet rules on
+//   opening nodes (inlet_momentum/outlet_momentum, App. A), moments, forces
+//   that need no neighbour density (aveforce, aveacceleration,
+//   adhesiveforce), equilibrium velocity by velocity shift and BGK
+//   collision with Eq. (2) -- all in one pass, one thread per node, nine
+//   loads and nine stores per component.
+// k_fluid_sc: the same plus interforce, which needs the densities of the
+//   eight neighbours after this step's streaming.  Each CTA pulls the
+//   populations of its tile and of a one-node ring around it, stages
+//   rho - rho_ref in shared memory, and reads the neighbours from there; the
+//   ring's extra loads hit L1/L2, the HBM traffic stays nine loads and nine
+//   stores per node.
+// k_gradient: gradient openings, f(wall) = 2 f(wall+n) - f(wall+2n) after
+//   the collision (inlet_momentum command).
+//
+// A CTA of 32 x BY threads covers one 32-node word column of the solid mask;
+// it loads the mask words of its rows (plus one row above and below) and of
+// the two neighbouring word columns into shared memory once, and every
+// thread takes its 3 x 3 solid neighbourhood from there.
+#include "lbdev.cuh"
+
+namespace lbk {
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+// mask words of rows y0-1 .. y0+BY (wrapped) and word columns c-1, c, c+1
+template <int BY>
+__device__ __forceinline__ void load_mask_window(const uint32_t *m, const Geometry &g, int c,
+                                                 int y0, uint32_t (*win)[3]) {
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < (BY + 2) * 3) {
+    const int r = tid / 3, k = tid - r * 3;
+    const int yy = wrapi(y0 - 1 + r, g.ny);
+    const int cc = c - 1 + k;
+    win[r][k] = (cc >= 0 && cc < g.mw) ? __ldg(m + (size_t)yy * g.mw + cc) : 0u;
+  }
+}
+
+// 3 x 3 solid bits of node (x, y) = (32 c + lane, y0 + ty): from the window,
+// except on the first and last column where the periodic neighbour lies in
+// a word the window does not hold
+__device__ __forceinline__ uint32_t window_bits(const uint32_t (*win)[3], const uint32_t *m,
+                                                const Geometry &g, int x, int y, int ty) {
+  const int lane = x & 31;
+  if (x == 0 || x == g.nx - 1) {
+    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+    return nbr_bits(m, g.mw, x, y, xm, xp, ym, yp);
+  }
+  const uint32_t s = row3(win[ty][0], win[ty][1], win[ty][2], lane);
+  const uint32_t c = row3(win[ty + 1][0], win[ty + 1][1], win[ty + 1][2], lane);
+  const uint32_t n = row3(win[ty + 2][0], win[ty + 2][1], win[ty + 2][2], lane);
+  return s | (c << 3) | (n << 6);
+}
+
+// pull the nine populations of node (x, y) from `base` (one component),
+// bouncing back from solid sources; `bits` is the node's neighbourhood
+template <class S>
+__device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, int y,
+                                      uint32_t bits, float inv, float (&h)[9]) {
+  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  const int P = (int)g.plane;
+  const int r0 = y * g.pitch, rm = ym * g.pitch, rp = yp * g.pitch;
+  const int self = r0 + x;
+  // source x - e_i of direction i
+  const int src[9] = {self, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+  // the nine streaming loads do not depend on the mask: issue them first
+#pragma unroll
+  for (int i = 0; i < 9; i++) h[i] = Store<S>::ld(base, i * P + src[i], inv);
+  // half-way bounce-back where the source x - e_i (neighbour opp(i)) is
+  // solid: the node's own outgoing population of the opposite direction
+  if (bits & ~(1u << 4)) {
+#pragma unroll
+    for (int i = 1; i < 9; i++)
+      if (nb(bits, OPP(i))) h[i] = Store<S>::ld(base, OPP(i) * P + self, inv);
+  }
+}
+
+// random word for (node, component, direction, step)
+__device__ __forceinline__ uint32_t rnd(uint32_t seed, int self, int c, int i) {
+  return mix32(((uint32_t)self * 0x9e3779b1u) ^ (seed + 0x632be5abu * (uint32_t)c) ^
+               (0x85ebca6bu * (uint32_t)(i + 1)));
+}
+
+// moments, forces, equilibrium velocity, BGK and the stores of one node.
+// Fsc: interforce already evaluated (zero when off).  ME: mass-exact
+// collision (see below).
+template <class S, int NC, bool ME>
+__device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
+                                              float (&h)[NC][9], const float (&Fsc)[NC][2]) {
+  const Geometry &g = p.g;
+  const int self = y * g.pitch + x;
+  const int P = (int)g.plane;
+  float drho[NC], rho[NC], jx[NC], jy[NC], Fx[NC], Fy[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    const float(&f)[9] = h[c];
+    drho[c] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    rho[c] = p.rho_ref[c] + drho[c];
+    jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    jy[c] = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    Fx[c] = p.fx[c] + rho[c] * p.ax[c] + Fsc[c][0];
+    Fy[c] = p.fy[c] + rho[c] * p.ay[c] + Fsc[c][1];
+    if (p.ads[c]) {
+      float sx, sy;
+      wall_sum(bits, sx, sy);
+      const float psi = (NC == 1) ? p.ads_psi0[c] * expf(-p.ads_rho0[c] / rho[c]) : rho[c];
+      Fx[c] -= p.Gads[c] * psi * sx;
+      Fy[c] -= p.Gads[c] * psi * sy;
+    }
+  }
+  // equilibrium velocity (velocity shift) and the momentum rho u_eq it
+  // carries, the latter formed without a division
+  float uex[NC], uey[NC], mxt[NC], myt[NC];
+  if (NC == 1) {
+    mxt[0] = jx[0] + p.tau[0] * Fx[0];
+    myt[0] = jy[0] + p.tau[0] * Fy[0];
+    const float ir = 1.0f / rho[0];
+    uex[0] = mxt[0] * ir;
+    uey[0] = myt[0] * ir;
+  } else {
+    // common velocity sum(j/tau) / sum(rho/tau), shifted per component
+    float nxs = 0.f, nys = 0.f, den = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      nxs += jx[c] * p.omega[c];
+      nys += jy[c] * p.omega[c];
+      den += rho[c] * p.omega[c];
+    }
+    const float upx = nxs / den, upy = nys / den;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      mxt[c] = rho[c] * upx + p.tau[c] * Fx[c];
+      myt[c] = rho[c] * upy + p.tau[c] * Fy[c];
+      uex[c] = upx + p.tau[c] * Fx[c] / rho[c];
+      uey[c] = upy + p.tau[c] * Fy[c] / rho[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    S *out = (S *)p.fout + (size_t)c * 9 * P;
+    float heq[9];
+    equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], heq);
+    const float om = p.omega[c];
+    if (!ME) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, self, c, i) | 1u) : 0u;
+        Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale, r);
+      }
+    } else {
+      // Mass-exact collision: when |h| is large (two components, or one far
+      // from rho_ref) the rounding of nine stored values of a slowly
+      // changing state repeats every step and drifts the mass.  Here the
+      // exact sum D of the pulled values and the exact sum S of the eight
+      // stored moving populations are formed with error-free sums, and the
+      // rest population is set to D - S -- the BGK value in exact
+      // arithmetic -- rounded stochastically, so the node's mass is kept
+      // up to an unbiased last-bit step.
+      float Dh = h[c][0], Dl = 0.f;
+#pragma unroll
+      for (int i = 1; i < 9; i++) {
+        float s, e;
+        two_sum(Dh, h[c][i], s, e);
+        Dh = s;
+        Dl += e;
+      }
+      float Sh = 0.f, Sl = 0.f;
+#pragma unroll
+      for (int i = 1; i < 9; i++) {
+        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, self, c, i) | 1u) : 0u;
+        const float v = Store<S>::st_ret(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]),
+                                         p.scale, p.inv_scale, r);
+        float s, e;
+        two_sum(Sh, v, s, e);
+        Sh = s;
+        Sl += e;
+      }
+      float rh, rl;
+      two_sum(Dh, -Sh, rh, rl);
+      rl += Dl - Sl;
+      float h0, rem;
+      two_sum(rh, rl, h0, rem);
+      if (rem != 0.f && h0 != 0.f) {
+        const int step = ((rem > 0.f) == (h0 > 0.f)) ? 1 : -1;
+        const float nxt = __int_as_float(__float_as_int(h0) + step);
+        const float pr = fabsf(rem) / fabsf(nxt - h0);
+        const float u01 = (float)(rnd(p.step_seed, self, c, 9) >> 8) * (1.0f / 16777216.0f);
+        if (u01 < pr) h0 = nxt;
+      }
+      const uint32_t r0 = p.sr_seed ? (rnd(p.sr_seed, self, c, 0) | 1u) : 0u;
+      Store<S>::st(out, self, h0, p.scale, r0);
+    }
+    if (p.fields) {
+      float *fl = p.fields + (size_t)c * NFIELD * P;
+      fl[self] = drho[c];
+      fl[P + self] = jx[c] + 0.5f * Fx[c];
+      fl[2 * P + self] = jy[c] + 0.5f * Fy[c];
+      // sum of the equilibrium populations (Mass_eq of the thermo command)
+      fl[3 * P + self] = heq[0] + ((heq[1] + heq[3]) + (heq[2] + heq[4])) +
+                         ((heq[5] + heq[7]) + (heq[6] + heq[8]));
+    }
+  }
+  if (p.uout) {
+    float pxs = 0.f, pys = 0.f, rs = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      pxs += jx[c] + 0.5f * Fx[c];
+      pys += jy[c] + 0.5f * Fy[c];
+      rs += rho[c];
+    }
+    p.uout[self] = pxs / rs;
+    p.uout[P + self] = pys / rs;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
+                                               float (&h)[NC][9]) {
+  const Geometry &g = p.g;
+  if (!(x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1)) return;
+#pragma unroll 1
+  for (int k = 0; k < p.nopen; k++) {
+    if (!opening_has(p.op[k], x, y, g.nx, g.ny)) continue;
+#pragma unroll
+    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, y, p.rho_ref[c]);
+    break;
+  }
+}
+
+constexpr int LOC_BY = 8;
+
+template <class S, int NC, bool ME>
+__global__ void __launch_bounds__(32 * LOC_BY) k_fluid_local(const FluidArgs p) {
+  __shared__ uint32_t win[LOC_BY + 2][3];
+  const Geometry &g = p.g;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * LOC_BY + threadIdx.y;
+  load_mask_window<LOC_BY>(p.mask, g, blockIdx.x, blockIdx.y * LOC_BY, win);
+  __syncthreads();
+  if (x >= g.nx || y >= g.ny) return;
+  if ((win[threadIdx.y + 1][1] >> threadIdx.x) & 1u) return;  // solid nodes hold no populations
+  const uint32_t bits = window_bits(win, p.mask, g, x, y, threadIdx.y);
+  float h[NC][9];
+#pragma unroll
+  for (int c = 0; c < NC; c++)
+    pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
+  if (p.nopen) apply_openings<NC>(p, x, y, h);
+  float F[NC][2];
+#pragma unroll
+  for (int c = 0; c < NC; c++) F[c][0] = F[c][1] = 0.f;
+  collide_store<S, NC, ME>(p, x, y, bits, h, F);
+}
+
+constexpr int SC_TX = 32, SC_TY = 16;
+
+template <class S, int NC>
+__global__ void __launch_bounds__(SC_TX *SC_TY) k_fluid_sc(const FluidArgs p) {
+  // rho - rho_ref of every component for the tile and a one-node ring; slot
+  // (ty + 1, tx + 1) holds node (x0 + tx, y0 + ty) wrapped periodically.
+  // Solid nodes are told apart by the mask bits, not by the stored value.
+  __shared__ float sd[NC][SC_TY + 2][SC_TX + 2];
+  const Geometry &g = p.g;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * SC_TX, y0 = blockIdx.y * SC_TY;
+  const int xr = x0 + tx, yr = y0 + ty;
+  const bool real = xr < g.nx && yr < g.ny;
+  const int x = wrapi(xr, g.nx), y = wrapi(yr, g.ny);
+  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  const uint32_t bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
+  const bool solid = (bits >> 4) & 1u;
+  float h[NC][9];
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    float d = 0.f;
+    if (!solid) {
+      pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
+#pragma unroll
+      for (int i = 0; i < 9; i++) d += h[c][i];
+    }
+    sd[c][ty + 1][tx + 1] = d;
+  }
+  // ring: 2 (TX + 2) + 2 TY slots, one thread each
+  const int tid = ty * SC_TX + tx;
+  constexpr int NRING = 2 * (SC_TX + 2) + 2 * SC_TY;
+  if (tid < NRING) {
+    int sx, sy;
+    if (tid < SC_TX + 2) { sx = tid; sy = 0; }
+    else if (tid < 2 * (SC_TX + 2)) { sx = tid - (SC_TX + 2); sy = SC_TY + 1; }
+    else if (tid < 2 * (SC_TX + 2) + SC_TY) { sx = 0; sy = tid - 2 * (SC_TX + 2) + 1; }
+    else { sx = SC_TX + 1; sy = tid - 2 * (SC_TX + 2) - SC_TY + 1; }
+    const int hx = wrapi(x0 + sx - 1, g.nx), hy = wrapi(y0 + sy - 1, g.ny);
+    const int hxm = hx ? hx - 1 : g.nx - 1, hxp = (hx + 1 == g.nx) ? 0 : hx + 1;
+    const int hym = hy ? hy - 1 : g.ny - 1, hyp = (hy + 1 == g.ny) ? 0 : hy + 1;
+    const uint32_t hb = nbr_bits(p.mask, g.mw, hx, hy, hxm, hxp, hym, hyp);
+    const bool hs = (hb >> 4) & 1u;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      float d = 0.f;
+      if (!hs) {
+        float hh[9];
+        pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, hx, hy, hb, p.inv_scale, hh);
+#pragma unroll
+        for (int i = 0; i < 9; i++) d += hh[i];
+      }
+      sd[c][sy][sx] = d;
+    }
+  }
+  __syncthreads();
+  if (!real || solid) return;
+  // Since sum_i w_i e_i = 0, sum_i w_i psi(x + e_i) e_i equals
+  // sum_i w_i (psi(x + e_i) - psi(x)) e_i; the differences are formed from
+  // rho - rho_ref without cancellation:
+  //   two components: rho_n - rho_c = drho_n - drho_c (psi = rho)
+  //   one component:  psi_n - psi_c = psi_c expm1(rho0 (rho_n - rho_c)/(rho_n rho_c))
+  // and a solid neighbour contributes psi = 0, i.e. a difference -psi_c.
+  float F[NC][2];
+  const int cx = tx + 1, cy = ty + 1;
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    const int o = (NC == 2) ? 1 - c : c;
+    const float dc = sd[o][cy][cx];
+    const float rc = p.rho_ref[o] + dc;
+    const float psic = (NC == 1) ? p.psi0 * expf(-p.sc_rho0 / rc) : rc;
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      float diff;
+      if (nb(bits, i)) {
+        diff = -psic;
+      } else {
+        const float dn = sd[o][cy + EY(i)][cx + EX(i)];
+        if (NC == 1) {
+          const float rn = p.rho_ref[o] + dn;
+          diff = psic * expm1f(p.sc_rho0 * (dn - dc) / (rn * rc));
+        } else {
+          diff = dn - dc;
+        }
+      }
+      sx += W9(i) * (float)EX(i) * diff;
+      sy += W9(i) * (float)EY(i) * diff;
+    }
+    const float self = (NC == 1) ? psic : p.rho_ref[c] + sd[c][cy][cx];
+    F[c][0] = -p.G * self * sx;
+    F[c][1] = -p.G * self * sy;
+  }
+  collide_store<S, NC, true>(p, x, y, bits, h, F);
+}
+
+template <class S>
+__global__ void k_gradient(const GradArgs a) {
+  // one thread per opening node of every gradient opening
+  const int k = blockIdx.y;
+  const OpenDesc &o = a.op[k];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > o.a1 - o.a0) return;
+  const Geometry &g = a.g;
+  const int c = o.a0 + i;
+  int x, y, dx = 0, dy = 0;
+  switch (o.wall) {
+    case 0: x = 0; y = c; dx = 1; break;
+    case 1: x = g.nx - 1; y = c; dx = -1; break;
+    case 2: x = c; y = 0; dy = 1; break;
+    default: x = c; y = g.ny - 1; dy = -1; break;
+  }
+  if (solid_at(a.mask, g.mw, x, y)) return;
+  const size_t n0 = (size_t)y * g.pitch + x;
+  const size_t n1 = (size_t)wrapi(y + dy, g.ny) * g.pitch + wrapi(x + dx, g.nx);
+  const size_t n2 = (size_t)wrapi(y + 2 * dy, g.ny) * g.pitch + wrapi(x + 2 * dx, g.nx);
+  for (int cc = 0; cc < a.nc; cc++) {
+    if (o.style[cc] != OPEN_GRADIENT) continue;
+    S *f = (S *)a.f + (size_t)cc * 9 * g.plane;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      const size_t b = (size_t)q * g.plane;
+      const float v1 = Store<S>::ld(f, b + n1, a.inv_scale);
+      const float v2 = Store<S>::ld(f, b + n2, a.inv_scale);
+      Store<S>::st(f, b + n0, 2.0f * v1 - v2, a.scale);
+    }
+    if (a.fields) {
+      float *fl = a.fields + (size_t)cc * NFIELD * g.plane;
+      for (int q = 0; q < NFIELD; q++) {
+        const size_t b = (size_t)q * g.plane;
+        fl[b + n0] = 2.0f * fl[b + n1] - fl[b + n2];
+      }
+    }
+  }
+}
+
+template <class S>
+int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
+  if (sc) {
+    dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.ny + SC_TY - 1) / SC_TY);
+    if (nc == 1) k_fluid_sc<S, 1><<<grd, blk, 0, s>>>(a);
+    else k_fluid_sc<S, 2><<<grd, blk, 0, s>>>(a);
+  } else {
+    dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
+    if (nc == 1) {
+      if (me) k_fluid_local<S, 1, true><<<grd, blk, 0, s>>>(a);
+      else k_fluid_local<S, 1, false><<<grd, blk, 0, s>>>(a);
+    } else {
+      k_fluid_local<S, 2, true><<<grd, blk, 0, s>>>(a);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace
+
+int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s) {
+  switch (storage) {
+    case ST_FP16: return launch_fluid_t<__half>(nc, sc, mass_exact, a, s);
+    case ST_BF16: return launch_fluid_t<__nv_bfloat16>(nc, sc, mass_exact, a, s);
+    default: return launch_fluid_t<float>(nc, sc, mass_exact, a, s);
+  }
+}
+
+int launch_gradient(int storage, const GradArgs &a, cudaStream_t s) {
+  int maxlen = 0;
+  for (int k = 0; k < a.nopen; k++) maxlen = max(maxlen, a.op[k].a1 - a.op[k].a0 + 1);
+  if (!a.nopen || maxlen <= 0) return 0;
+  dim3 blk(128), grd((maxlen + 127) / 128, a.nopen);
+  switch (storage) {
+    case ST_FP16: k_gradient<__half><<<grd, blk, 0, s>>>(a); break;
+    case ST_BF16: k_gradient<__nv_bfloat16><<<grd, blk, 0, s>>>(a); break;
+    default: k_gradient<float><<<grd, blk, 0, s>>>(a); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace lbk

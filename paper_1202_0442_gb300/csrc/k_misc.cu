@@ -1,0 +1,338 @@
+// k_misc.cu -- thermo reduction and state conversion kernels.
+//
+// k_thermo_partial / k_thermo_final: the thermo command's sums (mass,
+//   momentum j + F/2, equilibrium mass, solute, deposit, removed mass,
+//   node counts) over the state at the end of an iteration, in FP64.  The
+//   first kernel gives every block a fixed, strided set of nodes and reduces
+//   it with warp shuffles and one shared-memory pass into a per-block slot
+//   of a scratch array; the second reduces the slots in a fixed tree.  The
+//   order of every addition is fixed by the launch shape, so the result is
+//   the same bits on every run.
+// Conversions between FP64 arrays in the caller's layout ([q][ny][nx],
+// dense) and the library's storage (deviations from w_i rho_ref, pitched,
+// FP32/FP16/BF16), equilibrium initialisation from rho and u, and field
+// export.
+#include "lbdev.cuh"
+
+namespace lbk {
+
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
+  const Geometry &g = a.g;
+  double acc[NTHERMO];
+#pragma unroll
+  for (int q = 0; q < NTHERMO; q++) acc[q] = 0.0;
+  const long long N = (long long)g.nx * g.ny;
+  const long long stride = (long long)gridDim.x * TB;
+  for (long long n = (long long)blockIdx.x * TB + threadIdx.x; n < N; n += stride) {
+    const int y = (int)(n / g.nx), x = (int)(n - (long long)y * g.nx);
+    const size_t self = (size_t)y * g.pitch + x;
+    if (solid_at(a.mask, g.mw, x, y)) {
+      acc[13] += 1.0;
+      if (a.b) acc[9] += a.b[self];
+    } else {
+      acc[14] += 1.0;
+      const float *f0 = a.fields;
+      acc[0] += (double)f0[self];
+      acc[2] += (double)f0[3 * g.plane + self];
+      acc[4] += (double)f0[g.plane + self];
+      acc[5] += (double)f0[2 * g.plane + self];
+      if (a.nc > 1) {
+        const float *f1 = a.fields + (size_t)NFIELD * g.plane;
+        acc[1] += (double)f1[self];
+        acc[3] += (double)f1[3 * g.plane + self];
+        acc[6] += (double)f1[g.plane + self];
+        acc[7] += (double)f1[2 * g.plane + self];
+      }
+      if (a.Cfield) acc[8] += (double)a.Cfield[self];
+    }
+    if (a.removed) {
+      acc[10] += a.removed[self];
+      if (a.nc > 1) acc[11] += a.removed[g.plane + self];
+      acc[12] += a.removed[(size_t)a.nc * g.plane + self];
+    }
+  }
+  __shared__ double sm[TB / 32][NTHERMO];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NTHERMO; q++) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) sm[w][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NTHERMO) {
+    double s = 0.0;
+    for (int k = 0; k < TB / 32; k++) s += sm[k][threadIdx.x];
+    a.partials[(size_t)blockIdx.x * NTHERMO + threadIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(TB) k_thermo_final(const double *partials, int nblocks,
+                                                     double *out) {
+  __shared__ double sm[TB / 32];
+  for (int q = 0; q < NTHERMO; q++) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += TB) v += partials[(size_t)k * NTHERMO + q];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int k = 0; k < TB / 32; k++) s += sm[k];
+      out[q] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double w9d(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+__device__ __forceinline__ bool node_of(int idx, const Geometry &g, int &x, int &y) {
+  if (idx >= g.nx * g.ny) return false;
+  y = idx / g.nx;
+  x = idx - y * g.nx;
+  return true;
+}
+
+template <class S>
+__global__ void k_import_pops(const double *src, S *dst, const uint32_t *mask, Geometry g,
+                              int q, float rho_ref, float scale, bool shift) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t nn = (size_t)g.nx * g.ny;
+  for (int i = 0; i < q; i++) {
+    double v = sol ? 0.0 : src[(size_t)i * nn + dense];
+    if (shift && !sol) v -= w9d(i) * (double)rho_ref;
+    Store<S>::st(dst, (size_t)i * g.plane + self, (float)v, scale);
+  }
+}
+
+template <class S>
+__global__ void k_export_pops(const S *src, double *dst, const uint32_t *mask, Geometry g,
+                              int q, float rho_ref, float inv_scale, bool shift) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t nn = (size_t)g.nx * g.ny;
+  for (int i = 0; i < q; i++) {
+    double v = 0.0;
+    if (!sol) {
+      v = (double)Store<S>::ld(src, (size_t)i * g.plane + self, inv_scale);
+      if (shift) v += w9d(i) * (double)rho_ref;
+    }
+    dst[(size_t)i * nn + dense] = v;
+  }
+}
+
+// f_eq(rho, u) of Eq. (2), evaluated in FP64, stored as deviations
+template <class S>
+__global__ void k_equilibrium(const double *rho, const double *ux, const double *uy, S *dst,
+                              const uint32_t *mask, Geometry g, float rho_ref, float scale) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const double r = rho[dense], u = ux ? ux[dense] : 0.0, v = uy ? uy[dense] : 0.0;
+  const double dr = r - (double)rho_ref, usq = u * u + v * v;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const double eu = EX(i) * u + EY(i) * v;
+    const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const double h = w * (dr + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+    Store<S>::st(dst, (size_t)i * g.plane + self, sol ? 0.0f : (float)h, scale);
+  }
+}
+
+// g_eq(C, u) of Eq. (3) (D2Q4) or w_i C (1 + 3 e.u) (D2Q9), FP32 storage
+__global__ void k_solute_equilibrium(const double *C, const double *ux, const double *uy,
+                                     float *dst, const uint32_t *mask, Geometry g, int q) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const double c = C[dense], u = ux ? ux[dense] : 0.0, v = uy ? uy[dense] : 0.0;
+  for (int i = 0; i < q; i++) {
+    double val;
+    if (q == 4) val = 0.25 * c * (1.0 + 2.0 * (EX4(i) * u + EY4(i) * v));
+    else {
+      const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+      val = w * c * (1.0 + 3.0 * (EX(i) * u + EY(i) * v));
+    }
+    dst[(size_t)i * g.plane + self] = sol ? 0.0f : (float)val;
+  }
+}
+
+__global__ void k_export_fields(const float *fields, const uint32_t *mask, Geometry g,
+                                float rho_ref, double *rho, double *px, double *py,
+                                double *req) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const double R = (double)rho_ref;
+  if (rho) rho[dense] = sol ? 0.0 : R + (double)fields[self];
+  if (px) px[dense] = sol ? 0.0 : (double)fields[g.plane + self];
+  if (py) py[dense] = sol ? 0.0 : (double)fields[2 * g.plane + self];
+  if (req) req[dense] = sol ? 0.0 : R + (double)fields[3 * g.plane + self];
+}
+
+__global__ void k_export_velocity(const float *fields, int nc, const uint32_t *mask, Geometry g,
+                                  float r0, float r1, float *rho, float *ux, float *uy) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  float rs = 0.f, pxs = 0.f, pys = 0.f;
+  for (int c = 0; c < nc; c++) {
+    const float *fl = fields + (size_t)c * NFIELD * g.plane;
+    rs += (c ? r1 : r0) + fl[self];
+    pxs += fl[g.plane + self];
+    pys += fl[2 * g.plane + self];
+  }
+  rho[dense] = sol ? 0.f : rs;
+  ux[dense] = sol ? 0.f : pxs / rs;
+  uy[dense] = sol ? 0.f : pys / rs;
+}
+
+__global__ void k_export_plane_f32(const float *src, const uint32_t *mask, Geometry g, double *dst) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  const bool sol = solid_at(mask, g.mw, x, y);
+  dst[(size_t)y * g.nx + x] = sol ? 0.0 : (double)src[(size_t)y * g.pitch + x];
+}
+
+__global__ void k_export_plane_f64(const double *src, Geometry g, double *dst) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  dst[(size_t)y * g.nx + x] = src[(size_t)y * g.pitch + x];
+}
+
+__global__ void k_import_plane_f64(const double *src, Geometry g, double *dst) {
+  int x, y;
+  if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
+  dst[(size_t)y * g.pitch + x] = src[(size_t)y * g.nx + x];
+}
+
+inline unsigned grid1(const Geometry &g) {
+  return (unsigned)(((long long)g.nx * g.ny + 255) / 256);
+}
+
+inline int ok() { return cudaGetLastError() == cudaSuccess ? 1 : -1; }
+
+}  // namespace
+
+int thermo_blocks(const Geometry &g) {
+  const long long n = (long long)g.nx * g.ny;
+  long long b = (n + TB - 1) / TB;
+  if (b > 4 * 152) b = 4 * 152;
+  return (int)(b < 1 ? 1 : b);
+}
+
+int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {
+  k_thermo_partial<<<nblocks, TB, 0, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  k_thermo_final<<<1, TB, 0, s>>>(a.partials, nblocks, a.out);
+  return cudaGetLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,
+                       Geometry g, int q, float rho_ref, float scale, bool shift,
+                       cudaStream_t s) {
+  switch (storage) {
+    case ST_FP16:
+      k_import_pops<__half><<<grid1(g), 256, 0, s>>>(src, (__half *)dst, mask, g, q, rho_ref, scale, shift);
+      break;
+    case ST_BF16:
+      k_import_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(src, (__nv_bfloat16 *)dst, mask, g, q, rho_ref, scale, shift);
+      break;
+    default:
+      k_import_pops<float><<<grid1(g), 256, 0, s>>>(src, (float *)dst, mask, g, q, rho_ref, scale, shift);
+  }
+  return ok();
+}
+
+int launch_export_pops(int storage, const void *src, double *dst, const uint32_t *mask,
+                       Geometry g, int q, float rho_ref, float inv_scale, bool shift,
+                       cudaStream_t s) {
+  switch (storage) {
+    case ST_FP16:
+      k_export_pops<__half><<<grid1(g), 256, 0, s>>>((const __half *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+      break;
+    case ST_BF16:
+      k_export_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>((const __nv_bfloat16 *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+      break;
+    default:
+      k_export_pops<float><<<grid1(g), 256, 0, s>>>((const float *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+  }
+  return ok();
+}
+
+int launch_equilibrium(int storage, const double *rho, const double *ux, const double *uy,
+                       void *dst, const uint32_t *mask, Geometry g, float rho_ref,
+                       float scale, cudaStream_t s) {
+  switch (storage) {
+    case ST_FP16:
+      k_equilibrium<__half><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__half *)dst, mask, g, rho_ref, scale);
+      break;
+    case ST_BF16:
+      k_equilibrium<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__nv_bfloat16 *)dst, mask, g, rho_ref, scale);
+      break;
+    default:
+      k_equilibrium<float><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (float *)dst, mask, g, rho_ref, scale);
+  }
+  return ok();
+}
+
+int launch_solute_equilibrium(int q, const double *C, const double *ux, const double *uy,
+                              float *dst, const uint32_t *mask, Geometry g, cudaStream_t s) {
+  k_solute_equilibrium<<<grid1(g), 256, 0, s>>>(C, ux, uy, dst, mask, g, q);
+  return ok();
+}
+
+int launch_export_fields(const float *fields, int comp, const uint32_t *mask, Geometry g,
+                         float rho_ref, double *rho, double *px, double *py, double *req,
+                         cudaStream_t s) {
+  k_export_fields<<<grid1(g), 256, 0, s>>>(fields + (size_t)comp * NFIELD * g.plane, mask, g,
+                                           rho_ref, rho, px, py, req);
+  return ok();
+}
+
+int launch_export_velocity(const float *fields, int nc, const uint32_t *mask, Geometry g,
+                           const float *rho_ref, float *rho, float *ux, float *uy,
+                           cudaStream_t s) {
+  k_export_velocity<<<grid1(g), 256, 0, s>>>(fields, nc, mask, g, rho_ref[0],
+                                             nc > 1 ? rho_ref[1] : 0.f, rho, ux, uy);
+  return ok();
+}
+
+int launch_export_plane_f32(const float *src, const uint32_t *mask, Geometry g, double *dst,
+                            cudaStream_t s) {
+  k_export_plane_f32<<<grid1(g), 256, 0, s>>>(src, mask, g, dst);
+  return ok();
+}
+
+int launch_export_plane_f64(const double *src, Geometry g, double *dst, cudaStream_t s) {
+  k_export_plane_f64<<<grid1(g), 256, 0, s>>>(src, g, dst);
+  return ok();
+}
+
+int launch_import_plane_f64(const double *src, Geometry g, double *dst, cudaStream_t s) {
+  k_import_plane_f64<<<grid1(g), 256, 0, s>>>(src, g, dst);
+  return ok();
+}
+
+}  // namespace lbk

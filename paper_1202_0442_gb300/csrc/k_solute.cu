@@ -1,0 +1,242 @@
+// k_solute.cu -- solute lattice, precipitation and surface growth.
+//
+// k_solute<Q>: one iteration of the solute populations g (solute command,
+//   Eq. (3); Q = 4 is the paper's D2Q4, Q = 9 the D2Q9 variant): pull
+//   streaming; at a solid source either bounce-back or the reactive rule of
+//   the surface_reaction command (App. C) on that link,
+//     C_i = (2 g_out + kr Cs)/(kr + 2 w_i),  g_in = -g_out + 2 w_i C_i
+//   (w_i = 1/4 on D2Q4 is the printed rule); the inlet_solute/outlet_solute
+//   rules (dirichlet: the crossing modes make C = Cbar, split by weight;
+//   adiabatic: crossing mode = opposite mode, App. B); BGK with
+//   g_eq(C, u), u the solvent velocity of Eq. (4) written by the fluid
+//   kernel in the same iteration; then precipitation dB = kr (C_w - Cs) if
+//   positive, taken in equal parts from the incoming modes, the share
+//   dB/|U| recorded for the solid neighbours.
+// k_gather_grow: every solid node adds its fluid neighbours' shares to its
+//   FP64 deposit b in a fixed order, and, if b > bmax, picks one fluid
+//   4-neighbour (SplitMix64 of seed ^ (t nx ny + node) mod the number of
+//   candidates, in the order +x, +y, -x, -y) and marks it; b := 0.
+// k_apply_flips: marked nodes become solid (mask bit), start with b0, and
+//   their fluid and solute mass is booked as removed.
+// The two growth kernels run back to back, so every decision sees the
+// state before any flip.
+#include "lbdev.cuh"
+
+namespace lbk {
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+template <int Q> __device__ __forceinline__ constexpr int sex(int i) { return Q == 4 ? EX4(i) : EX(i); }
+template <int Q> __device__ __forceinline__ constexpr int sey(int i) { return Q == 4 ? EY4(i) : EY(i); }
+template <int Q> __device__ __forceinline__ constexpr int sopp(int i) { return Q == 4 ? OPP4(i) : OPP(i); }
+template <int Q> __device__ __forceinline__ constexpr float sw(int i) { return Q == 4 ? 0.25f : W9(i); }
+
+// which opening (if any) holds node (x, y)
+__device__ __forceinline__ int opening_of(const OpenDesc *op, int nopen, int x, int y, int nx, int ny) {
+  if (!(x == 0 || y == 0 || x == nx - 1 || y == ny - 1)) return -1;
+  for (int k = 0; k < nopen; k++)
+    if (opening_has(op[k], x, y, nx, ny)) return k;
+  return -1;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geometry &g = p.g;
+  if (x >= g.nx || y >= g.ny) return;
+  if (solid_at(p.mask, g.mw, x, y)) return;
+  const size_t self = (size_t)y * g.pitch + x;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  const int wall = k >= 0 ? p.op[k].wall : -1;
+  float gt[Q];
+  float Cw = 0.f;
+  int nU = 0;
+  uint32_t U = 0, cross = 0;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    if (wall >= 0 && crosses_wall(wall, sex<Q>(i), sey<Q>(i))) {
+      cross |= 1u << i;
+      gt[i] = 0.f;
+      continue;
+    }
+    const int xs = wrapi(x - sex<Q>(i), g.nx), ys = wrapi(y - sey<Q>(i), g.ny);
+    if (solid_at(p.mask, g.mw, xs, ys)) {
+      const float gout = __ldg(p.gin + (size_t)sopp<Q>(i) * g.plane + self);
+      if (p.react) {
+        const float Ci = (2.0f * gout + p.kr * p.Cs) / (p.kr + 2.0f * sw<Q>(i));
+        gt[i] = -gout + 2.0f * sw<Q>(i) * Ci;
+        Cw += Ci;
+        nU++;
+        U |= 1u << i;
+      } else {
+        gt[i] = gout;
+      }
+    } else {
+      gt[i] = __ldg(p.gin + (size_t)i * g.plane + (size_t)ys * g.pitch + xs);
+    }
+  }
+  if (k >= 0) {
+    const OpenDesc &o = p.op[k];
+    if (o.sstyle == SOL_DIRICHLET) {
+      float Cp = 0.f, ws = 0.f;
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        if (cross & (1u << i)) ws += sw<Q>(i);
+        else Cp += gt[i];
+      }
+      const float r = (o.Cbar - Cp) / ws;
+#pragma unroll
+      for (int i = 0; i < Q; i++)
+        if (cross & (1u << i)) gt[i] = r * sw<Q>(i);
+    } else if (o.sstyle == SOL_ADIABATIC) {
+#pragma unroll
+      for (int i = 0; i < Q; i++)
+        if (cross & (1u << i)) gt[i] = gt[sopp<Q>(i)];
+    }
+  }
+  float C = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) C += gt[i];
+  const float ux = __ldg(p.u + self), uy = __ldg(p.u + g.plane + self);
+  const float om = p.omega;
+  float geq[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const float eu = (float)sex<Q>(i) * ux + (float)sey<Q>(i) * uy;
+    geq[i] = Q == 4 ? 0.25f * C * (1.0f + 2.0f * eu) : sw<Q>(i) * C * (1.0f + 3.0f * eu);
+  }
+  if (Q == 9) {
+    // the rounded D2Q9 weights would bias sum g_eq and sum g_eq e (see
+    // equilibrium_exact); restore C and C u
+    const float mx = geq[1] - geq[3] + geq[5] - geq[6] - geq[7] + geq[8];
+    const float my = geq[2] - geq[4] + geq[5] + geq[6] - geq[7] - geq[8];
+    const float cx = 0.5f * (C * ux - mx), cy = 0.5f * (C * uy - my);
+    geq[1] += cx;
+    geq[3] -= cx;
+    geq[2] += cy;
+    geq[4] -= cy;
+    float m = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) m += geq[i];
+    geq[0] = C - m;
+  }
+  float gs[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) gs[i] = gt[i] + om * (geq[i] - gt[i]);
+  if (p.react && nU) {
+    const float share_n = 1.0f / (float)nU;
+    const float dB = p.kr * (Cw * share_n - p.Cs);
+    float share = 0.f;
+    if (dB > 0.f) {
+      share = dB * share_n;
+#pragma unroll
+      for (int i = 0; i < Q; i++)
+        if (U & (1u << i)) gs[i] -= share;
+    }
+    p.db[self] = share;
+  }
+  float Cn = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    p.gout[(size_t)i * g.plane + self] = gs[i];
+    Cn += gs[i];
+  }
+  if (p.Cfield) p.Cfield[self] = Cn;
+}
+
+__global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geometry &g = a.g;
+  if (x >= g.nx || y >= g.ny) return;
+  if (!solid_at(a.mask, g.mw, x, y)) return;
+  const size_t self = (size_t)y * g.pitch + x;
+  double acc = 0.0;
+  const int q = a.q;
+  for (int i = (q == 4 ? 0 : 1); i < q; i++) {
+    const int ex = q == 4 ? EX4(i) : EX(i), ey = q == 4 ? EY4(i) : EY(i);
+    const int xf = wrapi(x + ex, g.nx), yf = wrapi(y + ey, g.ny);
+    if (solid_at(a.mask, g.mw, xf, yf)) continue;
+    const int k = a.nopen ? opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) : -1;
+    if (k >= 0 && crosses_wall(a.op[k].wall, ex, ey)) continue;
+    acc += (double)__ldg(a.db + (size_t)yf * g.pitch + xf);
+  }
+  double b = a.b[self] + acc;
+  if (b > a.bmax) {
+    long long cand[4];
+    int n = 0;
+    for (int d = 0; d < 4; d++) {
+      const int xf = wrapi(x + EX4(d), g.nx), yf = wrapi(y + EY4(d), g.ny);
+      if (solid_at(a.mask, g.mw, xf, yf)) continue;
+      if (a.nopen && opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) >= 0) continue;
+      cand[n++] = (long long)yf * g.pitch + xf;
+    }
+    if (n) {
+      const uint64_t node = (uint64_t)y * (uint64_t)g.nx + (uint64_t)x;
+      const uint64_t key = a.seed ^ ((uint64_t)a.t * (uint64_t)g.nx * (uint64_t)g.ny + node);
+      const int pick = (int)(splitmix64(key) % (uint64_t)n);
+      a.flip[cand[pick]] = 1;
+      b = 0.0;
+    }
+  }
+  a.b[self] = b;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geometry &g = a.g;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t self = (size_t)y * g.pitch + x;
+  if (!a.flip[self]) return;
+  a.flip[self] = 0;
+  atomicOr(a.mask + (size_t)y * g.mw + (x >> 5), 1u << (x & 31));
+  a.b[self] = a.b0;
+  for (int c = 0; c < a.nc; c++) {
+    const S *f = (const S *)a.f + (size_t)c * 9 * g.plane;
+    float d = 0.f;
+    for (int i = 0; i < 9; i++) d += Store<S>::ld(f, (size_t)i * g.plane + self, a.inv_scale);
+    a.removed[(size_t)c * g.plane + self] += (double)a.rho_ref[c] + (double)d;
+  }
+  if (a.gpop) {
+    float m = 0.f;
+    for (int i = 0; i < a.q; i++) m += a.gpop[(size_t)i * g.plane + self];
+    a.removed[(size_t)a.nc * g.plane + self] += (double)m;
+  }
+  atomicAdd(a.nflips, 1ULL);
+}
+
+}  // namespace
+
+int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  if (q == 4) k_solute<4><<<grd, blk, 0, s>>>(a);
+  else k_solute<9><<<grd, blk, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_growth(const GrowthArgs &a, cudaStream_t s) {
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  k_gather_grow<<<grd, blk, 0, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return 1;
+}
+
+int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s) {
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  switch (storage) {
+    case ST_FP16: k_apply_flips<__half><<<grd, blk, 0, s>>>(a); break;
+    case ST_BF16: k_apply_flips<__nv_bfloat16><<<grd, blk, 0, s>>>(a); break;
+    default: k_apply_flips<float><<<grd, blk, 0, s>>>(a); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace lbk

@@ -1,0 +1,1640 @@
+// lb2d_api.cu -- host side of the C ABI declared in include/lb2d.h.
+//
+// Holds the command state of one lattice (the paper's command set, Sec.
+// Commands), checks command order and arguments the way the paper's module
+// does (lattice before processors, boundary_style before obstacle,
+// position0 before momentum0/concentration0, ...), paints the initial
+// state on the host, moves it to the GPU at the first call that needs
+// device memory, and then drives each iteration as a fixed sequence of
+// kernel launches on the caller's stream:
+//   fluid (k_fluid_local or k_fluid_sc) -> gradient openings -> solute ->
+//   precipitation gather + growth decisions -> flips -> [thermo]
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb2d.h"
+#include "lbbatch.h"
+#include "lbint.h"
+
+using namespace lbk;
+
+namespace {
+
+struct Opening {
+  int wall = 0, a0 = 0, a1 = 0, kind = 0;
+  std::string label[2];
+  int style[2] = {OPEN_NONE, OPEN_NONE};
+  double v[2] = {0, 0}, rho[2] = {1, 1};
+  int sstyle = SOL_NONE;
+  double C = 0;
+};
+
+const double W9D[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                       1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+const int EXD[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int EYD[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const int EX4D[4] = {1, 0, -1, 0};
+const int EY4D[4] = {0, 1, 0, -1};
+
+int wall_of(const char *s) {
+  if (!s) return -1;
+  if (!strcmp(s, "xlo")) return 0;
+  if (!strcmp(s, "xhi")) return 1;
+  if (!strcmp(s, "ylo")) return 2;
+  if (!strcmp(s, "yhi")) return 3;
+  return -1;
+}
+
+size_t storage_bytes(int st) { return st == ST_FP32 ? 4 : 2; }
+
+}  // namespace
+
+struct lb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  uint64_t launches = 0;
+
+  // command state
+  bool have_lattice = false, have_style = false, have_region = false;
+  bool momentum_cmd = false, committed = false;
+  int nx = 0, ny = 0, nc = 1;
+  double tau[2] = {1, 1};
+  int qs = 0;
+  double taus = 1.0;
+  int storage = ST_FP32;
+  bool sr = false;
+  double rho_ref[2] = {1, 1};
+  float scale = 1.f, inv_scale = 1.f;
+  std::vector<uint8_t> solid, region;
+  std::vector<double> paint_f[2], paint_C;
+  bool painted_f[2] = {false, false}, painted_C = false;
+  bool state_set[2] = {false, false}, solute_set = false;
+  double fave[2][2] = {{0, 0}, {0, 0}}, acc[2][2] = {{0, 0}, {0, 0}};
+  bool ads[2] = {false, false};
+  double Gads[2] = {0, 0}, ads_psi0[2] = {0, 0}, ads_rho0[2] = {0, 0};
+  bool sc = false;
+  double G = 0, psi0 = 0, sc_rho0 = 0;
+  std::vector<Opening> open;
+  bool react = false;
+  double kr = 0, Cs = 0, b0 = 0, bmax = 0;
+  uint64_t seed = 0;
+  int nf = 0;
+
+  // device state
+  Geometry g{};
+  void *fbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *mask = nullptr;
+  float *fields = nullptr, *u = nullptr, *gbuf[2] = {nullptr, nullptr};
+  float *Cfield = nullptr, *db = nullptr;
+  double *b = nullptr, *removed = nullptr;
+  uint8_t *flip = nullptr;
+  unsigned long long *nflips = nullptr;
+  double *partials = nullptr, *tout = nullptr;
+  int tblocks = 0;
+  int64_t t = 0;
+  bool fields_valid = false;
+  lb_thermo_t thermo{};
+  bool thermo_valid = false;
+
+  int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char *what) {
+    return fail(LB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+};
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call);       \
+  } while (0)
+
+#define LAUNCH(expr)                                                              \
+  do {                                                                            \
+    int n_ = (expr);                                                              \
+    if (n_ < 0) return ctx->cuda_fail(cudaGetLastError(), "kernel launch");       \
+    ctx->launches += (uint64_t)n_;                                                \
+  } while (0)
+
+#define NEED_CTX()                              \
+  do {                                          \
+    if (!ctx) return LB_E_ARG;                  \
+  } while (0)
+
+namespace {
+
+int set_device(lb_ctx *ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaSetDevice");
+  return LB_OK;
+}
+
+bool fluid_ok(lb_ctx *ctx, int fluid) { return fluid >= 1 && fluid <= ctx->nc; }
+
+int find_label(lb_ctx *ctx, const char *label, int kind, int *comp) {
+  if (!label) return -1;
+  for (size_t k = 0; k < ctx->open.size(); k++) {
+    const Opening &o = ctx->open[k];
+    if (o.kind != kind) continue;
+    for (int c = 0; c < 2; c++)
+      if (!o.label[c].empty() && o.label[c] == label) {
+        *comp = c;
+        return (int)k;
+      }
+  }
+  return -1;
+}
+
+void node_of_open(const lb_ctx *ctx, const Opening &o, int a, int &x, int &y) {
+  switch (o.wall) {
+    case 0: x = 0; y = a; break;
+    case 1: x = ctx->nx - 1; y = a; break;
+    case 2: x = a; y = 0; break;
+    default: x = a; y = ctx->ny - 1; break;
+  }
+}
+
+int opening_at(const lb_ctx *ctx, int x, int y) {
+  for (size_t k = 0; k < ctx->open.size(); k++) {
+    const Opening &o = ctx->open[k];
+    for (int a = o.a0; a <= o.a1; a++) {
+      int ox, oy;
+      node_of_open(ctx, o, a, ox, oy);
+      if (ox == x && oy == y) return (int)k;
+    }
+  }
+  return -1;
+}
+
+bool crosses(int wall, int ex, int ey) {
+  return wall == 0 ? ex > 0 : wall == 1 ? ex < 0 : wall == 2 ? ey > 0 : ey < 0;
+}
+
+OpenDesc desc_of(const lb_ctx *ctx, const Opening &o) {
+  OpenDesc d{};
+  d.wall = o.wall;
+  d.a0 = o.a0;
+  d.a1 = o.a1;
+  d.kind = o.kind;
+  for (int c = 0; c < 2; c++) {
+    d.style[c] = c < ctx->nc ? o.style[c] : OPEN_NONE;
+    d.v[c] = (float)o.v[c];
+    d.rho[c] = (float)o.rho[c];
+    d.drho[c] = (float)(o.rho[c] - ctx->rho_ref[c]);
+  }
+  d.sstyle = o.sstyle;
+  d.Cbar = (float)o.C;
+  return d;
+}
+
+int paint_check(lb_ctx *ctx) {
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  if (ctx->committed)
+    return ctx->fail(LB_E_ORDER, "geometry and initial state are fixed after the first iteration");
+  return LB_OK;
+}
+
+template <class T>
+int dalloc(lb_ctx *ctx, T **p, size_t n) {
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) ? n * sizeof(T) : 1);
+  if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "cudaMalloc(%zu): %s", n * sizeof(T), cudaGetErrorString(e));
+  e = cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
+  return LB_OK;
+}
+
+#define TRY(x)               \
+  do {                       \
+    int r_ = (x);            \
+    if (r_ != LB_OK) return r_; \
+  } while (0)
+
+int validate(lb_ctx *ctx) {
+  const int nx = ctx->nx, ny = ctx->ny;
+  if (ctx->sc && !ctx->open.empty())
+    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built");
+  for (const Opening &o : ctx->open) {
+    for (int c = 0; c < ctx->nc; c++) {
+      if (o.style[c] == OPEN_NONE)
+        return ctx->fail(LB_E_ARG, "opening '%s' has no momentum style for fluid %d",
+                         o.label[0].c_str(), c + 1);
+      if ((o.style[c] == OPEN_UNIFORM || o.style[c] == OPEN_POISEUILLE) && !(std::fabs(o.v[c]) < 1.0))
+        return ctx->fail(LB_E_ARG, "opening velocity must satisfy |v| < 1");
+      if (o.style[c] == OPEN_DIRICHLET && !(o.rho[c] > 0.0))
+        return ctx->fail(LB_E_ARG, "dirichlet density must be positive");
+      if (o.style[c] == OPEN_GRADIENT) {
+        int dx = o.wall == 0 ? 1 : o.wall == 1 ? -1 : 0, dy = o.wall == 2 ? 1 : o.wall == 3 ? -1 : 0;
+        for (int a = o.a0; a <= o.a1; a++) {
+          int x, y;
+          node_of_open(ctx, o, a, x, y);
+          if (ctx->solid[(size_t)y * nx + x]) continue;
+          for (int k = 1; k <= 2; k++) {
+            int xx = ((x + k * dx) % nx + nx) % nx, yy = ((y + k * dy) % ny + ny) % ny;
+            if (ctx->solid[(size_t)yy * nx + xx])
+              return ctx->fail(LB_E_ARG, "gradient opening node (%d,%d) needs two fluid nodes inside", x, y);
+          }
+        }
+      }
+    }
+    if (ctx->qs && o.sstyle == SOL_NONE)
+      return ctx->fail(LB_E_ARG, "opening '%s' has no solute style", o.label[0].c_str());
+  }
+  if (ctx->react) {
+    // App. C rule 1: two opposite unknown modes cannot occur
+    const int q = ctx->qs;
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        if (ctx->solid[(size_t)y * nx + x]) continue;
+        int k = opening_at(ctx, x, y);
+        for (int i = (q == 4 ? 0 : 1); i < q; i++) {
+          int ex = q == 4 ? EX4D[i] : EXD[i], ey = q == 4 ? EY4D[i] : EYD[i];
+          if (k >= 0 && (crosses(ctx->open[k].wall, ex, ey) || crosses(ctx->open[k].wall, -ex, -ey)))
+            continue;
+          int x1 = ((x - ex) % nx + nx) % nx, y1 = ((y - ey) % ny + ny) % ny;
+          int x2 = ((x + ex) % nx + nx) % nx, y2 = ((y + ey) % ny + ny) % ny;
+          if (ctx->solid[(size_t)y1 * nx + x1] && ctx->solid[(size_t)y2 * nx + x2])
+            return ctx->fail(LB_E_ARG,
+                             "fluid node (%d,%d) has solid on two opposite sides: the surface "
+                             "reaction needs a gap of at least two fluid nodes", x, y);
+        }
+      }
+  }
+  return LB_OK;
+}
+
+// allocate the device state and upload geometry and the painted state
+int commit(lb_ctx *ctx) {
+  if (ctx->committed) return LB_OK;
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  TRY(validate(ctx));
+  TRY(set_device(ctx));
+  Geometry &g = ctx->g;
+  g.nx = ctx->nx;
+  g.ny = ctx->ny;
+  g.pitch = (ctx->nx + 31) / 32 * 32;
+  g.mw = g.pitch / 32;
+  g.plane = (size_t)g.ny * g.pitch;
+  const size_t sb = storage_bytes(ctx->storage);
+  const size_t fbytes = (size_t)ctx->nc * 9 * g.plane * sb;
+  for (int k = 0; k < 2; k++) TRY(dalloc(ctx, (uint8_t **)&ctx->fbuf[k], fbytes));
+  TRY(dalloc(ctx, &ctx->mask, (size_t)g.ny * g.mw));
+  TRY(dalloc(ctx, &ctx->fields, (size_t)ctx->nc * NFIELD * g.plane));
+  if (ctx->qs) {
+    TRY(dalloc(ctx, &ctx->u, 2 * g.plane));
+    for (int k = 0; k < 2; k++) TRY(dalloc(ctx, &ctx->gbuf[k], (size_t)ctx->qs * g.plane));
+    TRY(dalloc(ctx, &ctx->Cfield, g.plane));
+    TRY(dalloc(ctx, &ctx->db, g.plane));
+    TRY(dalloc(ctx, &ctx->flip, g.plane));
+  }
+  TRY(dalloc(ctx, &ctx->b, g.plane));
+  TRY(dalloc(ctx, &ctx->removed, (size_t)(ctx->nc + 1) * g.plane));
+  TRY(dalloc(ctx, &ctx->nflips, 1));
+  ctx->tblocks = thermo_blocks(g);
+  TRY(dalloc(ctx, &ctx->partials, (size_t)ctx->tblocks * NTHERMO));
+  TRY(dalloc(ctx, &ctx->tout, NTHERMO));
+
+  // bit-packed mask
+  std::vector<uint32_t> m((size_t)g.ny * g.mw, 0u);
+  for (int y = 0; y < g.ny; y++)
+    for (int x = 0; x < g.nx; x++)
+      if (ctx->solid[(size_t)y * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
+  CK(cudaMemcpyAsync(ctx->mask, m.data(), m.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+
+  // initial deposit b0 on every solid node (surface_reaction command)
+  if (ctx->react) {
+    std::vector<double> bh(g.plane, 0.0);
+    for (int y = 0; y < g.ny; y++)
+      for (int x = 0; x < g.nx; x++)
+        if (ctx->solid[(size_t)y * g.nx + x]) bh[(size_t)y * g.pitch + x] = ctx->b0;
+    CK(cudaMemcpyAsync(ctx->b, bh.data(), bh.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  ctx->committed = true;
+
+  // painted initial state (position0/momentum0/concentration0); opening
+  // nodes start at the equilibrium of their opening's density and velocity
+  const size_t nn = (size_t)g.nx * g.ny;
+  for (int c = 0; c < ctx->nc; c++) {
+    if (!ctx->painted_f[c]) continue;
+    std::vector<double> f = ctx->paint_f[c];
+    for (const Opening &o : ctx->open) {
+      for (int a = o.a0; a <= o.a1; a++) {
+        int x, y;
+        node_of_open(ctx, o, a, x, y);
+        double v = 0.0;
+        if (o.style[c] == OPEN_UNIFORM) v = o.v[c];
+        if (o.style[c] == OPEN_POISEUILLE) {
+          double L = o.a1 - o.a0 + 1, d = 0.5 * (2 * a - o.a1 - o.a0);
+          v = 4 * o.v[c] / (L * L) * (0.25 * L * L - d * d);
+        }
+        double sgn = o.kind == 0 ? 1.0 : -1.0;
+        double ux = 0, uy = 0;
+        if (o.wall == 0) ux = sgn * v;
+        if (o.wall == 1) ux = -sgn * v;
+        if (o.wall == 2) uy = sgn * v;
+        if (o.wall == 3) uy = -sgn * v;
+        double r = o.rho[c], usq = ux * ux + uy * uy;
+        for (int i = 0; i < 9; i++) {
+          double eu = EXD[i] * ux + EYD[i] * uy;
+          f[(size_t)i * nn + (size_t)y * g.nx + x] = W9D[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * usq);
+        }
+      }
+    }
+    for (size_t n = 0; n < nn; n++) {
+      if (ctx->solid[n]) continue;
+      double r = 0;
+      for (int i = 0; i < 9; i++) r += f[(size_t)i * nn + n];
+      if (!(r > 0))
+        return ctx->fail(LB_E_ARG, "fluid node (%zu,%zu) of fluid %d has no positive density: "
+                         "initialise it with position0/momentum0 or lb_set_equilibrium",
+                         n % g.nx, n / g.nx, c + 1);
+    }
+    int rc = lb_set_populations(ctx, c + 1, f.data());
+    if (rc != LB_OK) return rc;
+  }
+  if (ctx->qs && ctx->painted_C) {
+    int rc = lb_set_solute_equilibrium(ctx, ctx->paint_C.data(), nullptr, nullptr);
+    if (rc != LB_OK) return rc;
+  }
+  return LB_OK;
+}
+
+FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
+  FluidArgs a{};
+  a.g = ctx->g;
+  a.fin = ctx->fbuf[ctx->cur];
+  a.fout = ctx->fbuf[1 - ctx->cur];
+  a.mask = ctx->mask;
+  a.scale = ctx->scale;
+  a.inv_scale = ctx->inv_scale;
+  for (int c = 0; c < 2; c++) {
+    a.rho_ref[c] = (float)ctx->rho_ref[c];
+    a.tau[c] = (float)ctx->tau[c];
+    a.omega[c] = (float)(1.0 / ctx->tau[c]);
+    a.fx[c] = (float)ctx->fave[c][0];
+    a.fy[c] = (float)ctx->fave[c][1];
+    a.ax[c] = (float)ctx->acc[c][0];
+    a.ay[c] = (float)ctx->acc[c][1];
+    a.ads[c] = ctx->ads[c] ? 1 : 0;
+    a.Gads[c] = (float)ctx->Gads[c];
+    a.ads_psi0[c] = (float)ctx->ads_psi0[c];
+    a.ads_rho0[c] = (float)ctx->ads_rho0[c];
+  }
+  a.G = (float)ctx->G;
+  a.psi0 = (float)ctx->psi0;
+  a.sc_rho0 = (float)ctx->sc_rho0;
+  a.nopen = (int)ctx->open.size();
+  for (int k = 0; k < a.nopen; k++) a.op[k] = desc_of(ctx, ctx->open[k]);
+  a.fields = fields ? ctx->fields : nullptr;
+  a.uout = ctx->qs ? ctx->u : nullptr;
+  uint64_t z = (uint64_t)ctx->t * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;
+  a.step_seed = (uint32_t)(z >> 32);
+  if (ctx->sr) a.sr_seed = (uint32_t)z | 1u;
+  return a;
+}
+
+int run_thermo(lb_ctx *ctx) {
+  ThermoArgs ta{};
+  ta.g = ctx->g;
+  ta.mask = ctx->mask;
+  ta.fields = ctx->fields;
+  ta.nc = ctx->nc;
+  ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
+  ta.b = ctx->react ? ctx->b : nullptr;
+  ta.removed = ctx->removed;
+  ta.partials = ctx->partials;
+  ta.out = ctx->tout;
+  LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
+  double h[NTHERMO];
+  unsigned long long nfl = 0;
+  CK(cudaMemcpyAsync(h, ctx->tout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&nfl, ctx->nflips, sizeof nfl, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  lb_thermo_t &T = ctx->thermo;
+  memset(&T, 0, sizeof T);
+  T.step = ctx->t;
+  T.nsolid = (int64_t)llround(h[13]);
+  T.nfluid = (int64_t)llround(h[14]);
+  for (int c = 0; c < ctx->nc; c++) {
+    T.mass[c] = ctx->rho_ref[c] * (double)T.nfluid + h[0 + c];
+    T.mass_eq[c] = ctx->rho_ref[c] * (double)T.nfluid + h[2 + c];
+    T.mom_comp[c][0] = h[4 + 2 * c];
+    T.mom_comp[c][1] = h[5 + 2 * c];
+    T.mom[0] += h[4 + 2 * c];
+    T.mom[1] += h[5 + 2 * c];
+  }
+  T.solute = h[8];
+  T.bsum = h[9];
+  T.removed[0] = h[10];
+  T.removed[1] = h[11];
+  T.removed_solute = h[12];
+  T.flips = (int64_t)nfl;
+  ctx->thermo_valid = true;
+  for (int q = 0; q < NTHERMO; q++)
+    if (!std::isfinite(h[q])) return ctx->fail(LB_E_NAN, "thermo sum %d is not finite at step %lld", q, (long long)ctx->t);
+  return LB_OK;
+}
+
+int one_step(lb_ctx *ctx, bool fields) {
+  cudaStream_t s = ctx->stream;
+  ctx->t += 1;
+  const int nxt = 1 - ctx->cur;
+  FluidArgs fa = fluid_args(ctx, fields);
+  // two components and Shan-Chen runs keep |f - w rho_ref| large: their
+  // collision is the mass-exact one
+  const bool mass_exact = ctx->nc == 2 || ctx->sc;
+  LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
+  // gradient openings
+  GradArgs ga{};
+  int ng = 0;
+  for (const Opening &o : ctx->open) {
+    bool grad = false;
+    for (int c = 0; c < ctx->nc; c++) grad |= o.style[c] == OPEN_GRADIENT;
+    if (grad) ga.op[ng++] = desc_of(ctx, o);
+  }
+  if (ng) {
+    ga.g = ctx->g;
+    ga.f = ctx->fbuf[nxt];
+    ga.fields = fields ? ctx->fields : nullptr;
+    ga.mask = ctx->mask;
+    ga.nc = ctx->nc;
+    ga.nopen = ng;
+    ga.inv_scale = ctx->inv_scale;
+    ga.scale = ctx->scale;
+    LAUNCH(launch_gradient(ctx->storage, ga, s));
+  }
+  if (ctx->qs) {
+    SoluteArgs sa{};
+    sa.g = ctx->g;
+    sa.gin = ctx->gbuf[ctx->cur];
+    sa.gout = ctx->gbuf[nxt];
+    sa.mask = ctx->mask;
+    sa.u = ctx->u;
+    sa.omega = (float)(1.0 / ctx->taus);
+    sa.react = ctx->react ? 1 : 0;
+    sa.kr = (float)ctx->kr;
+    sa.Cs = (float)ctx->Cs;
+    sa.db = ctx->db;
+    sa.Cfield = fields ? ctx->Cfield : nullptr;
+    sa.nopen = (int)ctx->open.size();
+    for (int k = 0; k < sa.nopen; k++) sa.op[k] = desc_of(ctx, ctx->open[k]);
+    LAUNCH(launch_solute(ctx->qs, sa, s));
+    if (ctx->react) {
+      GrowthArgs ga2{};
+      ga2.g = ctx->g;
+      ga2.mask = ctx->mask;
+      ga2.db = ctx->db;
+      ga2.b = ctx->b;
+      ga2.flip = ctx->flip;
+      ga2.bmax = ctx->bmax;
+      ga2.b0 = ctx->b0;
+      ga2.seed = ctx->seed;
+      ga2.t = ctx->t;
+      ga2.q = ctx->qs;
+      ga2.nopen = sa.nopen;
+      for (int k = 0; k < sa.nopen; k++) ga2.op[k] = sa.op[k];
+      ga2.f = ctx->fbuf[nxt];
+      ga2.nc = ctx->nc;
+      ga2.rho_ref[0] = (float)ctx->rho_ref[0];
+      ga2.rho_ref[1] = (float)ctx->rho_ref[1];
+      ga2.inv_scale = ctx->inv_scale;
+      ga2.gpop = ctx->gbuf[nxt];
+      ga2.removed = ctx->removed;
+      ga2.nflips = ctx->nflips;
+      LAUNCH(launch_growth(ga2, s));
+      LAUNCH(launch_apply_flips(ctx->storage, ga2, s));
+    }
+  }
+  ctx->cur = nxt;
+  return LB_OK;
+}
+
+// FP64 staging buffer on the device for host <-> device conversions
+struct Stage {
+  double *p = nullptr;
+  ~Stage() {
+    if (p) cudaFree(p);
+  }
+};
+
+int stage_in(lb_ctx *ctx, Stage &st, const double *host, size_t n) {
+  cudaError_t e = cudaMalloc((void **)&st.p, n * sizeof(double));
+  if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "staging cudaMalloc: %s", cudaGetErrorString(e));
+  if (host) CK(cudaMemcpyAsync(st.p, host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  return LB_OK;
+}
+
+int stage_alloc(lb_ctx *ctx, Stage &st, size_t n) { return stage_in(ctx, st, nullptr, n); }
+
+}  // namespace
+
+// ======================================================================
+// C ABI
+// ======================================================================
+
+extern "C" {
+
+int lb_create(int device, void *cuda_stream, lb_ctx **out) {
+  if (!out) return LB_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return LB_E_CUDA;
+  lb_ctx *ctx = new (std::nothrow) lb_ctx();
+  if (!ctx) return LB_E_NOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  *out = ctx;
+  return LB_OK;
+}
+
+int lb_destroy(lb_ctx *ctx) {
+  NEED_CTX();
+  cudaSetDevice(ctx->device);
+  if (ctx->committed) cudaStreamSynchronize(ctx->stream);
+  void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields, ctx->u,
+                  ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,     ctx->b,
+                  ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete ctx;
+  return LB_OK;
+}
+
+const char *lb_last_error(const lb_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int lb_launch_count(const lb_ctx *ctx, uint64_t *out) {
+  if (!ctx || !out) return LB_E_ARG;
+  *out = ctx->launches;
+  return LB_OK;
+}
+
+int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau) {
+  NEED_CTX();
+  if (ctx->committed) return ctx->fail(LB_E_ORDER, "lattice is fixed after the first iteration");
+  if (!style || strcmp(style, "d2q9")) return ctx->fail(LB_E_UNSUPPORTED, "lattice style must be d2q9");
+  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31) / 16)
+    return ctx->fail(LB_E_ARG, "bad lattice size %d x %d", nx, ny);
+  if (!(tau > 0.5)) return ctx->fail(LB_E_ARG, "tau must exceed 1/2");
+  ctx->have_lattice = true;
+  ctx->nx = nx;
+  ctx->ny = ny;
+  ctx->tau[0] = ctx->tau[1] = tau;
+  const size_t nn = (size_t)nx * ny;
+  ctx->solid.assign(nn, 0);
+  ctx->region.assign(nn, 0);
+  for (int c = 0; c < 2; c++) {
+    ctx->paint_f[c].assign(9 * nn, 0.0);
+    ctx->painted_f[c] = false;
+  }
+  ctx->paint_C.assign(nn, 0.0);
+  return LB_OK;
+}
+
+int lb_processors(lb_ctx *ctx, int px, int py) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "processors must follow lattice");
+  if (ctx->momentum_cmd)
+    return ctx->fail(LB_E_ORDER, "processors must precede inlet_momentum/outlet_momentum and momentum0");
+  if (px < 1 || py < 1) return ctx->fail(LB_E_ARG, "processor grid must be positive");
+  return LB_OK;  // one GPU runs the whole lattice
+}
+
+int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1, double alpha2) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!(tau1 > 0.5) || !(tau2 > 0.5)) return ctx->fail(LB_E_ARG, "tau must exceed 1/2");
+  if (std::fabs(alpha1 - 4.0 / 9.0) > 1e-12 || std::fabs(alpha2 - 4.0 / 9.0) > 1e-12)
+    return ctx->fail(LB_E_UNSUPPORTED, "density-ratio alpha other than 4/9 is not built");
+  ctx->nc = 2;
+  ctx->tau[0] = tau1;
+  ctx->tau[1] = tau2;
+  return LB_OK;
+}
+
+int lb_solute(lb_ctx *ctx, double taus, int q) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (q != 4 && q != 9) return ctx->fail(LB_E_ARG, "solute lattice must be D2Q4 or D2Q9");
+  if (!(taus > 0.5)) return ctx->fail(LB_E_ARG, "taus must exceed 1/2");
+  ctx->qs = q;
+  ctx->taus = taus;
+  return LB_OK;
+}
+
+int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref, double h_max) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  const bool sr = (storage & LB_STOCHASTIC_ROUNDING) != 0;
+  storage &= ~LB_STOCHASTIC_ROUNDING;
+  if (storage != LB_FP32 && storage != LB_FP16 && storage != LB_BF16)
+    return ctx->fail(LB_E_ARG, "unknown storage %d", storage);
+  if (sr && storage == LB_FP32) return ctx->fail(LB_E_ARG, "stochastic rounding applies to 16-bit storage");
+  ctx->storage = storage;
+  ctx->sr = sr;
+  double rmax = 0;
+  for (int c = 0; c < 2; c++) {
+    // a value FP32 holds exactly, so that the kernels and the FP64 host
+    // conversions shift by the same reference density
+    ctx->rho_ref[c] = (double)(float)(rho_ref ? rho_ref[c < ctx->nc ? c : 0] : 1.0);
+    if (!(ctx->rho_ref[c] > 0)) return ctx->fail(LB_E_ARG, "rho_ref must be positive");
+    rmax = std::max(rmax, ctx->rho_ref[c]);
+  }
+  ctx->scale = ctx->inv_scale = 1.f;
+  if (storage == LB_FP16) {
+    double hm = h_max > 0 ? h_max : 0.25 * rmax;
+    int s = (int)std::floor(std::log2(16384.0 / hm));
+    s = std::max(-14, std::min(s, 60));
+    ctx->scale = (float)std::ldexp(1.0, s);
+    ctx->inv_scale = (float)std::ldexp(1.0, -s);
+  }
+  return LB_OK;
+}
+
+int lb_boundary_style(lb_ctx *ctx, const char *style) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!style) return ctx->fail(LB_E_ARG, "no style");
+  if (!strcmp(style, "slip") || !strcmp(style, "mixed") || !strcmp(style, "hybrid"))
+    return ctx->fail(LB_E_UNSUPPORTED, "boundary style '%s' is not built (noslip only)", style);
+  if (strcmp(style, "noslip")) return ctx->fail(LB_E_ARG, "unknown boundary style '%s'", style);
+  ctx->have_style = true;
+  return LB_OK;
+}
+
+static int obstacle_check(lb_ctx *ctx) {
+  TRY(paint_check(ctx));
+  if (!ctx->have_style) return ctx->fail(LB_E_ORDER, "obstacle must follow boundary_style");
+  return LB_OK;
+}
+
+int lb_obstacle_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1) {
+  NEED_CTX();
+  TRY(obstacle_check(ctx));
+  if (x0 > x1 || y0 > y1) return ctx->fail(LB_E_ARG, "rectangle bounds must be ordered");
+  for (int y = std::max(y0, 0); y <= std::min(y1, ctx->ny - 1); y++)
+    for (int x = std::max(x0, 0); x <= std::min(x1, ctx->nx - 1); x++) ctx->solid[(size_t)y * ctx->nx + x] = 1;
+  return LB_OK;
+}
+
+static void circle_paint(lb_ctx *ctx, std::vector<uint8_t> &m, int xc, int yc, int r, uint8_t v) {
+  const int nx = ctx->nx, ny = ctx->ny;
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      int dx = x - xc, dy = y - yc;
+      dx = ((dx + nx / 2) % nx + nx) % nx - nx / 2;
+      dy = ((dy + ny / 2) % ny + ny) % ny - ny / 2;
+      if ((long long)dx * dx + (long long)dy * dy <= (long long)r * r) m[(size_t)y * nx + x] = v;
+    }
+}
+
+int lb_obstacle_circle(lb_ctx *ctx, int xc, int yc, int r) {
+  NEED_CTX();
+  TRY(obstacle_check(ctx));
+  if (r < 0) return ctx->fail(LB_E_ARG, "negative radius");
+  circle_paint(ctx, ctx->solid, xc, yc, r, 1);
+  return LB_OK;
+}
+
+int lb_obstacle_mask(lb_ctx *ctx, const uint8_t *mask) {
+  NEED_CTX();
+  TRY(obstacle_check(ctx));
+  if (!mask) return ctx->fail(LB_E_ARG, "null mask");
+  for (size_t n = 0; n < ctx->solid.size(); n++)
+    if (mask[n]) ctx->solid[n] = 1;
+  return LB_OK;
+}
+
+static int add_opening(lb_ctx *ctx, int kind, const char *wall, int a0, int a1, const char *l1,
+                       const char *l2) {
+  TRY(paint_check(ctx));
+  int w = wall_of(wall);
+  if (w < 0) return ctx->fail(LB_E_ARG, "wall must be xlo, xhi, ylo or yhi");
+  int len = w <= 1 ? ctx->ny : ctx->nx;
+  if (a0 > a1 || a0 < 0 || a1 >= len) return ctx->fail(LB_E_ARG, "opening extent %d..%d outside the wall", a0, a1);
+  if (!l1 || !*l1) return ctx->fail(LB_E_ARG, "opening needs a label");
+  if (ctx->nc == 2 && (!l2 || !*l2)) return ctx->fail(LB_E_ARG, "two fluids need two labels");
+  if ((int)ctx->open.size() >= MAX_OPEN) return ctx->fail(LB_E_UNSUPPORTED, "at most %d openings", MAX_OPEN);
+  Opening o;
+  o.wall = w;
+  o.a0 = a0;
+  o.a1 = a1;
+  o.kind = kind;
+  o.label[0] = l1;
+  if (l2) o.label[1] = l2;
+  for (int a = a0; a <= a1; a++) {
+    int x, y;
+    node_of_open(ctx, o, a, x, y);
+    if (opening_at(ctx, x, y) >= 0) return ctx->fail(LB_E_ARG, "node (%d,%d) already belongs to an opening", x, y);
+  }
+  for (const Opening &p : ctx->open)
+    for (int c = 0; c < 2; c++)
+      for (int d = 0; d < 2; d++)
+        if (!p.label[c].empty() && !o.label[d].empty() && p.label[c] == o.label[d])
+          return ctx->fail(LB_E_ARG, "label '%s' already used", o.label[d].c_str());
+  ctx->open.push_back(o);
+  return LB_OK;
+}
+
+int lb_inlet(lb_ctx *ctx, const char *wall, int a0, int a1, const char *l1, const char *l2) {
+  NEED_CTX();
+  return add_opening(ctx, 0, wall, a0, a1, l1, l2);
+}
+
+int lb_outlet(lb_ctx *ctx, const char *wall, int a0, int a1, const char *l1, const char *l2) {
+  NEED_CTX();
+  return add_opening(ctx, 1, wall, a0, a1, l1, l2);
+}
+
+static int set_momentum(lb_ctx *ctx, int kind, const char *label, const char *style, double v, double rho) {
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  int comp = 0;
+  int k = find_label(ctx, label, kind, &comp);
+  if (k < 0) return ctx->fail(LB_E_ARG, "no %s labelled '%s'", kind ? "outlet" : "inlet", label ? label : "");
+  int st;
+  if (!style) return ctx->fail(LB_E_ARG, "no style");
+  if (!strcmp(style, "poiseuille")) st = OPEN_POISEUILLE;
+  else if (!strcmp(style, "uniform")) st = OPEN_UNIFORM;
+  else if (!strcmp(style, "dirichlet")) st = OPEN_DIRICHLET;
+  else if (!strcmp(style, "gradient")) st = OPEN_GRADIENT;
+  else return ctx->fail(LB_E_ARG, "unknown momentum style '%s'", style);
+  if (!(rho > 0)) return ctx->fail(LB_E_ARG, "opening density must be positive");
+  if ((st == OPEN_UNIFORM || st == OPEN_POISEUILLE) && !(std::fabs(v) < 1.0))
+    return ctx->fail(LB_E_ARG, "opening velocity must satisfy |v| < 1");
+  if (ctx->committed && st != ctx->open[k].style[comp] &&
+      (st == OPEN_GRADIENT || ctx->open[k].style[comp] == OPEN_GRADIENT))
+    return ctx->fail(LB_E_ORDER, "gradient style cannot be switched after the first iteration");
+  ctx->open[k].style[comp] = st;
+  ctx->open[k].v[comp] = v;
+  ctx->open[k].rho[comp] = rho;
+  ctx->momentum_cmd = true;
+  return LB_OK;
+}
+
+int lb_inlet_momentum(lb_ctx *ctx, const char *label, const char *style, double v, double rho) {
+  NEED_CTX();
+  return set_momentum(ctx, 0, label, style, v, rho);
+}
+
+int lb_outlet_momentum(lb_ctx *ctx, const char *label, const char *style, double v, double rho) {
+  NEED_CTX();
+  return set_momentum(ctx, 1, label, style, v, rho);
+}
+
+static int set_solute_open(lb_ctx *ctx, int kind, const char *label, const char *style, double C) {
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "inlet_solute/outlet_solute need the solute command");
+  int comp = 0;
+  int k = find_label(ctx, label, kind, &comp);
+  if (k < 0) return ctx->fail(LB_E_ARG, "no %s labelled '%s'", kind ? "outlet" : "inlet", label ? label : "");
+  if (!style) return ctx->fail(LB_E_ARG, "no style");
+  if (!strcmp(style, "dirichlet")) ctx->open[k].sstyle = SOL_DIRICHLET;
+  else if (!strcmp(style, "adiabatic")) ctx->open[k].sstyle = SOL_ADIABATIC;
+  else if (!strcmp(style, "flux")) return ctx->fail(LB_E_UNSUPPORTED, "solute flux style is not built");
+  else return ctx->fail(LB_E_ARG, "unknown solute style '%s'", style);
+  ctx->open[k].C = C;
+  return LB_OK;
+}
+
+int lb_inlet_solute(lb_ctx *ctx, const char *label, const char *style, double C) {
+  NEED_CTX();
+  return set_solute_open(ctx, 0, label, style, C);
+}
+
+int lb_outlet_solute(lb_ctx *ctx, const char *label, const char *style, double C) {
+  NEED_CTX();
+  return set_solute_open(ctx, 1, label, style, C);
+}
+
+int lb_surface_reaction(lb_ctx *ctx, double kr, double Cs, const char *style, double b0, double bmax,
+                        uint64_t seed) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "surface_reaction needs the solute command");
+  if (!style || strcmp(style, "growth")) return ctx->fail(LB_E_ARG, "surface_reaction style must be growth");
+  if (!(kr >= 0)) return ctx->fail(LB_E_ARG, "kr must be >= 0");
+  ctx->react = true;
+  ctx->kr = kr;
+  ctx->Cs = Cs;
+  ctx->b0 = b0;
+  ctx->bmax = bmax;
+  ctx->seed = seed;
+  return LB_OK;
+}
+
+int lb_position0_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (x0 > x1 || y0 > y1) return ctx->fail(LB_E_ARG, "rectangle bounds must be ordered");
+  std::fill(ctx->region.begin(), ctx->region.end(), 0);
+  for (int y = std::max(y0, 0); y <= std::min(y1, ctx->ny - 1); y++)
+    for (int x = std::max(x0, 0); x <= std::min(x1, ctx->nx - 1); x++) ctx->region[(size_t)y * ctx->nx + x] = 1;
+  ctx->have_region = true;
+  return LB_OK;
+}
+
+int lb_position0_circle(lb_ctx *ctx, int xc, int yc, int r) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (r < 0) return ctx->fail(LB_E_ARG, "negative radius");
+  std::fill(ctx->region.begin(), ctx->region.end(), 0);
+  circle_paint(ctx, ctx->region, xc, yc, r, 1);
+  ctx->have_region = true;
+  return LB_OK;
+}
+
+int lb_momentum0(lb_ctx *ctx, int mode, double value, int fluid) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!ctx->have_region) return ctx->fail(LB_E_ORDER, "momentum0 must follow position0");
+  if (mode < 0 || mode > 8 || !fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad mode or fluid");
+  const size_t nn = ctx->region.size();
+  std::vector<double> &f = ctx->paint_f[fluid - 1];
+  for (size_t n = 0; n < nn; n++)
+    if (ctx->region[n]) f[(size_t)mode * nn + n] += value;
+  ctx->painted_f[fluid - 1] = true;
+  ctx->momentum_cmd = true;
+  return LB_OK;
+}
+
+int lb_concentration0(lb_ctx *ctx, double value) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!ctx->have_region) return ctx->fail(LB_E_ORDER, "concentration0 must follow position0");
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "concentration0 needs the solute command");
+  for (size_t n = 0; n < ctx->region.size(); n++)
+    if (ctx->region[n]) ctx->paint_C[n] += value;
+  ctx->painted_C = true;
+  return LB_OK;
+}
+
+int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho, const double *ux, const double *uy) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  if (!fluid_ok(ctx, fluid) || !rho) return ctx->fail(LB_E_ARG, "bad fluid or null rho");
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  for (size_t n = 0; n < nn; n++)
+    if (!ctx->solid[n] && !(rho[n] > 0))
+      return ctx->fail(LB_E_ARG, "density must be positive on fluid node (%zu,%zu)", n % ctx->nx, n / ctx->nx);
+  ctx->painted_f[fluid - 1] = false;
+  TRY(commit(ctx));
+  Stage r, u, v;
+  TRY(stage_in(ctx, r, rho, nn));
+  if (ux) TRY(stage_in(ctx, u, ux, nn));
+  if (uy) TRY(stage_in(ctx, v, uy, nn));
+  const size_t sb = storage_bytes(ctx->storage);
+  void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
+  LAUNCH(launch_equilibrium(ctx->storage, r.p, u.p, v.p, dst, ctx->mask, ctx->g,
+                            (float)ctx->rho_ref[fluid - 1], ctx->scale, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->state_set[fluid - 1] = true;
+  return LB_OK;
+}
+
+int lb_set_solute_equilibrium(lb_ctx *ctx, const double *C, const double *ux, const double *uy) {
+  NEED_CTX();
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
+  if (!C) return ctx->fail(LB_E_ARG, "null C");
+  ctx->painted_C = false;
+  TRY(commit(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  Stage c, u, v;
+  TRY(stage_in(ctx, c, C, nn));
+  if (ux) TRY(stage_in(ctx, u, ux, nn));
+  if (uy) TRY(stage_in(ctx, v, uy, nn));
+  LAUNCH(launch_solute_equilibrium(ctx->qs, c.p, u.p, v.p, ctx->gbuf[ctx->cur], ctx->mask, ctx->g, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->solute_set = true;
+  return LB_OK;
+}
+
+int lb_set_populations(lb_ctx *ctx, int fluid, const double *f) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  if (!fluid_ok(ctx, fluid) || !f) return ctx->fail(LB_E_ARG, "bad fluid or null array");
+  if (!ctx->committed) ctx->painted_f[fluid - 1] = false;
+  TRY(commit(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  Stage st;
+  TRY(stage_in(ctx, st, f, 9 * nn));
+  const size_t sb = storage_bytes(ctx->storage);
+  void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
+  LAUNCH(launch_import_pops(ctx->storage, st.p, dst, ctx->mask, ctx->g, 9, (float)ctx->rho_ref[fluid - 1],
+                            ctx->scale, true, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->state_set[fluid - 1] = true;
+  return LB_OK;
+}
+
+int lb_set_solute_populations(lb_ctx *ctx, const double *g) {
+  NEED_CTX();
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
+  if (!g) return ctx->fail(LB_E_ARG, "null array");
+  ctx->painted_C = false;
+  TRY(commit(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  Stage st;
+  TRY(stage_in(ctx, st, g, (size_t)ctx->qs * nn));
+  LAUNCH(launch_import_pops(ST_FP32, st.p, ctx->gbuf[ctx->cur], ctx->mask, ctx->g, ctx->qs, 0.f, 1.f, false,
+                            ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->solute_set = true;
+  return LB_OK;
+}
+
+int lb_set_precipitate(lb_ctx *ctx, const double *b) {
+  NEED_CTX();
+  if (!b) return ctx->fail(LB_E_ARG, "null array");
+  TRY(commit(ctx));
+  Stage st;
+  TRY(stage_in(ctx, st, b, (size_t)ctx->nx * ctx->ny));
+  LAUNCH(launch_import_plane_f64(st.p, ctx->g, ctx->b, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LB_OK;
+}
+
+static int add_vec(lb_ctx *ctx, double (*dst)[2], int mode, double value, int fluid) {
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "force commands must follow lattice or fluids");
+  if (mode < 0 || mode > 8 || !fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad mode or fluid");
+  dst[fluid - 1][0] += value * EXD[mode];
+  dst[fluid - 1][1] += value * EYD[mode];
+  return LB_OK;
+}
+
+int lb_aveforce(lb_ctx *ctx, int mode, double value, int fluid) {
+  NEED_CTX();
+  return add_vec(ctx, ctx->fave, mode, value, fluid);
+}
+
+int lb_aveforce_xy(lb_ctx *ctx, double fx, double fy, int fluid) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "force commands must follow lattice or fluids");
+  if (!fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad fluid");
+  ctx->fave[fluid - 1][0] += fx;
+  ctx->fave[fluid - 1][1] += fy;
+  return LB_OK;
+}
+
+int lb_aveacceleration(lb_ctx *ctx, int mode, double value, int fluid) {
+  NEED_CTX();
+  return add_vec(ctx, ctx->acc, mode, value, fluid);
+}
+
+int lb_aveacceleration_xy(lb_ctx *ctx, double ax, double ay, int fluid) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "force commands must follow lattice or fluids");
+  if (!fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad fluid");
+  ctx->acc[fluid - 1][0] += ax;
+  ctx->acc[fluid - 1][1] += ay;
+  return LB_OK;
+}
+
+int lb_interforce(lb_ctx *ctx, double G, double psi0, double rho0) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "interforce must follow lattice or fluids");
+  if (ctx->nc == 1 && G != 0.0 && !(rho0 > 0 || rho0 < 0 || psi0 == 0))
+    return ctx->fail(LB_E_ARG, "interforce needs rho0 for one component");
+  ctx->sc = (G != 0.0);
+  ctx->G = G;
+  ctx->psi0 = psi0;
+  ctx->sc_rho0 = rho0;
+  if (ctx->committed && ctx->sc && !ctx->open.empty())
+    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built");
+  return LB_OK;
+}
+
+int lb_adhesiveforce(lb_ctx *ctx, double G, double psi0, double rho0, int fluid) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "adhesiveforce must follow lattice or fluids");
+  if (!fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad fluid");
+  ctx->ads[fluid - 1] = (G != 0.0);
+  ctx->Gads[fluid - 1] = G;
+  ctx->ads_psi0[fluid - 1] = psi0;
+  ctx->ads_rho0[fluid - 1] = rho0;
+  return LB_OK;
+}
+
+int lb_thermo(lb_ctx *ctx, int Nf) {
+  NEED_CTX();
+  if (Nf < 0) return ctx->fail(LB_E_ARG, "Nf must be >= 0");
+  ctx->nf = Nf;
+  return LB_OK;
+}
+
+int lb_iteration(lb_ctx *ctx, int Nt) {
+  NEED_CTX();
+  if (Nt < 0) return ctx->fail(LB_E_ARG, "Nt must be >= 0");
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  for (int c = 0; c < ctx->nc; c++)
+    if (!ctx->painted_f[c] && !ctx->state_set[c])
+      return ctx->fail(LB_E_ORDER, "fluid %d has no initial state (position0/momentum0 or lb_set_equilibrium)", c + 1);
+  if (ctx->qs && !ctx->painted_C && !ctx->solute_set)
+    return ctx->fail(LB_E_ORDER, "solute has no initial state (concentration0 or lb_set_solute_equilibrium)");
+  TRY(commit(ctx));
+  TRY(set_device(ctx));
+  for (int k = 1; k <= Nt; k++) {
+    const bool thermo = ctx->nf > 0 ? ((ctx->t + 1) % ctx->nf == 0) : (k == Nt);
+    TRY(one_step(ctx, thermo));
+    if (thermo) {
+      ctx->fields_valid = true;
+      TRY(run_thermo(ctx));
+    }
+  }
+  return LB_OK;
+}
+
+int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out) {
+  NEED_CTX();
+  if (!out) return ctx->fail(LB_E_ARG, "null output");
+  if (!ctx->thermo_valid) return ctx->fail(LB_E_ORDER, "no thermo record yet: call lb_iteration first");
+  *out = ctx->thermo;
+  return LB_OK;
+}
+
+int lb_get_fields(lb_ctx *ctx, int fluid, double *rho, double *px, double *py, double *rho_eq) {
+  NEED_CTX();
+  if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+  if (!fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad fluid");
+  TRY(set_device(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  Stage st;
+  TRY(stage_alloc(ctx, st, 4 * nn));
+  LAUNCH(launch_export_fields(ctx->fields, fluid - 1, ctx->mask, ctx->g, (float)ctx->rho_ref[fluid - 1], st.p,
+                              st.p + nn, st.p + 2 * nn, st.p + 3 * nn, ctx->stream));
+  double *outs[4] = {rho, px, py, rho_eq};
+  for (int k = 0; k < 4; k++)
+    if (outs[k]) CK(cudaMemcpyAsync(outs[k], st.p + k * nn, nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LB_OK;
+}
+
+int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy) {
+  NEED_CTX();
+  if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+  if (!rho || !ux || !uy) return ctx->fail(LB_E_ARG, "null output");
+  TRY(set_device(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  float *st = nullptr;
+  CK(cudaMallocAsync((void **)&st, 3 * nn * sizeof(float), ctx->stream));
+  float rr[2] = {(float)ctx->rho_ref[0], (float)ctx->rho_ref[1]};
+  int n = launch_export_velocity(ctx->fields, ctx->nc, ctx->mask, ctx->g, rr, st, st + nn, st + 2 * nn,
+                                 ctx->stream);
+  cudaError_t e = n < 0 ? cudaGetLastError() : cudaSuccess;
+  if (n > 0) ctx->launches += n;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rho, st, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ux, st + nn, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(uy, st + 2 * nn, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(st, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "velocity export");
+  return LB_OK;
+}
+
+int lb_get_populations(lb_ctx *ctx, int fluid, double *f) {
+  NEED_CTX();
+  if (!ctx->committed) return ctx->fail(LB_E_ORDER, "no device state yet");
+  if (!fluid_ok(ctx, fluid) || !f) return ctx->fail(LB_E_ARG, "bad fluid or null array");
+  TRY(set_device(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  Stage st;
+  TRY(stage_alloc(ctx, st, 9 * nn));
+  const size_t sb = storage_bytes(ctx->storage);
+  const void *src = (const uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
+  LAUNCH(launch_export_pops(ctx->storage, src, st.p, ctx->mask, ctx->g, 9, (float)ctx->rho_ref[fluid - 1],
+                            ctx->inv_scale, true, ctx->stream));
+  CK(cudaMemcpyAsync(f, st.p, 9 * nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LB_OK;
+}
+
+int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b) {
+  NEED_CTX();
+  if (!ctx->committed) return ctx->fail(LB_E_ORDER, "no device state yet");
+  TRY(set_device(ctx));
+  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  if (g) {
+    if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
+    Stage st;
+    TRY(stage_alloc(ctx, st, (size_t)ctx->qs * nn));
+    LAUNCH(launch_export_pops(ST_FP32, ctx->gbuf[ctx->cur], st.p, ctx->mask, ctx->g, ctx->qs, 0.f, 1.f, false,
+                              ctx->stream));
+    CK(cudaMemcpyAsync(g, st.p, (size_t)ctx->qs * nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (C) {
+    if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
+    if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+    Stage st;
+    TRY(stage_alloc(ctx, st, nn));
+    LAUNCH(launch_export_plane_f32(ctx->Cfield, ctx->mask, ctx->g, st.p, ctx->stream));
+    CK(cudaMemcpyAsync(C, st.p, nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (b) {
+    Stage st;
+    TRY(stage_alloc(ctx, st, nn));
+    LAUNCH(launch_export_plane_f64(ctx->b, ctx->g, st.p, ctx->stream));
+    CK(cudaMemcpyAsync(b, st.p, nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LB_OK;
+}
+
+int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
+  NEED_CTX();
+  if (!mask) return ctx->fail(LB_E_ARG, "null output");
+  if (!ctx->committed) {
+    memcpy(mask, ctx->solid.data(), ctx->solid.size());
+    return LB_OK;
+  }
+  TRY(set_device(ctx));
+  std::vector<uint32_t> m((size_t)ctx->g.ny * ctx->g.mw);
+  CK(cudaMemcpyAsync(m.data(), ctx->mask, m.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int y = 0; y < ctx->ny; y++)
+    for (int x = 0; x < ctx->nx; x++)
+      mask[(size_t)y * ctx->nx + x] = (m[(size_t)y * ctx->g.mw + (x >> 5)] >> (x & 31)) & 1u;
+  return LB_OK;
+}
+
+// snapshot layout: header, populations (current buffer), mask, solute
+// populations, precipitate, removed tallies, flip count
+struct SnapHeader {
+  uint64_t magic, nx, ny, nc, qs, storage, t;
+};
+static const uint64_t SNAP_MAGIC = 0x4c42324453543031ULL;  // "LB2DST01"
+
+static void snap_parts(lb_ctx *ctx, std::vector<std::pair<void *, size_t>> &parts) {
+  const Geometry &g = ctx->g;
+  parts.clear();
+  parts.push_back({ctx->fbuf[ctx->cur], (size_t)ctx->nc * 9 * g.plane * storage_bytes(ctx->storage)});
+  parts.push_back({ctx->mask, (size_t)g.ny * g.mw * 4});
+  if (ctx->qs) parts.push_back({ctx->gbuf[ctx->cur], (size_t)ctx->qs * g.plane * 4});
+  parts.push_back({ctx->b, g.plane * 8});
+  parts.push_back({ctx->removed, (size_t)(ctx->nc + 1) * g.plane * 8});
+  parts.push_back({ctx->nflips, 8});
+}
+
+int lb_state_size(lb_ctx *ctx, size_t *bytes) {
+  NEED_CTX();
+  if (!bytes) return ctx->fail(LB_E_ARG, "null output");
+  TRY(commit(ctx));
+  std::vector<std::pair<void *, size_t>> parts;
+  snap_parts(ctx, parts);
+  size_t n = sizeof(SnapHeader);
+  for (auto &p : parts) n += p.second;
+  *bytes = n;
+  return LB_OK;
+}
+
+int lb_save_state(lb_ctx *ctx, void *host, size_t bytes) {
+  NEED_CTX();
+  size_t need = 0;
+  TRY(lb_state_size(ctx, &need));
+  if (!host || bytes != need) return ctx->fail(LB_E_ARG, "snapshot buffer must be %zu bytes", need);
+  TRY(set_device(ctx));
+  SnapHeader h{SNAP_MAGIC, (uint64_t)ctx->nx, (uint64_t)ctx->ny, (uint64_t)ctx->nc, (uint64_t)ctx->qs,
+               (uint64_t)ctx->storage, (uint64_t)ctx->t};
+  memcpy(host, &h, sizeof h);
+  std::vector<std::pair<void *, size_t>> parts;
+  snap_parts(ctx, parts);
+  size_t off = sizeof h;
+  for (auto &p : parts) {
+    CK(cudaMemcpyAsync((uint8_t *)host + off, p.first, p.second, cudaMemcpyDeviceToHost, ctx->stream));
+    off += p.second;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LB_OK;
+}
+
+int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
+  NEED_CTX();
+  size_t need = 0;
+  TRY(lb_state_size(ctx, &need));
+  if (!host || bytes != need) return ctx->fail(LB_E_ARG, "snapshot must be %zu bytes", need);
+  SnapHeader h;
+  memcpy(&h, host, sizeof h);
+  if (h.magic != SNAP_MAGIC || h.nx != (uint64_t)ctx->nx || h.ny != (uint64_t)ctx->ny ||
+      h.nc != (uint64_t)ctx->nc || h.qs != (uint64_t)ctx->qs || h.storage != (uint64_t)ctx->storage)
+    return ctx->fail(LB_E_ARG, "snapshot does not match this lattice");
+  TRY(set_device(ctx));
+  std::vector<std::pair<void *, size_t>> parts;
+  snap_parts(ctx, parts);
+  size_t off = sizeof h;
+  for (auto &p : parts) {
+    CK(cudaMemcpyAsync(p.first, (const uint8_t *)host + off, p.second, cudaMemcpyHostToDevice, ctx->stream));
+    off += p.second;
+  }
+  ctx->t = (int64_t)h.t;
+  for (int c = 0; c < ctx->nc; c++) ctx->state_set[c] = true;
+  if (ctx->qs) ctx->solute_set = true;
+  return LB_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// batched lattices
+// ======================================================================
+
+struct lb_batch {
+  std::vector<lb_ctx *> ctxs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int storage = ST_FP32;
+  std::string err;
+  uint64_t launches = 0;
+  BatchLat *d_lat = nullptr;
+  int4 *d_tiles = nullptr;
+  unsigned int *d_counters = nullptr;
+  std::vector<BatchLat> h_lat;
+  int shape = 0, dynamic = 1, order = 1;
+  int ntiles = 0, grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = 0;
+  // graphs are captured and replayed on a private stream (the caller's may
+  // be the legacy default stream, which cannot be captured), fenced to the
+  // caller's stream by events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+};
+
+namespace {
+
+int batch_cuda(lb_batch *b, cudaError_t e, const char *what) {
+  return b->fail(LB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define BCK(call)                                            \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return batch_cuda(b, e_, #call);  \
+  } while (0)
+
+void drop_graph(lb_batch *b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->graph_steps = 0;
+}
+
+// tile list for the current shape and order: 0 = lattice by lattice,
+// 1 = round robin over lattices, 2 = largest lattices first
+int build_tiles(lb_batch *b) {
+  const int TX = batch_shape_tx(b->shape), TY = batch_shape_ty(b->shape);
+  std::vector<std::vector<int4>> per(b->ctxs.size());
+  for (size_t l = 0; l < b->ctxs.size(); l++) {
+    const lb_ctx *c = b->ctxs[l];
+    for (int y0 = 0; y0 < c->ny; y0 += TY)
+      for (int x0 = 0; x0 < c->nx; x0 += TX) per[l].push_back(make_int4((int)l, x0, y0, 0));
+  }
+  std::vector<int> idx(b->ctxs.size());
+  for (size_t l = 0; l < idx.size(); l++) idx[l] = (int)l;
+  if (b->order == 2)
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return per[a].size() > per[c].size(); });
+  std::vector<int4> tiles;
+  if (b->order == 1) {
+    size_t maxn = 0;
+    for (auto &v : per) maxn = std::max(maxn, v.size());
+    for (size_t k = 0; k < maxn; k++)
+      for (int l : idx)
+        if (k < per[l].size()) tiles.push_back(per[l][k]);
+  } else {
+    for (int l : idx) tiles.insert(tiles.end(), per[l].begin(), per[l].end());
+  }
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  b->d_tiles = nullptr;
+  BCK(cudaMalloc((void **)&b->d_tiles, tiles.size() * sizeof(int4)));
+  BCK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+  b->ntiles = (int)tiles.size();
+  int sms = 0;
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  int occ = batch_occupancy(b->storage, b->shape);
+  b->grid = std::max(1, std::min(b->ntiles, sms * std::max(occ, 1)));
+  drop_graph(b);
+  return LB_OK;
+}
+
+// refresh the per-lattice descriptors (a context may have been advanced on
+// its own since the last batch call)
+int sync_descs(lb_batch *b) {
+  bool dirty = b->h_lat.empty();
+  if (dirty) b->h_lat.resize(b->ctxs.size());
+  for (size_t l = 0; l < b->ctxs.size(); l++) {
+    lb_ctx *c = b->ctxs[l];
+    BatchLat L{};
+    L.nx = c->g.nx;
+    L.ny = c->g.ny;
+    L.pitch = c->g.pitch;
+    L.mw = c->g.mw;
+    L.plane = c->g.plane;
+    L.buf[0] = c->fbuf[0];
+    L.buf[1] = c->fbuf[1];
+    L.cur = c->cur;
+    L.mask = c->mask;
+    L.rho_ref = (float)c->rho_ref[0];
+    L.scale = c->scale;
+    L.inv_scale = c->inv_scale;
+    L.tau = (float)c->tau[0];
+    L.omega = (float)(1.0 / c->tau[0]);
+    L.fx = (float)c->fave[0][0];
+    L.fy = (float)c->fave[0][1];
+    L.ax = (float)c->acc[0][0];
+    L.ay = (float)c->acc[0][1];
+    if (memcmp(&L, &b->h_lat[l], sizeof L)) {
+      b->h_lat[l] = L;
+      dirty = true;
+    }
+  }
+  if (dirty)
+    BCK(cudaMemcpyAsync(b->d_lat, b->h_lat.data(), b->h_lat.size() * sizeof(BatchLat), cudaMemcpyHostToDevice,
+                        b->stream));
+  return LB_OK;
+}
+
+BatchLaunch launch_desc(lb_batch *b) {
+  BatchLaunch L{};
+  L.lat = b->d_lat;
+  L.tiles = b->d_tiles;
+  L.ntiles = b->ntiles;
+  L.grid = b->grid;
+  L.shape = b->shape;
+  L.dynamic = b->dynamic;
+  L.counters = b->d_counters;
+  return L;
+}
+
+int batch_direct(lb_batch *b, int parity0, int n) {
+  BatchLaunch L = launch_desc(b);
+  for (int k = 0; k < n; k++) {
+    if (launch_batch(b->storage, L, (parity0 + k) & 1, b->stream) < 0)
+      return batch_cuda(b, cudaGetLastError(), "batch launch");
+    b->launches++;
+  }
+  return LB_OK;
+}
+
+void batch_advance(lb_batch *b, int n) {
+  for (lb_ctx *c : b->ctxs) {
+    c->cur = (c->cur + n) & 1;
+    c->t += n;
+    c->fields_valid = false;
+  }
+  b->h_lat.clear();
+}
+
+constexpr int GRAPH_STEPS = 20;  // kernels per captured graph (even)
+
+int ensure_graph(lb_batch *b) {
+  if (b->gexec) return LB_OK;
+  if (!b->gstream) {
+    BCK(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
+    BCK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    BCK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  }
+  cudaGraph_t graph = nullptr;
+  BCK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+  BatchLaunch L = launch_desc(b);
+  int bad = 0;
+  for (int k = 0; k < GRAPH_STEPS; k++)
+    if (launch_batch(b->storage, L, k & 1, b->gstream) < 0) bad = 1;
+  cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
+  if (bad || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return batch_cuda(b, e != cudaSuccess ? e : cudaGetLastError(), "graph capture");
+  }
+  e = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return batch_cuda(b, e, "cudaGraphInstantiate");
+  b->graph_steps = GRAPH_STEPS;
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out) {
+  if (!out || !ctxs || n < 1) return LB_E_ARG;
+  *out = nullptr;
+  lb_batch *b = new (std::nothrow) lb_batch();
+  if (!b) return LB_E_NOMEM;
+  for (int k = 0; k < n; k++) {
+    lb_ctx *c = ctxs[k];
+    int rc = LB_OK;
+    if (!c) rc = LB_E_ARG;
+    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0])
+      rc = c->fail(LB_E_UNSUPPORTED, "batched lattices are periodic single-component lattices with body forces");
+    else {
+      for (int s = 0; s < c->nc && rc == LB_OK; s++)
+        if (!c->painted_f[s] && !c->state_set[s]) rc = c->fail(LB_E_ORDER, "lattice %d has no initial state", k);
+      if (rc == LB_OK) rc = commit(c);
+    }
+    if (rc == LB_OK && k > 0 && (c->device != ctxs[0]->device || c->stream != ctxs[0]->stream ||
+                                 c->storage != ctxs[0]->storage))
+      rc = LB_E_ARG;
+    if (rc != LB_OK) {
+      delete b;
+      return rc;
+    }
+    b->ctxs.push_back(c);
+  }
+  b->device = ctxs[0]->device;
+  b->stream = ctxs[0]->stream;
+  b->storage = ctxs[0]->storage;
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc((void **)&b->d_lat, n * sizeof(BatchLat)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_counters, 2 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess) {
+    lb_batch_destroy(b);
+    return LB_E_CUDA;
+  }
+  if (build_tiles(b) != LB_OK) {
+    lb_batch_destroy(b);
+    return LB_E_CUDA;
+  }
+  *out = b;
+  return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch *b) {
+  if (!b) return LB_E_ARG;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  if (b->gstream) cudaStreamSynchronize(b->gstream);
+  if (b->gstream) cudaStreamDestroy(b->gstream);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->d_lat) cudaFree(b->d_lat);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_counters) cudaFree(b->d_counters);
+  delete b;
+  return LB_OK;
+}
+
+const char *lb_batch_last_error(const lb_batch *b) { return b ? b->err.c_str() : "no batch"; }
+
+int lb_batch_launch_count(const lb_batch *b, uint64_t *out) {
+  if (!b || !out) return LB_E_ARG;
+  *out = b->launches;
+  return LB_OK;
+}
+
+int lb_batch_iteration(lb_batch *b, int Nt, int use_graph) {
+  if (!b) return LB_E_ARG;
+  if (Nt < 0) return b->fail(LB_E_ARG, "Nt must be >= 0");
+  BCK(cudaSetDevice(b->device));
+  int rc = sync_descs(b);
+  if (rc != LB_OK) return rc;
+  int done = 0;
+  if (use_graph) {
+    rc = ensure_graph(b);
+    if (rc != LB_OK) return rc;
+    if (Nt >= b->graph_steps) {
+      BCK(cudaEventRecord(b->ev_in, b->stream));
+      BCK(cudaStreamWaitEvent(b->gstream, b->ev_in, 0));
+      while (Nt - done >= b->graph_steps) {
+        BCK(cudaGraphLaunch(b->gexec, b->gstream));
+        b->launches += (uint64_t)b->graph_steps;
+        done += b->graph_steps;
+      }
+      BCK(cudaEventRecord(b->ev_out, b->gstream));
+      BCK(cudaStreamWaitEvent(b->stream, b->ev_out, 0));
+    }
+  }
+  rc = batch_direct(b, done & 1, Nt - done);
+  if (rc != LB_OK) return rc;
+  batch_advance(b, Nt);
+  return LB_OK;
+}
+
+int lb_batch_autotune(lb_batch *b, const char *cache_json) {
+  if (!b) return LB_E_ARG;
+  BCK(cudaSetDevice(b->device));
+  // cache key: device name, storage and the lattice shapes
+  cudaDeviceProp prop;
+  BCK(cudaGetDeviceProperties(&prop, b->device));
+  uint64_t hsh = 1469598103934665603ULL;
+  for (lb_ctx *c : b->ctxs) {
+    hsh = (hsh ^ (uint64_t)c->nx) * 1099511628211ULL;
+    hsh = (hsh ^ (uint64_t)c->ny) * 1099511628211ULL;
+  }
+  char key[512];
+  snprintf(key, sizeof key, "%s|st%d|n%zu|%016llx", prop.name, b->storage, b->ctxs.size(), (unsigned long long)hsh);
+  std::string cache;
+  if (cache_json) {
+    FILE *fp = fopen(cache_json, "rb");
+    if (fp) {
+      char buf[4096];
+      size_t n;
+      while ((n = fread(buf, 1, sizeof buf, fp)) > 0) cache.append(buf, n);
+      fclose(fp);
+    }
+    size_t p = cache.find(std::string("\"") + key + "\"");
+    if (p != std::string::npos) {
+      int sh, dy, od;
+      const char *q = strchr(cache.c_str() + p, '{');
+      if (q && sscanf(q, "{\"shape\": %d, \"dynamic\": %d, \"order\": %d", &sh, &dy, &od) == 3 && sh >= 0 &&
+          sh < BATCH_SHAPES) {
+        b->shape = sh;
+        b->dynamic = dy;
+        b->order = od;
+        return build_tiles(b);
+      }
+    }
+  }
+  // keep the lattices' states: time on them, then put the states back
+  int rc = sync_descs(b);
+  if (rc != LB_OK) return rc;
+  std::vector<void *> saved(b->ctxs.size(), nullptr);
+  std::vector<size_t> sizes(b->ctxs.size());
+  for (size_t l = 0; l < b->ctxs.size(); l++) {
+    lb_ctx *c = b->ctxs[l];
+    sizes[l] = (size_t)9 * c->g.plane * storage_bytes(c->storage);
+    BCK(cudaMalloc(&saved[l], sizes[l]));
+    BCK(cudaMemcpyAsync(saved[l], c->fbuf[c->cur], sizes[l], cudaMemcpyDeviceToDevice, b->stream));
+  }
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bs = 0, bd = 1, bo = 1;
+  const int reps = 6;
+  for (int sh = 0; sh < BATCH_SHAPES; sh++)
+    for (int dy = 0; dy < 2; dy++)
+      for (int od = 0; od < 3; od++) {
+        if (dy && od == 0) continue;  // dynamic hand-out makes lattice order moot
+        b->shape = sh;
+        b->dynamic = dy;
+        b->order = od;
+        rc = build_tiles(b);
+        if (rc != LB_OK) return rc;
+        rc = batch_direct(b, 0, 2);
+        if (rc != LB_OK) return rc;
+        BCK(cudaEventRecord(e0, b->stream));
+        rc = batch_direct(b, 0, reps);
+        if (rc != LB_OK) return rc;
+        BCK(cudaEventRecord(e1, b->stream));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bs = sh;
+          bd = dy;
+          bo = od;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // an even number of launches per candidate leaves buf[cur] the input
+  for (size_t l = 0; l < b->ctxs.size(); l++) {
+    lb_ctx *c = b->ctxs[l];
+    BCK(cudaMemcpyAsync(c->fbuf[c->cur], saved[l], sizes[l], cudaMemcpyDeviceToDevice, b->stream));
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  for (void *p : saved) cudaFree(p);
+  b->shape = bs;
+  b->dynamic = bd;
+  b->order = bo;
+  rc = build_tiles(b);
+  if (rc != LB_OK) return rc;
+  if (cache_json) {
+    std::string entry = std::string("\"") + key + "\": {\"shape\": " + std::to_string(bs) +
+                        ", \"dynamic\": " + std::to_string(bd) + ", \"order\": " + std::to_string(bo) +
+                        ", \"ms_per_iter\": " + std::to_string(best / reps) + "}";
+    std::string body;
+    size_t l = cache.find('{'), r = cache.rfind('}');
+    if (l != std::string::npos && r != std::string::npos && r > l) body = cache.substr(l + 1, r - l - 1);
+    while (!body.empty() && isspace((unsigned char)body.back())) body.pop_back();
+    std::string outs = "{" + body + (body.empty() ? "\n  " : ",\n  ") + entry + "\n}\n";
+    FILE *fp = fopen(cache_json, "wb");
+    if (fp) {
+      fwrite(outs.data(), 1, outs.size(), fp);
+      fclose(fp);
+    }
+  }
+  return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// lbint.h -- internal interface between the host orchestration and the
+// kernels: argument structs (passed by value to the kernels) and the
+// launch functions each kernel file exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbk {
+
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+enum { OPEN_NONE = 0, OPEN_POISEUILLE = 1, OPEN_UNIFORM = 2, OPEN_DIRICHLET = 3,
+       OPEN_GRADIENT = 4 };
+enum { SOL_NONE = 0, SOL_DIRICHLET = 1, SOL_ADIABATIC = 2 };
+
+constexpr int MAX_OPEN = 8;
+constexpr int NFIELD = 4;   // per component: drho, px, py, drho_eq
+constexpr int NTHERMO = 16; // FP64 thermo partial sums per block
+
+struct OpenDesc {
+  int wall;      // 0 xlo, 1 xhi, 2 ylo, 3 yhi
+  int a0, a1;    // extent along the wall
+  int kind;      // 0 inlet, 1 outlet
+  int style[2];  // OPEN_* per component
+  float v[2];    // speed (uniform) or v_max (poiseuille)
+  float rho[2];  // density held by dirichlet
+  float drho[2]; // that density minus the component's rho_ref (from FP64)
+  int sstyle;    // SOL_* for the solute
+  float Cbar;    // dirichlet concentration
+};
+
+struct Geometry {
+  int nx, ny, pitch, mw;  // mw = pitch / 32 mask words per row
+  size_t plane;           // ny * pitch
+};
+
+// one iteration of the fluid lattice(s)
+struct FluidArgs {
+  Geometry g;
+  const void *fin;        // populations before the step [nc][9][plane]
+  void *fout;             // populations after the step
+  const uint32_t *mask;
+  float rho_ref[2];
+  float scale, inv_scale; // storage scale 2^s and 2^-s (FP16), else 1
+  float tau[2], omega[2];
+  float fx[2], fy[2];     // aveforce
+  float ax[2], ay[2];     // aveacceleration
+  int ads[2];             // adhesiveforce on/off per component
+  float Gads[2], ads_psi0[2], ads_rho0[2];
+  float G, psi0, sc_rho0; // interforce
+  int nopen;
+  OpenDesc op[MAX_OPEN];
+  float *fields;          // [nc][NFIELD][plane] or nullptr
+  float *uout;            // [2][plane] solvent velocity or nullptr
+  uint32_t sr_seed;       // 16-bit stores: 0 = round to nearest, else the
+                          // step's seed of the stochastic-rounding dither
+  uint32_t step_seed;     // per-iteration seed of the mass-exact collision
+};
+
+// gradient openings (after collision)
+struct GradArgs {
+  Geometry g;
+  void *f;                // populations after the step
+  float *fields;          // or nullptr
+  const uint32_t *mask;
+  int nc;
+  int nopen;
+  OpenDesc op[MAX_OPEN];
+  float inv_scale, scale;
+};
+
+// one iteration of the solute lattice
+struct SoluteArgs {
+  Geometry g;
+  const float *gin;       // [q][plane]
+  float *gout;
+  const uint32_t *mask;
+  const float *u;         // [2][plane] solvent velocity of this step
+  float omega;
+  int react;
+  float kr, Cs;
+  float *db;              // deposit share per fluid node
+  float *Cfield;          // or nullptr
+  int nopen;
+  OpenDesc op[MAX_OPEN];
+};
+
+// precipitation gather and growth decisions / flips
+struct GrowthArgs {
+  Geometry g;
+  uint32_t *mask;
+  const float *db;
+  double *b;
+  uint8_t *flip;
+  double bmax, b0;
+  uint64_t seed;
+  int64_t t;              // 1-based iteration number
+  int q;
+  int nopen;
+  OpenDesc op[MAX_OPEN];
+  // flip application
+  const void *f;          // fluid populations after the step [nc][9][plane]
+  int nc;
+  float rho_ref[2];
+  float inv_scale;
+  float *gpop;            // solute populations after the step
+  double *removed;        // [nc + 1][plane] booked mass of flipped nodes
+  unsigned long long *nflips;
+};
+
+// thermo reduction over the node fields
+struct ThermoArgs {
+  Geometry g;
+  const uint32_t *mask;
+  const float *fields;    // [nc][NFIELD][plane]
+  int nc;
+  const float *Cfield;    // or nullptr
+  const double *b;        // or nullptr
+  const double *removed;  // [nc + 1][plane] or nullptr
+  double *partials;       // [nblocks][NTHERMO]
+  double *out;            // [NTHERMO]
+};
+
+// launchers (return the kernel count launched, or -1 on a launch error)
+int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s);
+int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
+int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
+int launch_growth(const GrowthArgs &a, cudaStream_t s);
+int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);
+int thermo_blocks(const Geometry &g);
+int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s);
+
+// state conversion between FP64 host-layout arrays [q][ny][nx] and storage
+int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,
+                       Geometry g, int q, float rho_ref, float scale, bool shift,
+                       cudaStream_t s);
+int launch_export_pops(int storage, const void *src, double *dst, const uint32_t *mask,
+                       Geometry g, int q, float rho_ref, float inv_scale, bool shift,
+                       cudaStream_t s);
+int launch_equilibrium(int storage, const double *rho, const double *ux, const double *uy,
+                       void *dst, const uint32_t *mask, Geometry g, float rho_ref,
+                       float scale, cudaStream_t s);
+int launch_solute_equilibrium(int q, const double *C, const double *ux, const double *uy,
+                              float *dst, const uint32_t *mask, Geometry g, cudaStream_t s);
+int launch_export_fields(const float *fields, int comp, const uint32_t *mask, Geometry g,
+                         float rho_ref, double *rho, double *px, double *py, double *req,
+                         cudaStream_t s);
+int launch_export_velocity(const float *fields, int nc, const uint32_t *mask, Geometry g,
+                           const float *rho_ref, float *rho, float *ux, float *uy,
+                           cudaStream_t s);
+int launch_export_plane_f32(const float *src, const uint32_t *mask, Geometry g, double *dst,
+                            cudaStream_t s);
+int launch_export_plane_f64(const double *src, Geometry g, double *dst, cudaStream_t s);
+int launch_import_plane_f64(const double *src, Geometry g, double *dst, cudaStream_t s);
+
+}  // namespace lbk

@@ -116,8 +116,10 @@ def circle_mask(nx: int, ny: int, xc: int, yc: int, r: int,
 
 
 def _disc_stamp(m: np.ndarray, xc: int, yc: int, r: int, periodic_x: bool,
-                periodic_y: bool) -> None:
+                periodic_y: bool) -> int:
+    """Mark the disc solid; return how many nodes became solid."""
     ny, nx = m.shape
+    added = 0
     for dy in range(-r, r + 1):
         w = int(np.floor(np.sqrt(r * r - dy * dy)))
         yy = yc + dy
@@ -130,7 +132,9 @@ def _disc_stamp(m: np.ndarray, xc: int, yc: int, r: int, periodic_x: bool,
             xs %= nx
         else:
             xs = xs[(xs >= 0) & (xs < nx)]
+        added += int(len(xs) - int(m[yy, xs].sum()))
         m[yy, xs] = 1
+    return added
 
 
 def random_discs(nx: int, ny: int, seed: int, rmin: int, rmax: int, *,
@@ -151,11 +155,18 @@ def random_discs(nx: int, ny: int, seed: int, rmin: int, rmax: int, *,
     m = np.zeros((ny, nx), np.uint8) if base is None else base.copy()
     discs: List[Tuple[int, int, int]] = []
     target_solid = None if porosity is None else (1.0 - porosity) * nx * ny
+    solid_count = int(m.sum())
+    # placed discs bucketed on a grid of cells at least as wide as the
+    # largest exclusion distance, so a candidate is checked against the
+    # discs of its 3 x 3 cells only
+    cell = 2 * rmax + gap
+    gx, gy = max(1, nx // cell), max(1, ny // cell)
+    buckets = {}
     tries = 0
     while tries < max_tries:
         if count is not None and len(discs) >= count:
             break
-        if target_solid is not None and m.sum() >= target_solid:
+        if target_solid is not None and solid_count >= target_solid:
             break
         tries += 1
         r = int(rng.integers(rmin, rmax + 1))
@@ -168,8 +179,18 @@ def random_discs(nx: int, ny: int, seed: int, rmin: int, rmax: int, *,
         xc = int(rng.integers(lox, hix + 1))
         yc = int(rng.integers(loy, hiy + 1))
         ok = True
+        cx, cy = min(xc * gx // nx, gx - 1), min(yc * gy // ny, gy - 1)
         if not overlap:
-            for (x2, y2, r2) in discs:
+            near = []
+            for ddy in (-1, 0, 1):
+                for ddx in (-1, 0, 1):
+                    kx, ky = cx + ddx, cy + ddy
+                    if periodic_x:
+                        kx %= gx
+                    if periodic_y:
+                        ky %= gy
+                    near.extend(buckets.get((kx, ky), ()))
+            for (x2, y2, r2) in (discs if gx < 3 or gy < 3 else near):
                 dx = xc - x2
                 dy = yc - y2
                 if periodic_x:
@@ -183,7 +204,8 @@ def random_discs(nx: int, ny: int, seed: int, rmin: int, rmax: int, *,
         if not ok:
             continue
         discs.append((xc, yc, r))
-        _disc_stamp(m, xc, yc, r, periodic_x, periodic_y)
+        buckets.setdefault((cx, cy), []).append((xc, yc, r))
+        solid_count += _disc_stamp(m, xc, yc, r, periodic_x, periodic_y)
     por = 1.0 - float(m.sum()) / (nx * ny)
     return m, discs, por
 
