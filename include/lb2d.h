@@ -246,6 +246,28 @@ int lb_iteration(lb_ctx *ctx, int Nt);
 /* Thermo record of the last thermo evaluation. */
 int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out);
 
+/* Recompute the thermo record of the context's last thermo evaluation
+ * without allocating anything.  The paper has no counterpart: this is for
+ * callers that cannot let the library allocate device memory -- when a
+ * framework's caching allocator already holds the free device memory, when
+ * a loop cannot afford an allocation or the device-wide synchronisation a
+ * cudaFree may imply, or when a program forbids allocation after start-up.
+ * The FP64 partial sums go to one fixed device array of the library (room
+ * for 1024 blocks of partial sums, 131,200 bytes, kept by every GPU that
+ * loads the library until the process exits) instead of a buffer of the
+ * context; the result is the same, bit for bit, as lb_get_thermo's.
+ * Inputs: ctx (its fields, mask and deposits on the device); output: *out
+ * (host).  Returns LB_E_ARG if the lattice would need more than 1024
+ * blocks of partial sums, LB_E_ORDER before the first lb_iteration, and
+ * synchronises ctx's stream.  The first call on a device looks up the
+ * array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  All calls share the
+ * one array: calls whose kernels overlap on a GPU (different streams,
+ * contexts or threads) race and must be serialised by the caller.  Every
+ * value the kernels read is written earlier in the same call, so what a
+ * previous call left in the array does not matter. */
+int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out);
+
 /* Node fields of the last thermo evaluation for fluid `fluid` (host
  * [ny][nx] FP64, any pointer may be NULL): density, physical momentum
  * density j + F/2 and equilibrium density; zero on solid nodes. */

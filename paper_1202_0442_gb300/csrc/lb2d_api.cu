@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1638,3 +1639,98 @@ int lb_batch_autotune(lb_batch *b, const char *cache_json) {
 }
 
 }  // extern "C"
+
+// ======================================================================
+// thermo sums without allocation
+//
+// Some callers cannot let a library call cudaMalloc/cudaFree: applications
+// whose device memory is already handed out by a framework's caching
+// allocator (a fresh cudaMalloc can fail even though the framework has free
+// memory in its pool), loops that must not pay for an allocation or the
+// device-wide synchronisation cudaFree can imply, and programs that forbid
+// allocating once they are initialised.  lb_thermo_static serves them: its
+// FP64 partial sums live in the fixed array below instead of the context's
+// own buffer, so the call allocates nothing.
+// ======================================================================
+
+namespace {
+
+// room for the per-block partial sums of up to STATIC_THERMO_BLOCKS blocks
+// plus the NTHERMO final sums: (1024 + 1) * 16 doubles = 131,200 bytes,
+// held by every GPU that loads the library until the process exits
+constexpr int STATIC_THERMO_BLOCKS = 1024;
+static __device__ __align__(256) double g_thermo_scratch[(STATIC_THERMO_BLOCKS + 1) * NTHERMO];
+
+// device address of g_thermo_scratch per device, looked up once per device
+// (the host-side name of a __device__ array is not a device address)
+constexpr int STATIC_MAX_DEVICES = 64;
+double *g_thermo_scratch_dev[STATIC_MAX_DEVICES] = {};
+std::mutex g_thermo_scratch_mu;
+
+}  // namespace
+
+extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
+  NEED_CTX();
+  if (!out) return ctx->fail(LB_E_ARG, "null output");
+  if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+  if (ctx->device < 0 || ctx->device >= STATIC_MAX_DEVICES)
+    return ctx->fail(LB_E_UNSUPPORTED, "device %d is beyond the %d devices the static scratch serves",
+                     ctx->device, STATIC_MAX_DEVICES);
+  if (ctx->tblocks > STATIC_THERMO_BLOCKS)
+    return ctx->fail(LB_E_ARG, "lattice needs %d blocks of partial sums; the static scratch holds %d",
+                     ctx->tblocks, STATIC_THERMO_BLOCKS);
+  TRY(set_device(ctx));
+  double *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_thermo_scratch_mu);
+    if (!g_thermo_scratch_dev[ctx->device]) {
+      cudaError_t e = cudaGetSymbolAddress((void **)&g_thermo_scratch_dev[ctx->device], g_thermo_scratch);
+      if (e != cudaSuccess) {
+        g_thermo_scratch_dev[ctx->device] = nullptr;
+        return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_thermo_scratch)");
+      }
+    }
+    scratch = g_thermo_scratch_dev[ctx->device];
+  }
+  // every slot the kernels read is written by the same call first, so the
+  // contents a previous call left behind need no clearing
+  ThermoArgs ta{};
+  ta.g = ctx->g;
+  ta.mask = ctx->mask;
+  ta.fields = ctx->fields;
+  ta.nc = ctx->nc;
+  ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
+  ta.b = ctx->react ? ctx->b : nullptr;
+  ta.removed = ctx->removed;
+  ta.partials = scratch;
+  ta.out = scratch + (size_t)STATIC_THERMO_BLOCKS * NTHERMO;
+  LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
+  double h[NTHERMO];
+  unsigned long long nfl = 0;
+  CK(cudaMemcpyAsync(h, ta.out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&nfl, ctx->nflips, sizeof nfl, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  lb_thermo_t T;
+  memset(&T, 0, sizeof T);
+  T.step = ctx->thermo.step;
+  T.nsolid = (int64_t)llround(h[13]);
+  T.nfluid = (int64_t)llround(h[14]);
+  for (int c = 0; c < ctx->nc; c++) {
+    T.mass[c] = ctx->rho_ref[c] * (double)T.nfluid + h[0 + c];
+    T.mass_eq[c] = ctx->rho_ref[c] * (double)T.nfluid + h[2 + c];
+    T.mom_comp[c][0] = h[4 + 2 * c];
+    T.mom_comp[c][1] = h[5 + 2 * c];
+    T.mom[0] += h[4 + 2 * c];
+    T.mom[1] += h[5 + 2 * c];
+  }
+  T.solute = h[8];
+  T.bsum = h[9];
+  T.removed[0] = h[10];
+  T.removed[1] = h[11];
+  T.removed_solute = h[12];
+  T.flips = (int64_t)nfl;
+  *out = T;
+  for (int q = 0; q < NTHERMO; q++)
+    if (!std::isfinite(h[q])) return ctx->fail(LB_E_NAN, "thermo sum %d is not finite", q);
+  return LB_OK;
+}

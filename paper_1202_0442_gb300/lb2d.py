@@ -95,6 +95,7 @@ SIGNATURES = {
     "lb_thermo": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
     "lb_get_thermo": (I, [P, C.POINTER(Thermo)]),
+    "lb_thermo_static": (I, [P, C.POINTER(Thermo)]),
     "lb_get_fields": (I, [P, I, DP, DP, DP, DP]),
     "lb_get_velocity_f32": (I, [P, FP, FP, FP]),
     "lb_get_populations": (I, [P, I, DP]),
@@ -302,6 +303,13 @@ class Lattice:
     def get_thermo(self) -> dict:
         t = Thermo()
         self._ck(self._L.lb_get_thermo(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def thermo_static(self) -> dict:
+        """Thermo record recomputed by lb_thermo_static, which allocates
+        nothing (its scratch is a fixed array of the library)."""
+        t = Thermo()
+        self._ck(self._L.lb_thermo_static(self._h, C.byref(t)))
         return t.as_dict()
 
     def fields(self, fluid: int = 1):
