@@ -187,6 +187,77 @@ def run_reference(args, world, rank, dist):
     return 0
 
 
+def time_steps(lt, steps, flush, stream):
+    """Per-step CUDA-event times (ms) of lt.iteration(1), L2 flushed before
+    each step."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush()
+        ev[k][0].record(stream)
+        lt.iteration(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def variants(args, local, stream, flush, value_fp32):
+    """16-bit storage on the same workload, and the 256-lattice batch as one
+    launch per iteration against one launch per lattice."""
+    import torch
+    from paper_1202_0442_gb300 import lb2d, synth
+    out = {}
+    w = synth.porous()
+    for st in ("fp16", "bf16"):
+        lt = lb2d.from_workload(w, st, h_max=2e-3, device=local, stream=stream.cuda_stream,
+                                rounding="stochastic")
+        lt.thermo(100)
+        time_steps(lt, 5, flush, stream)
+        t = time_steps(lt, min(args.steps, 60), flush, stream)
+        v = w.nodes / (t.mean() * 1e-3) / 1e6
+        out[st] = {"value": v, "unit": "MLUPS", "speedup_vs_fp32": v / value_fp32,
+                   "rounding": "stochastic", "tolerance_met": "2e-3 (FP16) / 1e-2 (BF16) rel. u, parity tests",
+                   "kernel_ms": float(np.median(t))}
+        del lt
+    # config 5: 256 periodic porous lattices, sides 64..512
+    ws = synth.batch()
+    lats = [lb2d.from_workload(x, "fp32", device=local, stream=stream.cuda_stream) for x in ws]
+    for lt in lats:
+        lt.thermo(1 << 30)
+    nodes = sum(x.nodes for x in ws)
+    b = lb2d.Batch(lats)
+    b.autotune(None)
+    b.iteration(20, use_graph=True)
+    torch.cuda.synchronize()
+    n = 100
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.iteration(n, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / n
+    for lt in lats:
+        lt.iteration(2)
+    torch.cuda.synchronize()
+    m = 10
+    e0.record(stream)
+    for _ in range(m):
+        for lt in lats:
+            lt.iteration(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1) / m
+    out["batched"] = {"workload": f"{len(ws)} periodic porous lattices, sides 64-512 step 32, "
+                                  f"porosity 0.4-0.9, tau 0.6-1.5 ({nodes} nodes)",
+                      "mlups_one_launch": nodes / (ms_b * 1e-3) / 1e6,
+                      "mlups_one_launch_per_lattice": nodes / (ms_s * 1e-3) / 1e6,
+                      "speedup": ms_s / ms_b, "ms_per_iteration_batched": ms_b,
+                      "ms_per_iteration_per_lattice": ms_s, "graph": True,
+                      "state_bytes": int(2 * 36 * nodes)}
+    del b, lats
+    return out
+
+
 def run_gb300(args, world, rank, local, dist):
     import torch
     from paper_1202_0442_gb300 import build, lb2d, synth
@@ -291,6 +362,7 @@ def run_gb300(args, world, rank, local, dist):
                    "l2": "flushed before every timed step (write 2xL2, read 2xL2)",
                    "thermo_every": 100, "parallelism": f"replicas x{world}"},
         "mflups": world * fluid / (ms_step * 1e-3) / 1e6,
+        "bytes_all_nodes_frac": BYTES_PER_FLUID_NODE[storage] * nodes / (kernel_ms * 1e-3) / 1e9 / peaks()[0],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_fluid_local", "kernel_ms": kernel_ms,
@@ -301,6 +373,8 @@ def run_gb300(args, world, rank, local, dist):
     }
     if clocks:
         line["clocks"] = clocks
+    if world == 1 and not args.no_variants:
+        line["variants"] = variants(args, local, stream, flush, value)
     if world == 1 and not args.no_cpu_baseline:
         v, n, dt = oracle_rate(w, args.cpu_seconds, 2000)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
@@ -318,6 +392,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

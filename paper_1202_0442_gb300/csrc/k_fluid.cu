@@ -62,7 +62,10 @@ __device__ __forceinline__ uint32_t window_bits(const uint32_t (*win)[3], const 
 }
 
 // pull the nine populations of node (x, y) from `base` (one component),
-// bouncing back from solid sources; `bits` is the node's neighbourhood
+// bouncing back from solid sources; `bits` is the node's neighbourhood.
+// One load per direction: the streaming source x - e_i, or, where that
+// node (neighbour opp(i)) is solid, the node's own outgoing population of
+// the opposite direction (half-way bounce-back).
 template <class S>
 __device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, int y,
                                       uint32_t bits, float inv, float (&h)[9]) {
@@ -71,17 +74,11 @@ __device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, i
   const int P = (int)g.plane;
   const int r0 = y * g.pitch, rm = ym * g.pitch, rp = yp * g.pitch;
   const int self = r0 + x;
-  // source x - e_i of direction i
   const int src[9] = {self, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
-  // the nine streaming loads do not depend on the mask: issue them first
 #pragma unroll
-  for (int i = 0; i < 9; i++) h[i] = Store<S>::ld(base, i * P + src[i], inv);
-  // half-way bounce-back where the source x - e_i (neighbour opp(i)) is
-  // solid: the node's own outgoing population of the opposite direction
-  if (bits & ~(1u << 4)) {
-#pragma unroll
-    for (int i = 1; i < 9; i++)
-      if (nb(bits, OPP(i))) h[i] = Store<S>::ld(base, OPP(i) * P + self, inv);
+  for (int i = 0; i < 9; i++) {
+    const int k = (i && nb(bits, OPP(i))) ? OPP(i) * P + self : i * P + src[i];
+    h[i] = Store<S>::ld(base, k, inv);
   }
 }
 
@@ -240,15 +237,31 @@ __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
 constexpr int LOC_BY = 8;
 
 template <class S, int NC, bool ME>
-__global__ void __launch_bounds__(32 * LOC_BY) k_fluid_local(const FluidArgs p) {
+__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid_local(const FluidArgs p) {
   __shared__ uint32_t win[LOC_BY + 2][3];
   const Geometry &g = p.g;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * LOC_BY + threadIdx.y;
   load_mask_window<LOC_BY>(p.mask, g, blockIdx.x, blockIdx.y * LOC_BY, win);
   __syncthreads();
-  if (x >= g.nx || y >= g.ny) return;
-  if ((win[threadIdx.y + 1][1] >> threadIdx.x) & 1u) return;  // solid nodes hold no populations
+  if (y >= g.ny) return;
+  // solid nodes (and the row padding past nx) hold no populations.  In a
+  // warp that also has fluid lanes they still store zeros, so the warp
+  // writes whole 32-byte sectors rather than partial ones.
+  const bool idle = x >= g.nx || ((win[threadIdx.y + 1][1] >> threadIdx.x) & 1u);
+  const unsigned busy = __ballot_sync(0xffffffffu, !idle);
+  if (idle) {
+    if (busy) {
+      const int self = y * g.pitch + x;
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        S *out = (S *)p.fout + (size_t)c * 9 * g.plane;
+#pragma unroll
+        for (int i = 0; i < 9; i++) Store<S>::st(out, i * (int)g.plane + self, 0.0f, 1.0f);
+      }
+    }
+    return;
+  }
   const uint32_t bits = window_bits(win, p.mask, g, x, y, threadIdx.y);
   float h[NC][9];
 #pragma unroll
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(32 * LOC_BY) k_fluid_local(const FluidArgs p) 
 constexpr int SC_TX = 32, SC_TY = 16;
 
 template <class S, int NC>
-__global__ void __launch_bounds__(SC_TX *SC_TY) k_fluid_sc(const FluidArgs p) {
+__global__ void __launch_bounds__(SC_TX *SC_TY, 2) k_fluid_sc(const FluidArgs p) {
   // rho - rho_ref of every component for the tile and a one-node ring; slot
   // (ty + 1, tx + 1) holds node (x0 + tx, y0 + ty) wrapped periodically.
   // Solid nodes are told apart by the mask bits, not by the stored value.

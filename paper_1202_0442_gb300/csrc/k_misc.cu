@@ -26,39 +26,42 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Block b handles rows b, b + gridDim.x, ...; its threads stride over x.
+// Each thread keeps FP64 sums of the quantities the run has, then the block
+// reduces them with warp shuffles and one shared-memory pass.
 __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
   const Geometry &g = a.g;
   double acc[NTHERMO];
 #pragma unroll
   for (int q = 0; q < NTHERMO; q++) acc[q] = 0.0;
-  const long long N = (long long)g.nx * g.ny;
-  const long long stride = (long long)gridDim.x * TB;
-  for (long long n = (long long)blockIdx.x * TB + threadIdx.x; n < N; n += stride) {
-    const int y = (int)(n / g.nx), x = (int)(n - (long long)y * g.nx);
-    const size_t self = (size_t)y * g.pitch + x;
-    if (solid_at(a.mask, g.mw, x, y)) {
-      acc[13] += 1.0;
-      if (a.b) acc[9] += a.b[self];
-    } else {
-      acc[14] += 1.0;
-      const float *f0 = a.fields;
-      acc[0] += (double)f0[self];
-      acc[2] += (double)f0[3 * g.plane + self];
-      acc[4] += (double)f0[g.plane + self];
-      acc[5] += (double)f0[2 * g.plane + self];
-      if (a.nc > 1) {
-        const float *f1 = a.fields + (size_t)NFIELD * g.plane;
-        acc[1] += (double)f1[self];
-        acc[3] += (double)f1[3 * g.plane + self];
-        acc[6] += (double)f1[g.plane + self];
-        acc[7] += (double)f1[2 * g.plane + self];
+  const size_t P = g.plane;
+  const float *f0 = a.fields;
+  const float *f1 = a.nc > 1 ? a.fields + (size_t)NFIELD * P : nullptr;
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    for (int x = threadIdx.x; x < g.nx; x += TB) {
+      const size_t self = (size_t)y * g.pitch + x;
+      if (solid_at(a.mask, g.mw, x, y)) {
+        acc[13] += 1.0;
+        if (a.b) acc[9] += a.b[self];
+      } else {
+        acc[14] += 1.0;
+        acc[0] += (double)f0[self];
+        acc[2] += (double)f0[3 * P + self];
+        acc[4] += (double)f0[P + self];
+        acc[5] += (double)f0[2 * P + self];
+        if (f1) {
+          acc[1] += (double)f1[self];
+          acc[3] += (double)f1[3 * P + self];
+          acc[6] += (double)f1[P + self];
+          acc[7] += (double)f1[2 * P + self];
+        }
+        if (a.Cfield) acc[8] += (double)a.Cfield[self];
       }
-      if (a.Cfield) acc[8] += (double)a.Cfield[self];
-    }
-    if (a.removed) {
-      acc[10] += a.removed[self];
-      if (a.nc > 1) acc[11] += a.removed[g.plane + self];
-      acc[12] += a.removed[(size_t)a.nc * g.plane + self];
+      if (a.removed) {
+        acc[10] += a.removed[self];
+        if (a.nc > 1) acc[11] += a.removed[P + self];
+        acc[12] += a.removed[(size_t)a.nc * P + self];
+      }
     }
   }
   __shared__ double sm[TB / 32][NTHERMO];
@@ -76,22 +79,15 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(TB) k_thermo_final(const double *partials, int nblocks,
-                                                     double *out) {
-  __shared__ double sm[TB / 32];
-  for (int q = 0; q < NTHERMO; q++) {
-    double v = 0.0;
-    for (int k = threadIdx.x; k < nblocks; k += TB) v += partials[(size_t)k * NTHERMO + q];
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int k = 0; k < TB / 32; k++) s += sm[k];
-      out[q] = s;
-    }
-    __syncthreads();
-  }
+// one warp per quantity: lanes stride over the blocks' partial sums in a
+// fixed order, then a shuffle tree
+__global__ void __launch_bounds__(32 * NTHERMO) k_thermo_final(const double *partials, int nblocks,
+                                                               double *out) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int k = lane; k < nblocks; k += 32) v += partials[(size_t)k * NTHERMO + q];
+  v = warp_sum(v);
+  if (lane == 0) out[q] = v;
 }
 
 __device__ __forceinline__ double w9d(int i) {
@@ -236,16 +232,16 @@ inline int ok() { return cudaGetLastError() == cudaSuccess ? 1 : -1; }
 }  // namespace
 
 int thermo_blocks(const Geometry &g) {
-  const long long n = (long long)g.nx * g.ny;
-  long long b = (n + TB - 1) / TB;
+  // one block per row, at most 4 per SM of a 152-SM GB300
+  int b = g.ny;
   if (b > 4 * 152) b = 4 * 152;
-  return (int)(b < 1 ? 1 : b);
+  return b < 1 ? 1 : b;
 }
 
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {
   k_thermo_partial<<<nblocks, TB, 0, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return -1;
-  k_thermo_final<<<1, TB, 0, s>>>(a.partials, nblocks, a.out);
+  k_thermo_final<<<1, 32 * NTHERMO, 0, s>>>(a.partials, nblocks, a.out);
   return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 

@@ -416,7 +416,7 @@ int run_thermo(lb_ctx *ctx) {
   ta.nc = ctx->nc;
   ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
   ta.b = ctx->react ? ctx->b : nullptr;
-  ta.removed = ctx->removed;
+  ta.removed = ctx->react ? ctx->removed : nullptr;
   ta.partials = ctx->partials;
   ta.out = ctx->tout;
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
@@ -1701,7 +1701,7 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   ta.nc = ctx->nc;
   ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
   ta.b = ctx->react ? ctx->b : nullptr;
-  ta.removed = ctx->removed;
+  ta.removed = ctx->react ? ctx->removed : nullptr;
   ta.partials = scratch;
   ta.out = scratch + (size_t)STATIC_THERMO_BLOCKS * NTHERMO;
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
