@@ -49,7 +49,7 @@ def peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("k_fluid.cu", "lbdev.cuh", "lbint.h"):
+    for name in ("k_fluid.cu", "lbcollide.cuh", "lbdev.cuh", "lbint.h"):
         with open(os.path.join(ROOT, "paper_1202_0442_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -45,6 +45,7 @@ extern "C" {
 #define LB_E_CUDA (-4)        /* CUDA runtime error (message has details) */
 #define LB_E_NAN (-5)         /* thermo found a non-finite sum */
 #define LB_E_NOMEM (-6)       /* device or host allocation failed */
+#define LB_E_TIMEOUT (-7)     /* a bounded wait inside a kernel gave up */
 
 /* population storage (lb_set_storage) */
 #define LB_FP32 0 /* f_i - w_i rho_ref in FP32 */
@@ -237,6 +238,16 @@ int lb_adhesiveforce(lb_ctx *ctx, double G, double psi0, double rho0,
  * the default).  Evaluating them reads the record back to the host, so it
  * synchronises the stream. */
 int lb_thermo(lb_ctx *ctx, int Nf);
+
+/* Fluid kernel for single-component lattices without interforce:
+ * "streaming" (one thread per node, loads straight from HBM; the fastest
+ * on GB300), "tma" (a persistent kernel that streams 128 x 4 tiles into
+ * shared memory with bulk asynchronous copies; same results bit for bit,
+ * needs the width to be a multiple of 4 nodes for FP32 or 8 for 16-bit
+ * storage) or "auto" (streaming, the default).  Other lattices always use
+ * the streaming kernels.  A timed-out wait inside the TMA kernel is
+ * reported as LB_E_TIMEOUT at the next thermo evaluation. */
+int lb_set_kernel(lb_ctx *ctx, const char *name);
 
 /* iteration command: advance Nt iterations.  The first call validates the
  * setup (LB_E_ARG with a message if it is inconsistent) and moves the

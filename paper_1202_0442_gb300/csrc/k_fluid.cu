@@ -20,7 +20,7 @@
 // it loads the mask words of its rows (plus one row above and below) and of
 // the two neighbouring word columns into shared memory once, and every
 // thread takes its 3 x 3 solid neighbourhood from there.
-#include "lbdev.cuh"
+#include "lbcollide.cuh"
 
 namespace lbk {
 
@@ -79,158 +79,6 @@ __device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, i
   for (int i = 0; i < 9; i++) {
     const int k = (i && nb(bits, OPP(i))) ? OPP(i) * P + self : i * P + src[i];
     h[i] = Store<S>::ld(base, k, inv);
-  }
-}
-
-// random word for (node, component, direction, step)
-__device__ __forceinline__ uint32_t rnd(uint32_t seed, int self, int c, int i) {
-  return mix32(((uint32_t)self * 0x9e3779b1u) ^ (seed + 0x632be5abu * (uint32_t)c) ^
-               (0x85ebca6bu * (uint32_t)(i + 1)));
-}
-
-// moments, forces, equilibrium velocity, BGK and the stores of one node.
-// Fsc: interforce already evaluated (zero when off).  ME: mass-exact
-// collision (see below).
-template <class S, int NC, bool ME>
-__device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
-                                              float (&h)[NC][9], const float (&Fsc)[NC][2]) {
-  const Geometry &g = p.g;
-  const int self = y * g.pitch + x;
-  const int P = (int)g.plane;
-  float drho[NC], rho[NC], jx[NC], jy[NC], Fx[NC], Fy[NC];
-#pragma unroll
-  for (int c = 0; c < NC; c++) {
-    const float(&f)[9] = h[c];
-    drho[c] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    rho[c] = p.rho_ref[c] + drho[c];
-    jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
-    jy[c] = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    Fx[c] = p.fx[c] + rho[c] * p.ax[c] + Fsc[c][0];
-    Fy[c] = p.fy[c] + rho[c] * p.ay[c] + Fsc[c][1];
-    if (p.ads[c]) {
-      float sx, sy;
-      wall_sum(bits, sx, sy);
-      const float psi = (NC == 1) ? p.ads_psi0[c] * expf(-p.ads_rho0[c] / rho[c]) : rho[c];
-      Fx[c] -= p.Gads[c] * psi * sx;
-      Fy[c] -= p.Gads[c] * psi * sy;
-    }
-  }
-  // equilibrium velocity (velocity shift) and the momentum rho u_eq it
-  // carries, the latter formed without a division
-  float uex[NC], uey[NC], mxt[NC], myt[NC];
-  if (NC == 1) {
-    mxt[0] = jx[0] + p.tau[0] * Fx[0];
-    myt[0] = jy[0] + p.tau[0] * Fy[0];
-    const float ir = 1.0f / rho[0];
-    uex[0] = mxt[0] * ir;
-    uey[0] = myt[0] * ir;
-  } else {
-    // common velocity sum(j/tau) / sum(rho/tau), shifted per component
-    float nxs = 0.f, nys = 0.f, den = 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      nxs += jx[c] * p.omega[c];
-      nys += jy[c] * p.omega[c];
-      den += rho[c] * p.omega[c];
-    }
-    const float upx = nxs / den, upy = nys / den;
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      mxt[c] = rho[c] * upx + p.tau[c] * Fx[c];
-      myt[c] = rho[c] * upy + p.tau[c] * Fy[c];
-      uex[c] = upx + p.tau[c] * Fx[c] / rho[c];
-      uey[c] = upy + p.tau[c] * Fy[c] / rho[c];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NC; c++) {
-    S *out = (S *)p.fout + (size_t)c * 9 * P;
-    float heq[9];
-    equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], heq);
-    const float om = p.omega[c];
-    if (!ME) {
-#pragma unroll
-      for (int i = 0; i < 9; i++) {
-        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, self, c, i) | 1u) : 0u;
-        Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale, r);
-      }
-    } else {
-      // Mass-exact collision: when |h| is large (two components, or one far
-      // from rho_ref) the rounding of nine stored values of a slowly
-      // changing state repeats every step and drifts the mass.  Here the
-      // exact sum D of the pulled values and the exact sum S of the eight
-      // stored moving populations are formed with error-free sums, and the
-      // rest population is set to D - S -- the BGK value in exact
-      // arithmetic -- rounded stochastically, so the node's mass is kept
-      // up to an unbiased last-bit step.
-      float Dh = h[c][0], Dl = 0.f;
-#pragma unroll
-      for (int i = 1; i < 9; i++) {
-        float s, e;
-        two_sum(Dh, h[c][i], s, e);
-        Dh = s;
-        Dl += e;
-      }
-      float Sh = 0.f, Sl = 0.f;
-#pragma unroll
-      for (int i = 1; i < 9; i++) {
-        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, self, c, i) | 1u) : 0u;
-        const float v = Store<S>::st_ret(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]),
-                                         p.scale, p.inv_scale, r);
-        float s, e;
-        two_sum(Sh, v, s, e);
-        Sh = s;
-        Sl += e;
-      }
-      float rh, rl;
-      two_sum(Dh, -Sh, rh, rl);
-      rl += Dl - Sl;
-      float h0, rem;
-      two_sum(rh, rl, h0, rem);
-      if (rem != 0.f && h0 != 0.f) {
-        const int step = ((rem > 0.f) == (h0 > 0.f)) ? 1 : -1;
-        const float nxt = __int_as_float(__float_as_int(h0) + step);
-        const float pr = fabsf(rem) / fabsf(nxt - h0);
-        const float u01 = (float)(rnd(p.step_seed, self, c, 9) >> 8) * (1.0f / 16777216.0f);
-        if (u01 < pr) h0 = nxt;
-      }
-      const uint32_t r0 = p.sr_seed ? (rnd(p.sr_seed, self, c, 0) | 1u) : 0u;
-      Store<S>::st(out, self, h0, p.scale, r0);
-    }
-    if (p.fields) {
-      float *fl = p.fields + (size_t)c * NFIELD * P;
-      fl[self] = drho[c];
-      fl[P + self] = jx[c] + 0.5f * Fx[c];
-      fl[2 * P + self] = jy[c] + 0.5f * Fy[c];
-      // sum of the equilibrium populations (Mass_eq of the thermo command)
-      fl[3 * P + self] = heq[0] + ((heq[1] + heq[3]) + (heq[2] + heq[4])) +
-                         ((heq[5] + heq[7]) + (heq[6] + heq[8]));
-    }
-  }
-  if (p.uout) {
-    float pxs = 0.f, pys = 0.f, rs = 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      pxs += jx[c] + 0.5f * Fx[c];
-      pys += jy[c] + 0.5f * Fy[c];
-      rs += rho[c];
-    }
-    p.uout[self] = pxs / rs;
-    p.uout[P + self] = pys / rs;
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
-                                               float (&h)[NC][9]) {
-  const Geometry &g = p.g;
-  if (!(x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1)) return;
-#pragma unroll 1
-  for (int k = 0; k < p.nopen; k++) {
-    if (!opening_has(p.op[k], x, y, g.nx, g.ny)) continue;
-#pragma unroll
-    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, y, p.rho_ref[c]);
-    break;
   }
 }
 

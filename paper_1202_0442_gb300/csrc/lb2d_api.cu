@@ -100,6 +100,9 @@ struct lb_ctx {
   double *partials = nullptr, *tout = nullptr;
   int tblocks = 0;
   int64_t t = 0;
+  int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline
+  int *errw = nullptr;   // device error word of the TMA kernel
+  int sms = 0;
   bool fields_valid = false;
   lb_thermo_t thermo{};
   bool thermo_valid = false;
@@ -304,6 +307,8 @@ int commit(lb_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->b, g.plane));
   TRY(dalloc(ctx, &ctx->removed, (size_t)(ctx->nc + 1) * g.plane));
   TRY(dalloc(ctx, &ctx->nflips, 1));
+  TRY(dalloc(ctx, &ctx->errw, 1));
+  CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->tblocks = thermo_blocks(g);
   TRY(dalloc(ctx, &ctx->partials, (size_t)ctx->tblocks * NTHERMO));
   TRY(dalloc(ctx, &ctx->tout, NTHERMO));
@@ -422,9 +427,12 @@ int run_thermo(lb_ctx *ctx) {
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
   double h[NTHERMO];
   unsigned long long nfl = 0;
+  int errw = 0;
   CK(cudaMemcpyAsync(h, ctx->tout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(&nfl, ctx->nflips, sizeof nfl, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&errw, ctx->errw, sizeof errw, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (errw) return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
   lb_thermo_t &T = ctx->thermo;
   memset(&T, 0, sizeof T);
   T.step = ctx->t;
@@ -458,7 +466,14 @@ int one_step(lb_ctx *ctx, bool fields) {
   // two components and Shan-Chen runs keep |f - w rho_ref| large: their
   // collision is the mass-exact one
   const bool mass_exact = ctx->nc == 2 || ctx->sc;
-  LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
+  const bool tma_ok = ctx->nc == 1 && !ctx->sc && tma_supported(ctx->storage, ctx->g);
+  if (ctx->kernel == 2 && !tma_ok)
+    return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component lattices without interforce "
+                     "whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
+  if (tma_ok && ctx->kernel == 2)
+    LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, s, ctx->sms));
+  else
+    LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
   // gradient openings
   GradArgs ga{};
   int ng = 0;
@@ -566,9 +581,10 @@ int lb_destroy(lb_ctx *ctx) {
   NEED_CTX();
   cudaSetDevice(ctx->device);
   if (ctx->committed) cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields, ctx->u,
-                  ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,     ctx->b,
-                  ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout};
+  void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
+                  ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
+                  ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
+                  ctx->errw};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -1024,6 +1040,16 @@ int lb_adhesiveforce(lb_ctx *ctx, double G, double psi0, double rho0, int fluid)
   ctx->Gads[fluid - 1] = G;
   ctx->ads_psi0[fluid - 1] = psi0;
   ctx->ads_rho0[fluid - 1] = rho0;
+  return LB_OK;
+}
+
+int lb_set_kernel(lb_ctx *ctx, const char *name) {
+  NEED_CTX();
+  if (!name) return ctx->fail(LB_E_ARG, "no kernel name");
+  if (!strcmp(name, "auto")) ctx->kernel = 0;
+  else if (!strcmp(name, "streaming")) ctx->kernel = 1;
+  else if (!strcmp(name, "tma")) ctx->kernel = 2;
+  else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming or tma");
   return LB_OK;
 }
 

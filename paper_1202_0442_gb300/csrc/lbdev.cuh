@@ -49,6 +49,7 @@ template <> struct Store<float> {
   static __device__ __forceinline__ float ld(const float *p, size_t k, float) {
     return __ldg(p + k);
   }
+  static __device__ __forceinline__ float ld_smem(const float *p, int k, float) { return p[k]; }
   static __device__ __forceinline__ void st(float *p, size_t k, float v, float) {
     p[k] = v;
   }
@@ -70,6 +71,9 @@ template <> struct Store<float> {
 template <> struct Store<__half> {
   static __device__ __forceinline__ float ld(const __half *p, size_t k, float inv) {
     return __half2float(__ldg(p + k)) * inv;
+  }
+  static __device__ __forceinline__ float ld_smem(const __half *p, int k, float inv) {
+    return __half2float(p[k]) * inv;
   }
   static __device__ __forceinline__ void st(__half *p, size_t k, float v, float sc) {
     p[k] = __float2half_rn(v * sc);
@@ -94,6 +98,9 @@ template <> struct Store<__half> {
 template <> struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, size_t k, float) {
     return __bfloat162float(__ldg(p + k));
+  }
+  static __device__ __forceinline__ float ld_smem(const __nv_bfloat16 *p, int k, float) {
+    return __bfloat162float(p[k]);
   }
   static __device__ __forceinline__ void st(__nv_bfloat16 *p, size_t k, float v, float) {
     p[k] = __float2bfloat16_rn(v);

@@ -125,6 +125,10 @@ struct ThermoArgs {
 // launchers (return the kernel count launched, or -1 on a launch error)
 int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s);
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
+// persistent TMA-pipelined single-component kernel (k_tma.cu); err is a
+// device word the kernel sets when an mbarrier wait times out
+bool tma_supported(int storage, const Geometry &g);
+int launch_fluid_tma(int storage, const FluidArgs &a, int *err, cudaStream_t s, int sms);
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
 int launch_growth(const GrowthArgs &a, cudaStream_t s);
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);

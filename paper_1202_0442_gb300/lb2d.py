@@ -20,11 +20,12 @@ from . import synth
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblb2d.so")
 
-LB_OK, LB_E_ORDER, LB_E_ARG, LB_E_UNSUPPORTED, LB_E_CUDA, LB_E_NAN, LB_E_NOMEM = 0, -1, -2, -3, -4, -5, -6
+LB_OK, LB_E_ORDER, LB_E_ARG, LB_E_UNSUPPORTED, LB_E_CUDA, LB_E_NAN, LB_E_NOMEM, LB_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LB_STOCHASTIC_ROUNDING = 0x100
 _CODES = {LB_E_ORDER: "LB_E_ORDER", LB_E_ARG: "LB_E_ARG", LB_E_UNSUPPORTED: "LB_E_UNSUPPORTED",
-          LB_E_CUDA: "LB_E_CUDA", LB_E_NAN: "LB_E_NAN", LB_E_NOMEM: "LB_E_NOMEM"}
+          LB_E_CUDA: "LB_E_CUDA", LB_E_NAN: "LB_E_NAN", LB_E_NOMEM: "LB_E_NOMEM",
+          LB_E_TIMEOUT: "LB_E_TIMEOUT"}
 
 
 class LBError(RuntimeError):
@@ -92,6 +93,7 @@ SIGNATURES = {
     "lb_aveacceleration_xy": (I, [P, D, D, I]),
     "lb_interforce": (I, [P, D, D, D]),
     "lb_adhesiveforce": (I, [P, D, D, D, I]),
+    "lb_set_kernel": (I, [P, S]),
     "lb_thermo": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
     "lb_get_thermo": (I, [P, C.POINTER(Thermo)]),
@@ -294,6 +296,9 @@ class Lattice:
         self._ck(self._L.lb_adhesiveforce(self._h, G, psi0, rho0, fluid))
 
     # -- output and action -----------------------------------------------------
+    def set_kernel(self, name: str = "auto"):
+        self._ck(self._L.lb_set_kernel(self._h, _b(name)))
+
     def thermo(self, Nf: int):
         self._ck(self._L.lb_thermo(self._h, Nf))
 
@@ -431,7 +436,7 @@ class Batch:
 
 def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0,
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
-                  rounding: str = "nearest") -> Lattice:
+                  rounding: str = "nearest", kernel: str = "auto") -> Lattice:
     """Issue the command sequence that sets up workload ``w``."""
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
@@ -467,6 +472,7 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
     if w.interforce is not None:
         lt.interforce(*w.interforce)
     lt.thermo(thermo)
+    lt.set_kernel(kernel)
     for s in range(w.ncomp):
         lt.set_equilibrium(w.rho[s], w.ux, w.uy, s + 1)
     if w.solute_q:
