@@ -55,20 +55,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, storage: str, units: int):
-    """Per-launch DRAM bytes of the fused kernel from the committed ncu
-    summary, scaled to this launch's fluid nodes; None when the summary was
-    taken on different kernel source."""
+def recorded_traffic(kernel: str, storage: str, workload: str):
+    """DRAM bytes (read + write) of one launch of the fused kernel on this
+    workload, from the committed ncu capture (profiles/traffic.json); None
+    when there is none or it was taken on different kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except Exception:
         return None
-    e = d.get(f"{kernel}/{storage}")
+    e = d.get(f"{kernel}/{storage}@{workload}")
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e["dram_bytes_per_fluid_node"] * units
+    return e["dram_bytes_read"] + e["dram_bytes_write"]
 
 
 class ClockSampler:
@@ -352,7 +352,7 @@ def run_gb300(args, world, rank, local, dist):
     peak, peak_kind = peaks()
     alg_bytes = BYTES_PER_FLUID_NODE[storage] * fluid
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    traffic = recorded_traffic("k_fluid_local", storage, fluid)
+    traffic = recorded_traffic("k_fluid_local", storage, "porous1024")
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

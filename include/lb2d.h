@@ -107,9 +107,11 @@ int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau);
 int lb_processors(lb_ctx *ctx, int px, int py);
 
 /* fluids command: two components with relaxation times tau1, tau2 and
- * density-ratio parameters alpha1, alpha2 (pass 4/9 for the plain
- * equilibrium of Eq. (2); other values give LB_E_UNSUPPORTED).  Must follow
- * lb_lattice and precede openings, initial state and forces. */
+ * density-ratio parameters alpha1, alpha2 in [0, 1) (LB_E_ARG otherwise).
+ * Component s then relaxes to f_eq,i = w_i rho [A_i + 3 e.u + 9/2 (e.u)^2
+ * - 3/2 u.u] with A_0 = (9/4) alpha_s, A_{1..8} = (9/5)(1 - alpha_s), so its
+ * sound speed squared is (3/5)(1 - alpha_s); alpha = 4/9 is Eq. (2).  Must
+ * follow lb_lattice and precede openings, initial state and forces. */
 int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1,
               double alpha2);
 

@@ -41,7 +41,7 @@ __device__ __forceinline__ void batch_node(const BatchLat &L, const S *fin, S *f
   const float mx = jx + L.tau * Fx, my = jy + L.tau * Fy;
   const float ux = mx * ir, uy = my * ir;
   float heq[9];
-  equilibrium_pairs(d, rho, ux, uy, mx, my, heq);
+  equilibrium_pairs(d, rho, ux, uy, mx, my, 1.0f / 9.0f, 1.0f / 36.0f, heq);
 #pragma unroll
   for (int i = 0; i < 9; i++)
     Store<S>::st(fout, (size_t)i * L.plane + self, h[i] + L.omega * (heq[i] - h[i]), L.scale);

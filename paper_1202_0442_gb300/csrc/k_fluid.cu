@@ -16,10 +16,11 @@
 // k_gradient: gradient openings, f(wall) = 2 f(wall+n) - f(wall+2n) after
 //   the collision (inlet_momentum command).
 //
-// A CTA of 32 x BY threads covers one 32-node word column of the solid mask;
-// it loads the mask words of its rows (plus one row above and below) and of
-// the two neighbouring word columns into shared memory once, and every
-// thread takes its 3 x 3 solid neighbourhood from there.
+// In k_fluid_local a warp covers one 32-node word of the solid mask: its
+// lanes read the words of rows y-1, y, y+1 (one broadcast load each; the two
+// edge lanes also read the words beside them) and every thread takes its
+// 3 x 3 solid neighbourhood from those, with no shared memory and no CTA
+// barrier.
 #include "lbcollide.cuh"
 
 namespace lbk {
@@ -29,36 +30,6 @@ namespace {
 __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
-}
-
-// mask words of rows y0-1 .. y0+BY (wrapped) and word columns c-1, c, c+1
-template <int BY>
-__device__ __forceinline__ void load_mask_window(const uint32_t *m, const Geometry &g, int c,
-                                                 int y0, uint32_t (*win)[3]) {
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  if (tid < (BY + 2) * 3) {
-    const int r = tid / 3, k = tid - r * 3;
-    const int yy = wrapi(y0 - 1 + r, g.ny);
-    const int cc = c - 1 + k;
-    win[r][k] = (cc >= 0 && cc < g.mw) ? __ldg(m + (size_t)yy * g.mw + cc) : 0u;
-  }
-}
-
-// 3 x 3 solid bits of node (x, y) = (32 c + lane, y0 + ty): from the window,
-// except on the first and last column where the periodic neighbour lies in
-// a word the window does not hold
-__device__ __forceinline__ uint32_t window_bits(const uint32_t (*win)[3], const uint32_t *m,
-                                                const Geometry &g, int x, int y, int ty) {
-  const int lane = x & 31;
-  if (x == 0 || x == g.nx - 1) {
-    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
-    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-    return nbr_bits(m, g.mw, x, y, xm, xp, ym, yp);
-  }
-  const uint32_t s = row3(win[ty][0], win[ty][1], win[ty][2], lane);
-  const uint32_t c = row3(win[ty + 1][0], win[ty + 1][1], win[ty + 1][2], lane);
-  const uint32_t n = row3(win[ty + 2][0], win[ty + 2][1], win[ty + 2][2], lane);
-  return s | (c << 3) | (n << 6);
 }
 
 // pull the nine populations of node (x, y) from `base` (one component),
@@ -86,17 +57,29 @@ constexpr int LOC_BY = 8;
 
 template <class S, int NC, bool ME>
 __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid_local(const FluidArgs p) {
-  __shared__ uint32_t win[LOC_BY + 2][3];
   const Geometry &g = p.g;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * LOC_BY + threadIdx.y;
-  load_mask_window<LOC_BY>(p.mask, g, blockIdx.x, blockIdx.y * LOC_BY, win);
-  __syncthreads();
   if (y >= g.ny) return;
+  // the warp's mask words: rows y-1, y, y+1 of its word column (broadcast
+  // loads), and for the two edge lanes the words beside them
+  uint32_t win[3][3];
+  {
+    const int lane = threadIdx.x, cw = blockIdx.x;
+    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+    const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw,
+                               p.mask + (size_t)yp * g.mw};
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      win[r][1] = __ldg(rows[r] + cw);
+      win[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
+      win[r][2] = (lane == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
+    }
+  }
   // solid nodes (and the row padding past nx) hold no populations.  In a
   // warp that also has fluid lanes they still store zeros, so the warp
   // writes whole 32-byte sectors rather than partial ones.
-  const bool idle = x >= g.nx || ((win[threadIdx.y + 1][1] >> threadIdx.x) & 1u);
+  const bool idle = x >= g.nx || ((win[1][1] >> threadIdx.x) & 1u);
   const unsigned busy = __ballot_sync(0xffffffffu, !idle);
   if (idle) {
     if (busy) {
@@ -110,7 +93,16 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid
     }
     return;
   }
-  const uint32_t bits = window_bits(win, p.mask, g, x, y, threadIdx.y);
+  uint32_t bits;
+  if (x == 0 || x == g.nx - 1) {
+    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+    bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
+  } else {
+    const int lane = threadIdx.x;
+    bits = row3(win[0][0], win[0][1], win[0][2], lane) | (row3(win[1][0], win[1][1], win[1][2], lane) << 3) |
+           (row3(win[2][0], win[2][1], win[2][2], lane) << 6);
+  }
   float h[NC][9];
 #pragma unroll
   for (int c = 0; c < NC; c++)

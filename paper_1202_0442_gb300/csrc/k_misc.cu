@@ -2,12 +2,17 @@
 //
 // k_thermo_partial / k_thermo_final: the thermo command's sums (mass,
 //   momentum j + F/2, equilibrium mass, solute, deposit, removed mass,
-//   node counts) over the state at the end of an iteration, in FP64.  The
-//   first kernel gives every block a fixed, strided set of nodes and reduces
-//   it with warp shuffles and one shared-memory pass into a per-block slot
-//   of a scratch array; the second reduces the slots in a fixed tree.  The
-//   order of every addition is fixed by the launch shape, so the result is
-//   the same bits on every run.
+//   node counts) over the state at the end of an iteration.  The first
+//   kernel gives every thread a fixed, strided set of nodes; a thread sums
+//   the FP32 fields of its nodes as an unevaluated pair hi + lo of FP32
+//   values with error-free additions (GB300's FP64 rate is a small fraction
+//   of its FP32 rate, and a plain FP64 add per node and quantity made the
+//   pass ALU-bound), counts nodes in integers and adds the FP64 arrays in
+//   FP64; the block then reduces in FP64 with warp shuffles and one
+//   shared-memory pass into a per-block slot of a scratch array, and the
+//   second kernel reduces the slots in a fixed tree.  The order of every
+//   addition is fixed by the launch shape, so the result is the same bits
+//   on every run.
 // Conversions between FP64 arrays in the caller's layout ([q][ny][nx],
 // dense) and the library's storage (deviations from w_i rho_ref, pitched,
 // FP32/FP16/BF16), equilibrium initialisation from rho and u, and field
@@ -26,14 +31,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// hi + lo += v without rounding error in hi + lo's leading part (Knuth's
+// two-sum; the rounding of lo's own additions is second order)
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
 // Block b handles rows b, b + gridDim.x, ...; its threads stride over x.
-// Each thread keeps FP64 sums of the quantities the run has, then the block
-// reduces them with warp shuffles and one shared-memory pass.
+// Quantities 0..8 come from FP32 planes and are summed per thread as FP32
+// pairs; 9..12 are FP64 arrays (reaction runs only); 13, 14 are counts.
 __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
   const Geometry &g = a.g;
-  double acc[NTHERMO];
+  float hi[9], lo[9];
 #pragma unroll
-  for (int q = 0; q < NTHERMO; q++) acc[q] = 0.0;
+  for (int q = 0; q < 9; q++) hi[q] = lo[q] = 0.f;
+  double dacc[4] = {0.0, 0.0, 0.0, 0.0};
+  unsigned nsolid = 0, nfluid = 0;
   const size_t P = g.plane;
   const float *f0 = a.fields;
   const float *f1 = a.nc > 1 ? a.fields + (size_t)NFIELD * P : nullptr;
@@ -41,29 +57,38 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
     for (int x = threadIdx.x; x < g.nx; x += TB) {
       const size_t self = (size_t)y * g.pitch + x;
       if (solid_at(a.mask, g.mw, x, y)) {
-        acc[13] += 1.0;
-        if (a.b) acc[9] += a.b[self];
+        nsolid++;
+        if (a.b) dacc[0] += a.b[self];
       } else {
-        acc[14] += 1.0;
-        acc[0] += (double)f0[self];
-        acc[2] += (double)f0[3 * P + self];
-        acc[4] += (double)f0[P + self];
-        acc[5] += (double)f0[2 * P + self];
+        nfluid++;
+        pair_add(hi[0], lo[0], f0[self]);
+        pair_add(hi[2], lo[2], f0[3 * P + self]);
+        pair_add(hi[4], lo[4], f0[P + self]);
+        pair_add(hi[5], lo[5], f0[2 * P + self]);
         if (f1) {
-          acc[1] += (double)f1[self];
-          acc[3] += (double)f1[3 * P + self];
-          acc[6] += (double)f1[P + self];
-          acc[7] += (double)f1[2 * P + self];
+          pair_add(hi[1], lo[1], f1[self]);
+          pair_add(hi[3], lo[3], f1[3 * P + self]);
+          pair_add(hi[6], lo[6], f1[P + self]);
+          pair_add(hi[7], lo[7], f1[2 * P + self]);
         }
-        if (a.Cfield) acc[8] += (double)a.Cfield[self];
+        if (a.Cfield) pair_add(hi[8], lo[8], a.Cfield[self]);
       }
       if (a.removed) {
-        acc[10] += a.removed[self];
-        if (a.nc > 1) acc[11] += a.removed[P + self];
-        acc[12] += a.removed[(size_t)a.nc * P + self];
+        dacc[1] += a.removed[self];
+        if (a.nc > 1) dacc[2] += a.removed[P + self];
+        dacc[3] += a.removed[(size_t)a.nc * P + self];
       }
     }
   }
+  double acc[NTHERMO];
+#pragma unroll
+  for (int q = 0; q < 9; q++) acc[q] = (double)hi[q] + (double)lo[q];
+#pragma unroll
+  for (int q = 0; q < 4; q++) acc[9 + q] = dacc[q];
+  acc[13] = (double)nsolid;
+  acc[14] = (double)nfluid;
+#pragma unroll
+  for (int q = 15; q < NTHERMO; q++) acc[q] = 0.0;
   __shared__ double sm[TB / 32][NTHERMO];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -90,10 +115,6 @@ __global__ void __launch_bounds__(32 * NTHERMO) k_thermo_final(const double *par
   if (lane == 0) out[q] = v;
 }
 
-__device__ __forceinline__ double w9d(int i) {
-  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-}
-
 __device__ __forceinline__ bool node_of(int idx, const Geometry &g, int &x, int &y) {
   if (idx >= g.nx * g.ny) return false;
   y = idx / g.nx;
@@ -103,7 +124,7 @@ __device__ __forceinline__ bool node_of(int idx, const Geometry &g, int &x, int 
 
 template <class S>
 __global__ void k_import_pops(const double *src, S *dst, const uint32_t *mask, Geometry g,
-                              int q, float rho_ref, float scale, bool shift) {
+                              int q, float rho_ref, float scale, bool shift, double alpha) {
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
@@ -111,14 +132,14 @@ __global__ void k_import_pops(const double *src, S *dst, const uint32_t *mask, G
   const size_t nn = (size_t)g.nx * g.ny;
   for (int i = 0; i < q; i++) {
     double v = sol ? 0.0 : src[(size_t)i * nn + dense];
-    if (shift && !sol) v -= w9d(i) * (double)rho_ref;
+    if (shift && !sol) v -= wshare(i, alpha) * (double)rho_ref;
     Store<S>::st(dst, (size_t)i * g.plane + self, (float)v, scale);
   }
 }
 
 template <class S>
 __global__ void k_export_pops(const S *src, double *dst, const uint32_t *mask, Geometry g,
-                              int q, float rho_ref, float inv_scale, bool shift) {
+                              int q, float rho_ref, float inv_scale, bool shift, double alpha) {
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
@@ -128,16 +149,18 @@ __global__ void k_export_pops(const S *src, double *dst, const uint32_t *mask, G
     double v = 0.0;
     if (!sol) {
       v = (double)Store<S>::ld(src, (size_t)i * g.plane + self, inv_scale);
-      if (shift) v += w9d(i) * (double)rho_ref;
+      if (shift) v += wshare(i, alpha) * (double)rho_ref;
     }
     dst[(size_t)i * nn + dense] = v;
   }
 }
 
-// f_eq(rho, u) of Eq. (2), evaluated in FP64, stored as deviations
+// f_eq(rho, u) of Eq. (2) (with the fluids command's alpha), evaluated in
+// FP64, stored as deviations from s_i rho_ref
 template <class S>
 __global__ void k_equilibrium(const double *rho, const double *ux, const double *uy, S *dst,
-                              const uint32_t *mask, Geometry g, float rho_ref, float scale) {
+                              const uint32_t *mask, Geometry g, float rho_ref, float scale,
+                              double alpha) {
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
@@ -148,7 +171,8 @@ __global__ void k_equilibrium(const double *rho, const double *ux, const double 
   for (int i = 0; i < 9; i++) {
     const double eu = EX(i) * u + EY(i) * v;
     const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-    const double h = w * (dr + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq));
+    const double h = (alpha == 4.0 / 9.0) ? w * (dr + r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq))
+                                          : wshare(i, alpha) * dr + w * r * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
     Store<S>::st(dst, (size_t)i * g.plane + self, sol ? 0.0f : (float)h, scale);
   }
 }
@@ -247,48 +271,48 @@ int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {
 
 int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,
                        Geometry g, int q, float rho_ref, float scale, bool shift,
-                       cudaStream_t s) {
+                       double alpha, cudaStream_t s) {
   switch (storage) {
     case ST_FP16:
-      k_import_pops<__half><<<grid1(g), 256, 0, s>>>(src, (__half *)dst, mask, g, q, rho_ref, scale, shift);
+      k_import_pops<__half><<<grid1(g), 256, 0, s>>>(src, (__half *)dst, mask, g, q, rho_ref, scale, shift, alpha);
       break;
     case ST_BF16:
-      k_import_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(src, (__nv_bfloat16 *)dst, mask, g, q, rho_ref, scale, shift);
+      k_import_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(src, (__nv_bfloat16 *)dst, mask, g, q, rho_ref, scale, shift, alpha);
       break;
     default:
-      k_import_pops<float><<<grid1(g), 256, 0, s>>>(src, (float *)dst, mask, g, q, rho_ref, scale, shift);
+      k_import_pops<float><<<grid1(g), 256, 0, s>>>(src, (float *)dst, mask, g, q, rho_ref, scale, shift, alpha);
   }
   return ok();
 }
 
 int launch_export_pops(int storage, const void *src, double *dst, const uint32_t *mask,
                        Geometry g, int q, float rho_ref, float inv_scale, bool shift,
-                       cudaStream_t s) {
+                       double alpha, cudaStream_t s) {
   switch (storage) {
     case ST_FP16:
-      k_export_pops<__half><<<grid1(g), 256, 0, s>>>((const __half *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+      k_export_pops<__half><<<grid1(g), 256, 0, s>>>((const __half *)src, dst, mask, g, q, rho_ref, inv_scale, shift, alpha);
       break;
     case ST_BF16:
-      k_export_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>((const __nv_bfloat16 *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+      k_export_pops<__nv_bfloat16><<<grid1(g), 256, 0, s>>>((const __nv_bfloat16 *)src, dst, mask, g, q, rho_ref, inv_scale, shift, alpha);
       break;
     default:
-      k_export_pops<float><<<grid1(g), 256, 0, s>>>((const float *)src, dst, mask, g, q, rho_ref, inv_scale, shift);
+      k_export_pops<float><<<grid1(g), 256, 0, s>>>((const float *)src, dst, mask, g, q, rho_ref, inv_scale, shift, alpha);
   }
   return ok();
 }
 
 int launch_equilibrium(int storage, const double *rho, const double *ux, const double *uy,
                        void *dst, const uint32_t *mask, Geometry g, float rho_ref,
-                       float scale, cudaStream_t s) {
+                       float scale, double alpha, cudaStream_t s) {
   switch (storage) {
     case ST_FP16:
-      k_equilibrium<__half><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__half *)dst, mask, g, rho_ref, scale);
+      k_equilibrium<__half><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__half *)dst, mask, g, rho_ref, scale, alpha);
       break;
     case ST_BF16:
-      k_equilibrium<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__nv_bfloat16 *)dst, mask, g, rho_ref, scale);
+      k_equilibrium<__nv_bfloat16><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (__nv_bfloat16 *)dst, mask, g, rho_ref, scale, alpha);
       break;
     default:
-      k_equilibrium<float><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (float *)dst, mask, g, rho_ref, scale);
+      k_equilibrium<float><<<grid1(g), 256, 0, s>>>(rho, ux, uy, (float *)dst, mask, g, rho_ref, scale, alpha);
   }
   return ok();
 }

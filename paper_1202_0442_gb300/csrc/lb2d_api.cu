@@ -66,6 +66,7 @@ struct lb_ctx {
   bool momentum_cmd = false, committed = false;
   int nx = 0, ny = 0, nc = 1;
   double tau[2] = {1, 1};
+  double alpha[2] = {4.0 / 9.0, 4.0 / 9.0};  // fluids command, density-ratio parameter
   int qs = 0;
   double taus = 1.0;
   int storage = ST_FP32;
@@ -355,7 +356,9 @@ int commit(lb_ctx *ctx) {
         double r = o.rho[c], usq = ux * ux + uy * uy;
         for (int i = 0; i < 9; i++) {
           double eu = EXD[i] * ux + EYD[i] * uy;
-          f[(size_t)i * nn + (size_t)y * g.nx + x] = W9D[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * usq);
+          f[(size_t)i * nn + (size_t)y * g.nx + x] =
+              ctx->alpha[c] == 4.0 / 9.0 ? W9D[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * usq)
+                                         : wshare(i, ctx->alpha[c]) * r + W9D[i] * r * (3 * eu + 4.5 * eu * eu - 1.5 * usq);
         }
       }
     }
@@ -390,6 +393,8 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
     a.rho_ref[c] = (float)ctx->rho_ref[c];
     a.tau[c] = (float)ctx->tau[c];
     a.omega[c] = (float)(1.0 / ctx->tau[c]);
+    a.wa[c] = (float)wshare(1, ctx->alpha[c]);
+    a.wd[c] = (float)wshare(5, ctx->alpha[c]);
     a.fx[c] = (float)ctx->fave[c][0];
     a.fy[c] = (float)ctx->fave[c][1];
     a.ax[c] = (float)ctx->acc[c][0];
@@ -634,9 +639,13 @@ int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1, double alpha
   NEED_CTX();
   TRY(paint_check(ctx));
   if (!(tau1 > 0.5) || !(tau2 > 0.5)) return ctx->fail(LB_E_ARG, "tau must exceed 1/2");
-  if (std::fabs(alpha1 - 4.0 / 9.0) > 1e-12 || std::fabs(alpha2 - 4.0 / 9.0) > 1e-12)
-    return ctx->fail(LB_E_UNSUPPORTED, "density-ratio alpha other than 4/9 is not built");
+  // c_s^2 = (3/5)(1 - alpha) must stay positive, and A_0 = (9/4) alpha
+  // must not be negative
+  if (!(alpha1 >= 0.0 && alpha1 < 1.0) || !(alpha2 >= 0.0 && alpha2 < 1.0))
+    return ctx->fail(LB_E_ARG, "alpha must lie in [0, 1)");
   ctx->nc = 2;
+  ctx->alpha[0] = alpha1;
+  ctx->alpha[1] = alpha2;
   ctx->tau[0] = tau1;
   ctx->tau[1] = tau2;
   return LB_OK;
@@ -914,7 +923,7 @@ int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho, const double *
   const size_t sb = storage_bytes(ctx->storage);
   void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
   LAUNCH(launch_equilibrium(ctx->storage, r.p, u.p, v.p, dst, ctx->mask, ctx->g,
-                            (float)ctx->rho_ref[fluid - 1], ctx->scale, ctx->stream));
+                            (float)ctx->rho_ref[fluid - 1], ctx->scale, ctx->alpha[fluid - 1], ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->state_set[fluid - 1] = true;
   return LB_OK;
@@ -949,7 +958,7 @@ int lb_set_populations(lb_ctx *ctx, int fluid, const double *f) {
   const size_t sb = storage_bytes(ctx->storage);
   void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
   LAUNCH(launch_import_pops(ctx->storage, st.p, dst, ctx->mask, ctx->g, 9, (float)ctx->rho_ref[fluid - 1],
-                            ctx->scale, true, ctx->stream));
+                            ctx->scale, true, ctx->alpha[fluid - 1], ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->state_set[fluid - 1] = true;
   return LB_OK;
@@ -965,7 +974,7 @@ int lb_set_solute_populations(lb_ctx *ctx, const double *g) {
   Stage st;
   TRY(stage_in(ctx, st, g, (size_t)ctx->qs * nn));
   LAUNCH(launch_import_pops(ST_FP32, st.p, ctx->gbuf[ctx->cur], ctx->mask, ctx->g, ctx->qs, 0.f, 1.f, false,
-                            ctx->stream));
+                            4.0 / 9.0, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->solute_set = true;
   return LB_OK;
@@ -1140,7 +1149,7 @@ int lb_get_populations(lb_ctx *ctx, int fluid, double *f) {
   const size_t sb = storage_bytes(ctx->storage);
   const void *src = (const uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
   LAUNCH(launch_export_pops(ctx->storage, src, st.p, ctx->mask, ctx->g, 9, (float)ctx->rho_ref[fluid - 1],
-                            ctx->inv_scale, true, ctx->stream));
+                            ctx->inv_scale, true, ctx->alpha[fluid - 1], ctx->stream));
   CK(cudaMemcpyAsync(f, st.p, 9 * nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return LB_OK;
@@ -1156,7 +1165,7 @@ int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b) {
     Stage st;
     TRY(stage_alloc(ctx, st, (size_t)ctx->qs * nn));
     LAUNCH(launch_export_pops(ST_FP32, ctx->gbuf[ctx->cur], st.p, ctx->mask, ctx->g, ctx->qs, 0.f, 1.f, false,
-                              ctx->stream));
+                              4.0 / 9.0, ctx->stream));
     CK(cudaMemcpyAsync(g, st.p, (size_t)ctx->qs * nn * 8, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }

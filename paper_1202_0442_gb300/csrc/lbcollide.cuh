@@ -75,7 +75,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
   for (int c = 0; c < NC; c++) {
     S *out = (S *)p.fout + (size_t)c * 9 * P;
     float heq[9];
-    equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], heq);
+    equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], p.wa[c], p.wd[c], heq);
     const float om = p.omega[c];
     if (!ME) {
       uint32_t r = p.sr_seed ? rnd(p.sr_seed, self, c, 0) : 0u;

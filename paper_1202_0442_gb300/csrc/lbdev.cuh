@@ -179,10 +179,16 @@ __device__ __forceinline__ void wall_sum(uint32_t bits, float &sx, float &sy) {
 }
 
 // ---------------------------------------------------------------------
-// Equilibrium of Eq. (2) as deviations h_eq,i = f_eq,i(rho, u) - w_i rho_ref,
-// drho = rho - rho_ref, in symmetric/antisymmetric pairs (i, opp(i)):
-//   A_i = w_i (drho + rho (9/2 (e_i.u)^2 - 3/2 u.u)),  B_i = 3 w_i rho e_i.u
+// Equilibrium of Eq. (2), generalised by the fluids command to
+// f_eq,i = w_i rho [A_i + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u] with A_0 = 9/4 alpha,
+// A_{1..8} = 9/5 (1 - alpha), as deviations h_eq,i = f_eq,i - s_i rho_ref
+// from the rest state s_i = w_i A_i (s_0 = alpha, wa = s_{1..4} =
+// (1 - alpha)/5, wd = s_{5..8} = (1 - alpha)/20; 4/9, 1/9, 1/36 at
+// alpha = 4/9), drho = rho - rho_ref, in symmetric/antisymmetric pairs
+// (i, opp(i)):
+//   A_i = s_i drho + w_i rho (9/2 (e_i.u)^2 - 3/2 u.u),  B_i = 3 w_i rho e_i.u
 //   h_eq,i = A_i + B_i,  h_eq,opp(i) = A_i - B_i
+// (sum_i s_i = 1, so h_eq,0 = drho - the other eight holds for any alpha)
 // The rounded FP32 weights would make sum h_eq and sum h_eq e miss drho and
 // rho u by a fixed relative 1e-8..1e-7, repeated by every collision (a
 // spurious force proportional to the momentum).  So the two moments are
@@ -192,10 +198,11 @@ __device__ __forceinline__ void wall_sum(uint32_t bits, float &sx, float &sy) {
 // Output slots: heq[0..8] in direction order.
 // ---------------------------------------------------------------------
 __device__ __forceinline__ void equilibrium_pairs(float drho, float rho, float ux, float uy,
-                                                  float mx, float my, float (&heq)[9]) {
+                                                  float mx, float my, float wa, float wd,
+                                                  float (&heq)[9]) {
   const float q = rho * (ux * ux + uy * uy);
   const float sp = ux + uy, sm = uy - ux;  // e5.u and e6.u
-  const float d9 = drho * (1.0f / 9.0f), d36 = drho * (1.0f / 36.0f);
+  const float d9 = drho * wa, d36 = drho * wd;
   const float A1 = d9 + 0.5f * rho * ux * ux - q * (1.0f / 6.0f);
   const float A2 = d9 + 0.5f * rho * uy * uy - q * (1.0f / 6.0f);
   const float A5 = d36 + 0.125f * rho * sp * sp - q * (1.0f / 24.0f);

@@ -36,6 +36,16 @@ struct Geometry {
 };
 
 // one iteration of the fluid lattice(s)
+// rest-state share s_i = w_i A_i of population i under the fluids
+// command's density-ratio parameter alpha (Eq. (2) weights at alpha = 4/9)
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline double wshare(int i, double alpha) {
+  if (alpha == 4.0 / 9.0) return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  return i == 0 ? alpha : (i < 5 ? (1.0 - alpha) / 5.0 : (1.0 - alpha) / 20.0);
+}
+
 struct FluidArgs {
   Geometry g;
   const void *fin;        // populations before the step [nc][9][plane]
@@ -44,6 +54,7 @@ struct FluidArgs {
   float rho_ref[2];
   float scale, inv_scale; // storage scale 2^s and 2^-s (FP16), else 1
   float tau[2], omega[2];
+  float wa[2], wd[2];     // rest-state shares s_1..4, s_5..8 (fluids alpha)
   float fx[2], fy[2];     // aveforce
   float ax[2], ay[2];     // aveacceleration
   int ads[2];             // adhesiveforce on/off per component
@@ -138,13 +149,13 @@ int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s);
 // state conversion between FP64 host-layout arrays [q][ny][nx] and storage
 int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,
                        Geometry g, int q, float rho_ref, float scale, bool shift,
-                       cudaStream_t s);
+                       double alpha, cudaStream_t s);
 int launch_export_pops(int storage, const void *src, double *dst, const uint32_t *mask,
                        Geometry g, int q, float rho_ref, float inv_scale, bool shift,
-                       cudaStream_t s);
+                       double alpha, cudaStream_t s);
 int launch_equilibrium(int storage, const double *rho, const double *ux, const double *uy,
                        void *dst, const uint32_t *mask, Geometry g, float rho_ref,
-                       float scale, cudaStream_t s);
+                       float scale, double alpha, cudaStream_t s);
 int launch_solute_equilibrium(int q, const double *C, const double *ux, const double *uy,
                               float *dst, const uint32_t *mask, Geometry g, cudaStream_t s);
 int launch_export_fields(const float *fields, int comp, const uint32_t *mask, Geometry g,

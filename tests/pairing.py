@@ -8,8 +8,8 @@ from paper_1202_0442_gb300 import lb2d
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
 
-def run_pair(w, steps, storage="fp32", h_max=0.0, thermo=0, oracle_steps=None):
-    lt = lb2d.from_workload(w, storage, h_max=h_max, thermo=thermo)
+def run_pair(w, steps, storage="fp32", h_max=0.0, thermo=0, oracle_steps=None, **kw):
+    lt = lb2d.from_workload(w, storage, h_max=h_max, thermo=thermo, **kw)
     o = oracle_from_workload(w)
     if steps:
         lt.iteration(steps)

@@ -504,6 +504,71 @@ def test_two_component_sc_flat_interface():
     assert abs(th["mass2"] - r2.sum()) / r2.sum() < 1e-12
 
 
+@pytest.mark.parametrize("alpha", [4.0 / 9.0, 0.8, 0.0])
+def test_density_ratio_sound_speed(alpha):
+    """fluids command: a component with parameter alpha has sound speed
+    c_s^2 = (3/5)(1 - alpha).  Two non-interacting components with the same
+    alpha carry a small standing density wave in a periodic box; its
+    oscillation frequency must be c_s k (lattice dispersion and damping
+    shift it by well under 1 % at k = 2 pi / 64)."""
+    nx, ny, eps = 64, 2, 1e-4
+    o = Oracle(nx, ny, 2)
+    for s in range(2):
+        o.set_tau(0.6, s)
+        o.set_alpha(alpha, s)
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    r = np.broadcast_to(0.5 * (1 + eps * np.cos(k * x)), (ny, nx))
+    o.set_equilibrium(r, comp=0)
+    o.set_equilibrium(r, comp=1)
+    cs = np.sqrt(0.6 * (1 - alpha))
+    period = 2 * np.pi / (cs * k)
+    amp = []
+    for _ in range(int(2.6 * period)):
+        o.step()
+        rho = o.fields(0)[0] + o.fields(1)[0]
+        amp.append(np.sum(rho[0] * np.cos(k * x)))
+    a = np.array(amp)
+    t = np.arange(1, len(a) + 1, dtype=float)
+    zc = [t[i] - a[i] * (t[i + 1] - t[i]) / (a[i + 1] - a[i])
+          for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
+    assert len(zc) >= 4
+    half = np.mean(np.diff(zc))
+    assert abs(2 * half / period - 1) < 1e-2, (2 * half, period)
+    th = o.thermo()
+    assert abs(th["mass1"] - r.sum()) / r.sum() < 1e-12
+
+
+def test_density_ratio_interface_pressure():
+    """Two components with alpha = 4/9 and 0.8 (an example of the fluids
+    command) separated by interforce: in mechanical equilibrium the
+    pressure rho1 c1^2 + rho2 c2^2 + G rho1 rho2 / 3, with each component's
+    own c_s^2 = (3/5)(1 - alpha), is the same in both bulk phases; with
+    c2^2 = 1/3 it is not (the phases differ in rho2 by a factor > 10)."""
+    nx, ny, G = 128, 4, 1.0
+    o = Oracle(nx, ny, 2)
+    o.set_alpha(4.0 / 9.0, 0)
+    o.set_alpha(0.8, 1)
+    o.set_interforce(G)
+    x = np.arange(nx)
+    one = (x > nx // 4) & (x < 3 * nx // 4)
+    r1 = np.broadcast_to(np.where(one, 1.0, 0.05), (ny, nx))
+    r2 = np.broadcast_to(np.where(one, 0.05, 1.0), (ny, nx))
+    o.set_equilibrium(r1, comp=0)
+    o.set_equilibrium(r2, comp=1)
+    o.step(16000)
+    a, b = o.fields(0)[0][0], o.fields(1)[0][0]
+    c1, c2 = 0.6 * (1 - 4.0 / 9.0), 0.6 * (1 - 0.8)
+    p = a * c1 + b * c2 + G * a * b / 3
+    assert a[nx // 2] / a[2] > 10 and b[2] / b[nx // 2] > 10
+    assert abs(p[nx // 2] - p[2]) / p[2] < 1e-4, (p[nx // 2], p[2])
+    q = (a + b) / 3 + G * a * b / 3
+    assert abs(q[nx // 2] - q[2]) / q[2] > 1e-1
+    th = o.thermo()
+    # FP64 rounding over 16000 steps: about 1e-12
+    assert abs(th["mass2"] - r2.sum()) / r2.sum() < 1e-11
+
+
 def test_sc_force_is_cohesive_for_negative_G():
     """A single dense node in a uniform field: with G < 0 (cohesive, Sec.
     Phase separation) its neighbours are pulled toward it; G > 0 pushes.
