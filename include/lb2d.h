@@ -163,14 +163,20 @@ int lb_inlet_momentum(lb_ctx *ctx, const char *label, const char *style,
 int lb_outlet_momentum(lb_ctx *ctx, const char *label, const char *style,
                        double v, double rho);
 
-/* inlet_solute/outlet_solute commands (App. B): "dirichlet" (C held at C)
- * or "adiabatic" (zero flux; C is the initial value).  "flux" gives
- * LB_E_UNSUPPORTED.  Every opening needs a solute style when a solute is
- * on. */
+/* inlet_solute/outlet_solute commands (App. B): "dirichlet" (C held at C),
+ * "adiabatic" (zero flux; C is the initial value) or "flux" (C is the
+ * injected concentration C0, v its velocity: after streaming the opening
+ * node takes C = (v C0 + D C1)/(D + v) on an inlet, (v C0 - D C1)/(v - D)
+ * on an outlet, C1 the streamed concentration of the nearest inner node,
+ * D = (tau_s - 1/2)/2 on D2Q4 or /3 on D2Q9, and every mode is set to
+ * g_eq(C, u); v = D on an outlet is LB_E_ARG at the first iteration).  v
+ * is ignored by the other styles.  Every opening needs a solute style when
+ * a solute is on; an opening with a solute style but no momentum style
+ * leaves the fluid periodic across its wall. */
 int lb_inlet_solute(lb_ctx *ctx, const char *label, const char *style,
-                    double C);
+                    double C, double v);
 int lb_outlet_solute(lb_ctx *ctx, const char *label, const char *style,
-                     double C);
+                     double C, double v);
 
 /* surface_reaction command: rate kr >= 0, saturation Cs, style "growth",
  * initial deposit b0 on every solid node, growth threshold bmax.  seed
@@ -232,6 +238,14 @@ int lb_interforce(lb_ctx *ctx, double G, double psi0, double rho0);
  * psi = rho_fluid. */
 int lb_adhesiveforce(lb_ctx *ctx, double G, double psi0, double rho0,
                      int fluid);
+
+/* intersolute command: interfaces for the solute.  The solute collision
+ * relaxes to g_eq(C, u + tau_s F / C) with F = -G psi(x) sum_{i=1..4}
+ * psi(x + e_i) e_i over the D2Q4 neighbours, psi = psi0 exp(-C0 / C) of
+ * the concentrations after this step's streaming and opening rules (0 on
+ * solid nodes and where C <= 0).  Needs lb_solute; adds one pass over the
+ * solute lattice per iteration. */
+int lb_intersolute(lb_ctx *ctx, double G, double psi0, double C0);
 
 /* ---- output and action ----------------------------------------------- */
 

@@ -33,13 +33,16 @@ def oracle_from_workload(w, solute_q=None) -> Oracle:
         for s, (style, v, rho) in enumerate(op.momentum):
             o.set_opening_momentum(k, style, v, rho, s)
         if op.solute is not None and q:
-            o.set_opening_solute(k, op.solute[0], op.solute[1])
+            v = op.solute[2] if len(op.solute) > 2 else 0.0
+            o.set_opening_solute(k, op.solute[0], op.solute[1], v)
     ux = 0.0 if w.ux is None else w.ux
     uy = 0.0 if w.uy is None else w.uy
     for s in range(w.ncomp):
         o.set_equilibrium(w.rho[s], ux, uy, s)
     if q:
         o.set_taus(w.taus)
+        if getattr(w, "intersolute", None) is not None:
+            o.set_intersolute(*w.intersolute)
         C = np.zeros((w.ny, w.nx)) if w.C is None else w.C
         o.set_solute_equilibrium(C, ux, uy)
         if w.reaction is not None:

@@ -25,7 +25,9 @@
  *      command)
  *   9. solute on D2Q4 (solute command, Eq. (3)) or D2Q9: streaming,
  *      bounce-back or surface reaction (surface_reaction command, App. C),
- *      inlet_solute/outlet_solute rules (App. B), BGK collision
+ *      inlet_solute/outlet_solute rules (dirichlet, adiabatic, flux;
+ *      App. B), BGK collision, with the intersolute force in the
+ *      equilibrium velocity
  *  10. precipitation after collision and 11. surface growth
  *      (surface_reaction command, App. C)
  *  12. thermo sums over the final state (thermo command)
@@ -51,6 +53,10 @@
  *   - precipitation dB = kr (C_w - Cs) if > 0, taken in equal parts from
  *     the incoming modes after collision and credited in equal parts to
  *     the solid nodes behind them.
+ *   - solute flux openings: C1 is the inner neighbour's concentration
+ *     right after streaming (before its own opening rule); intersolute
+ *     uses the concentrations after streaming and the opening rules of the
+ *     same step, psi = 0 on solid nodes and where C <= 0.
  *   - growth: a solid node with b > bmax turns one fluid 4-neighbour (not
  *     an opening node) to solid; the choice is SplitMix64(seed ^ (t*nx*ny
  *     + node)) mod (number of candidates), candidates in the order
@@ -84,7 +90,7 @@ typedef struct {
   int style[2];
   double v[2], rho[2];
   int sstyle;
-  double Cbar;
+  double Cbar, sv;
 } opening_t;
 
 struct orc {
@@ -104,6 +110,9 @@ struct orc {
   opening_t op[MAXOPEN];
   int *open_id;
   double *g, *gt, *C, *b, *db, *Cw;
+  double *Cst, *Cpre; /* solute: C after streaming; after the opening rules */
+  int is_on;          /* intersolute */
+  double isG, ispsi0, isC0;
   int *nU, *Ubits;
   int react_on;
   double kr, Cs, b0, bmax;
@@ -157,6 +166,8 @@ orc_t *orc_create(int nx, int ny, int ncomp, int solute_q) {
     o->C = (double *)calloc(nn, sizeof(double));
     o->db = (double *)calloc(nn, sizeof(double));
     o->Cw = (double *)calloc(nn, sizeof(double));
+    o->Cst = (double *)calloc(nn, sizeof(double));
+    o->Cpre = (double *)calloc(nn, sizeof(double));
     o->nU = (int *)calloc(nn, sizeof(int));
     o->Ubits = (int *)calloc(nn, sizeof(int));
   }
@@ -173,6 +184,7 @@ void orc_destroy(orc_t *o) {
   }
   free(o->g); free(o->gt); free(o->C); free(o->db); free(o->b);
   free(o->Cw); free(o->nU); free(o->Ubits);
+  free(o->Cst); free(o->Cpre);
   free(o->solid); free(o->open_id); free(o->flip);
   free(o);
 }
@@ -284,6 +296,19 @@ int orc_set_equilibrium(orc_t *o, int comp, const double *rho,
 /* Eq. (3) on D2Q4: g_i^eq = C/4 [1 + 2 e_i.u]; on D2Q9 the same linear
  * advection-diffusion equilibrium with the D2Q9 weights and c_s^2 = 1/3:
  * g_i^eq = w_i C [1 + 3 e_i.u]. */
+/* solvent velocity of Eq. (4) at node n: sum of the physical momenta
+ * (j + F/2) over the sum of the densities of the fluid components */
+static void solvent_velocity(const orc_t *o, size_t n, double *u) {
+  double rs = 0.0, pxs = 0.0, pys = 0.0;
+  for (int s = 0; s < o->nc; s++) {
+    rs += o->rho[s][n];
+    pxs += o->px[s][n];
+    pys += o->py[s][n];
+  }
+  u[0] = pxs / rs;
+  u[1] = pys / rs;
+}
+
 static void solute_geq(int q, double C, double ux, double uy, double *geq) {
   if (q == 4) {
     for (int i = 0; i < 4; i++)
@@ -389,10 +414,21 @@ int orc_set_opening_momentum(orc_t *o, int opening, int comp, int style,
   return 0;
 }
 
-int orc_set_opening_solute(orc_t *o, int opening, int style, double Cbar) {
+int orc_set_opening_solute(orc_t *o, int opening, int style, double Cbar,
+                           double v) {
   if (opening < 0 || opening >= o->nopen) return -1;
   o->op[opening].sstyle = style;
   o->op[opening].Cbar = Cbar;
+  o->op[opening].sv = v;
+  return 0;
+}
+
+int orc_set_intersolute(orc_t *o, double G, double psi0, double C0) {
+  if (!o->qs) return -1;
+  o->is_on = 1;
+  o->isG = G;
+  o->ispsi0 = psi0;
+  o->isC0 = C0;
   return 0;
 }
 
@@ -829,26 +865,28 @@ int orc_step(orc_t *o) {
             gt[i] = o->g[ns * q + i];
           }
         }
+        double Cs = 0.0;
+        for (int i = 0; i < q; i++) Cs += gt[i];
+        o->Cst[n] = Cs;
       }
 
-    /* 9b. inlet_solute/outlet_solute rules (App. B), then the collision
-     * with g^eq(C, u), u the solvent velocity of Eq. (4) */
+    /* 9b. inlet_solute/outlet_solute rules (App. B) on the opening nodes,
+     * then the node concentrations that enter the collision */
+    const double Dsol = (o->taus - 0.5) / (q == 4 ? 2.0 : 3.0);
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
         size_t n = (size_t)y * nx + x;
         double *gt = &o->gt[n * q];
-        o->db[n] = 0.0;
-        if (o->solid[n]) {
-          for (int i = 0; i < q; i++) o->g[n * q + i] = 0.0;
-          o->C[n] = 0.0;
-          continue;
-        }
+        o->Cpre[n] = 0.0;
+        if (o->solid[n]) continue;
         int id = o->open_id[n];
         const opening_t *p = (id >= 0) ? &o->op[id] : NULL;
         if (p) {
           /* dirichlet sets the crossing modes so that C = Cbar (split by
            * weight when several modes cross); adiabatic reflects the
-           * opposite mode */
+           * opposite mode; flux balances v C0 against the advective and
+           * diffusive flux to the nearest inner node and puts every mode
+           * at equilibrium */
           if (p->sstyle == ORC_S_DIRICHLET) {
             double Cp = 0.0, wsum = 0.0;
             for (int i = 0; i < q; i++) {
@@ -861,16 +899,63 @@ int orc_step(orc_t *o) {
           } else if (p->sstyle == ORC_S_ADIABATIC) {
             for (int i = 0; i < q; i++)
               if (crosses(p->wall, EX[i], EY[i])) gt[i] = gt[OPP[i]];
+          } else if (p->sstyle == ORC_S_FLUX) {
+            /* inward normal of the wall: xlo +x, xhi -x, ylo +y, yhi -y */
+            static const int NXW[4] = {1, -1, 0, 0}, NYW[4] = {0, 0, 1, -1};
+            size_t ni = (size_t)wrap(y + NYW[p->wall], ny) * nx +
+                        wrap(x + NXW[p->wall], nx);
+            double C1 = o->solid[ni] ? 0.0 : o->Cst[ni];
+            double v = p->sv, C0 = p->Cbar, Cf;
+            if (p->kind == ORC_INLET)
+              Cf = (v * C0 + Dsol * C1) / (Dsol + v);
+            else
+              Cf = (v * C0 - Dsol * C1) / (v - Dsol);
+            double u[2];
+            solvent_velocity(o, n, u);
+            double geq[9];
+            solute_geq(q, Cf, u[0], u[1], geq);
+            for (int i = 0; i < q; i++) gt[i] = geq[i];
           }
         }
-        double C = 0.0, rs = 0.0, pxs = 0.0, pys = 0.0;
+        double C = 0.0;
         for (int i = 0; i < q; i++) C += gt[i];
-        for (int s = 0; s < nc; s++) {
-          rs += o->rho[s][n];
-          pxs += o->px[s][n];
-          pys += o->py[s][n];
+        o->Cpre[n] = C;
+      }
+
+    /* 9c. collision with g^eq(C, u_s), u the solvent velocity of Eq. (4);
+     * with intersolute u_s = u + taus F / C, F = -G psi(x) sum_{i=1..4}
+     * psi(x + e_i) e_i over the D2Q4 neighbours, psi = psi0 exp(-C0/C)
+     * from the concentrations of this step (0 on solid nodes and where
+     * C <= 0) */
+    for (int y = 0; y < ny; y++)
+      for (int x = 0; x < nx; x++) {
+        size_t n = (size_t)y * nx + x;
+        double *gt = &o->gt[n * q];
+        o->db[n] = 0.0;
+        if (o->solid[n]) {
+          for (int i = 0; i < q; i++) o->g[n * q + i] = 0.0;
+          o->C[n] = 0.0;
+          continue;
         }
-        double ux = pxs / rs, uy = pys / rs;
+        double C = o->Cpre[n];
+        double u[2];
+        solvent_velocity(o, n, u);
+        double ux = u[0], uy = u[1];
+        if (o->is_on && C > 0.0) {
+          double Fx = 0.0, Fy = 0.0;
+          for (int d = 0; d < 4; d++) {
+            size_t nb = (size_t)wrap(y + EY4[d], ny) * nx + wrap(x + EX4[d], nx);
+            double Cn = o->Cpre[nb];
+            double psin = (o->solid[nb] || !(Cn > 0.0)) ? 0.0 : o->ispsi0 * exp(-o->isC0 / Cn);
+            Fx += psin * EX4[d];
+            Fy += psin * EY4[d];
+          }
+          double psi = o->ispsi0 * exp(-o->isC0 / C);
+          Fx *= -o->isG * psi;
+          Fy *= -o->isG * psi;
+          ux += o->taus * Fx / C;
+          uy += o->taus * Fy / C;
+        }
         double geq[9];
         solute_geq(q, C, ux, uy, geq);
         for (int i = 0; i < q; i++)

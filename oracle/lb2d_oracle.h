@@ -33,7 +33,7 @@ enum { ORC_INLET = 0, ORC_OUTLET = 1 };
 enum { ORC_M_NONE = 0, ORC_M_POISEUILLE = 1, ORC_M_UNIFORM = 2,
        ORC_M_DIRICHLET = 3, ORC_M_GRADIENT = 4 };
 /* inlet_solute/outlet_solute styles */
-enum { ORC_S_NONE = 0, ORC_S_DIRICHLET = 1, ORC_S_ADIABATIC = 2 };
+enum { ORC_S_NONE = 0, ORC_S_DIRICHLET = 1, ORC_S_ADIABATIC = 2, ORC_S_FLUX = 3 };
 
 /* thermo record (thermo command), all sums in FP64 over the state at the
  * end of the last iteration */
@@ -76,7 +76,12 @@ int orc_set_adhesiveforce(orc_t *o, int comp, double G, double psi0,
 int orc_add_opening(orc_t *o, int wall, int a0, int a1, int kind);
 int orc_set_opening_momentum(orc_t *o, int opening, int comp, int style,
                              double v, double rho);
-int orc_set_opening_solute(orc_t *o, int opening, int style, double Cbar);
+/* Cbar: dirichlet concentration, or C0 of the flux style; v: the flux
+ * style's velocity (ignored by the others) */
+int orc_set_opening_solute(orc_t *o, int opening, int style, double Cbar,
+                           double v);
+/* intersolute command: G, psi0, C0 */
+int orc_set_intersolute(orc_t *o, double G, double psi0, double C0);
 
 int orc_set_reaction(orc_t *o, double kr, double Cs, double b0,
                      double bmax, uint64_t seed);

@@ -25,11 +25,11 @@ _LIB = os.path.join(_OUT_DIR, "liblb2d_oracle.so")
 XLO, XHI, YLO, YHI = 0, 1, 2, 3
 INLET, OUTLET = 0, 1
 M_NONE, M_POISEUILLE, M_UNIFORM, M_DIRICHLET, M_GRADIENT = 0, 1, 2, 3, 4
-S_NONE, S_DIRICHLET, S_ADIABATIC = 0, 1, 2
+S_NONE, S_DIRICHLET, S_ADIABATIC, S_FLUX = 0, 1, 2, 3
 WALLS = {"xlo": XLO, "xhi": XHI, "ylo": YLO, "yhi": YHI}
 MSTYLES = {"poiseuille": M_POISEUILLE, "uniform": M_UNIFORM,
            "dirichlet": M_DIRICHLET, "gradient": M_GRADIENT}
-SSTYLES = {"dirichlet": S_DIRICHLET, "adiabatic": S_ADIABATIC}
+SSTYLES = {"dirichlet": S_DIRICHLET, "adiabatic": S_ADIABATIC, "flux": S_FLUX}
 
 THERMO_KEYS = ["mass1", "mass2", "momx", "momy", "mass_eq1", "mass_eq2",
                "solute", "bsum", "removed1", "removed2", "removed_solute",
@@ -82,7 +82,8 @@ def _load():
         "orc_set_adhesiveforce": (I, [P, I, D, D, D]),
         "orc_add_opening": (I, [P, I, I, I, I]),
         "orc_set_opening_momentum": (I, [P, I, I, I, D, D]),
-        "orc_set_opening_solute": (I, [P, I, I, D]),
+        "orc_set_opening_solute": (I, [P, I, I, D, D]),
+        "orc_set_intersolute": (I, [P, D, D, D]),
         "orc_set_reaction": (I, [P, D, D, D, D, U64]),
         "orc_step": (I, [P]),
         "orc_time": (C.c_long, [P]),
@@ -220,9 +221,14 @@ class Oracle:
                                                 MSTYLES[style], v, rho),
                "opening momentum")
 
-    def set_opening_solute(self, opening: int, style: str, Cbar: float = 0.0):
+    def set_opening_solute(self, opening: int, style: str, Cbar: float = 0.0, v: float = 0.0):
+        """Cbar: dirichlet concentration or the flux style's C0; v: the flux
+        style's velocity."""
         _check(self._l.orc_set_opening_solute(self._h, opening, SSTYLES[style],
-                                              Cbar), "opening solute")
+                                              Cbar, v), "opening solute")
+
+    def set_intersolute(self, G: float, psi0: float, C0: float):
+        _check(self._l.orc_set_intersolute(self._h, G, psi0, C0), "intersolute")
 
     def set_reaction(self, kr: float, Cs: float, b0: float, bmax: float,
                      seed: int):

@@ -80,21 +80,36 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
       }
     }
   }
-  double acc[NTHERMO];
-#pragma unroll
-  for (int q = 0; q < 9; q++) acc[q] = (double)hi[q] + (double)lo[q];
-#pragma unroll
-  for (int q = 0; q < 4; q++) acc[9 + q] = dacc[q];
-  acc[13] = (double)nsolid;
-  acc[14] = (double)nfluid;
-#pragma unroll
-  for (int q = 15; q < NTHERMO; q++) acc[q] = 0.0;
-  __shared__ double sm[TB / 32][NTHERMO];
+  // warp: the FP32 pairs with error-free additions, the counts in
+  // integers; FP64 shuffles only for the FP64 arrays of reaction runs
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < NTHERMO; q++) {
-    const double v = warp_sum(acc[q]);
-    if (lane == 0) sm[w][q] = v;
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi[q], o);
+      const float ol = __shfl_down_sync(0xffffffffu, lo[q], o);
+      const float l = lo[q] + ol;
+      lo[q] = l;
+      pair_add(hi[q], lo[q], oh);
+    }
+  }
+  nsolid = __reduce_add_sync(0xffffffffu, nsolid);
+  nfluid = __reduce_add_sync(0xffffffffu, nfluid);
+  if (a.b || a.removed) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) dacc[q] = warp_sum(dacc[q]);
+  }
+  __shared__ double sm[TB / 32][NTHERMO];
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) sm[w][q] = (double)hi[q] + (double)lo[q];
+#pragma unroll
+    for (int q = 0; q < 4; q++) sm[w][9 + q] = dacc[q];
+    sm[w][13] = (double)nsolid;
+    sm[w][14] = (double)nfluid;
+#pragma unroll
+    for (int q = 15; q < NTHERMO; q++) sm[w][q] = 0.0;
   }
   __syncthreads();
   if (threadIdx.x < NTHERMO) {
@@ -105,12 +120,21 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
 }
 
 // one warp per quantity: lanes stride over the blocks' partial sums in a
-// fixed order, then a shuffle tree
+// fixed order (four independent chains, so the loads overlap), then a
+// shuffle tree
 __global__ void __launch_bounds__(32 * NTHERMO) k_thermo_final(const double *partials, int nblocks,
                                                                double *out) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double v = 0.0;
-  for (int k = lane; k < nblocks; k += 32) v += partials[(size_t)k * NTHERMO + q];
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+  int k = lane;
+  for (; k + 96 < nblocks; k += 128) {
+    v0 += partials[(size_t)k * NTHERMO + q];
+    v1 += partials[(size_t)(k + 32) * NTHERMO + q];
+    v2 += partials[(size_t)(k + 64) * NTHERMO + q];
+    v3 += partials[(size_t)(k + 96) * NTHERMO + q];
+  }
+  for (; k < nblocks; k += 32) v0 += partials[(size_t)k * NTHERMO + q];
+  double v = (v0 + v1) + (v2 + v3);
   v = warp_sum(v);
   if (lane == 0) out[q] = v;
 }

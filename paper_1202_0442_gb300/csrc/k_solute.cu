@@ -7,11 +7,16 @@
 //     C_i = (2 g_out + kr Cs)/(kr + 2 w_i),  g_in = -g_out + 2 w_i C_i
 //   (w_i = 1/4 on D2Q4 is the printed rule); the inlet_solute/outlet_solute
 //   rules (dirichlet: the crossing modes make C = Cbar, split by weight;
-//   adiabatic: crossing mode = opposite mode, App. B); BGK with
-//   g_eq(C, u), u the solvent velocity of Eq. (4) written by the fluid
-//   kernel in the same iteration; then precipitation dB = kr (C_w - Cs) if
-//   positive, taken in equal parts from the incoming modes, the share
-//   dB/|U| recorded for the solid neighbours.
+//   adiabatic: crossing mode = opposite mode; flux: C from the flux balance
+//   with the nearest inner node, all modes at equilibrium; App. B); BGK
+//   with g_eq(C, u_s), u the solvent velocity of Eq. (4) written by the
+//   fluid kernel in the same iteration, u_s = u + tau_s F / C with the
+//   intersolute force F (else u_s = u); then precipitation
+//   dB = kr (C_w - Cs) if positive, taken in equal parts from the incoming
+//   modes, the share dB/|U| recorded for the solid neighbours.
+// k_solute_pre<Q>: with intersolute, a first pass that writes every node's
+//   concentration after streaming and the opening rules, so the update can
+//   read its neighbours' psi of the same step.
 // k_gather_grow: every solid node adds its fluid neighbours' shares to its
 //   FP64 deposit b in a fixed order, and, if b > bmax, picks one fluid
 //   4-neighbour (SplitMix64 of seed ^ (t nx ny + node) mod the number of
@@ -44,20 +49,19 @@ __device__ __forceinline__ int opening_of(const OpenDesc *op, int nopen, int x, 
   return -1;
 }
 
+// Streamed populations of node (x, y): pull from x - e_i; at a solid source
+// bounce-back, or the reaction rule on that link (then Ci is added to Cw,
+// the link counted in nU and flagged in U).  Modes crossing the wall of an
+// opening node (wall >= 0) are left 0 and flagged in `cross`.
 template <int Q>
-__global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void solute_pull(const SoluteArgs &p, int x, int y, int wall, float (&gt)[Q],
+                                            float &Cw, int &nU, uint32_t &U, uint32_t &cross) {
   const Geometry &g = p.g;
-  if (x >= g.nx || y >= g.ny) return;
-  if (solid_at(p.mask, g.mw, x, y)) return;
   const size_t self = (size_t)y * g.pitch + x;
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
-  const int wall = k >= 0 ? p.op[k].wall : -1;
-  float gt[Q];
-  float Cw = 0.f;
-  int nU = 0;
-  uint32_t U = 0, cross = 0;
+  Cw = 0.f;
+  nU = 0;
+  U = 0;
+  cross = 0;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     if (wall >= 0 && crosses_wall(wall, sex<Q>(i), sey<Q>(i))) {
@@ -81,31 +85,64 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
       gt[i] = __ldg(p.gin + (size_t)i * g.plane + (size_t)ys * g.pitch + xs);
     }
   }
-  if (k >= 0) {
-    const OpenDesc &o = p.op[k];
-    if (o.sstyle == SOL_DIRICHLET) {
-      float Cp = 0.f, ws = 0.f;
-#pragma unroll
-      for (int i = 0; i < Q; i++) {
-        if (cross & (1u << i)) ws += sw<Q>(i);
-        else Cp += gt[i];
-      }
-      const float r = (o.Cbar - Cp) / ws;
-#pragma unroll
-      for (int i = 0; i < Q; i++)
-        if (cross & (1u << i)) gt[i] = r * sw<Q>(i);
-    } else if (o.sstyle == SOL_ADIABATIC) {
-#pragma unroll
-      for (int i = 0; i < Q; i++)
-        if (cross & (1u << i)) gt[i] = gt[sopp<Q>(i)];
-    }
-  }
+}
+
+// concentration of node (x, y) right after streaming, before any opening
+// rule (0 on solid nodes): the C1 of the flux rule
+template <int Q>
+__device__ float solute_streamed_C(const SoluteArgs &p, int x, int y) {
+  const Geometry &g = p.g;
+  if (solid_at(p.mask, g.mw, x, y)) return 0.f;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  float gt[Q], Cw;
+  int nU;
+  uint32_t U, cross;
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
   float C = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; i++) C += gt[i];
-  const float ux = __ldg(p.u + self), uy = __ldg(p.u + g.plane + self);
-  const float om = p.omega;
-  float geq[Q];
+  return C;
+}
+
+// inlet_solute/outlet_solute rules (App. B) on an opening node.
+// dirichlet: the crossing modes make C = Cbar (split by weight); adiabatic:
+// crossing mode = opposite mode; flux: C from the flux balance with the
+// nearest inner node, C = (v C0 + D C1)/(D + v) (inlet) or
+// (v C0 - D C1)/(v - D) (outlet), every mode then at equilibrium (the
+// caller sets them; returns true and the C to use).
+template <int Q>
+__device__ __forceinline__ bool solute_openings(const SoluteArgs &p, const OpenDesc &o, int x, int y,
+                                                float (&gt)[Q], uint32_t cross, float &Cflux) {
+  if (o.sstyle == SOL_DIRICHLET) {
+    float Cp = 0.f, ws = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if (cross & (1u << i)) ws += sw<Q>(i);
+      else Cp += gt[i];
+    }
+    const float r = (o.Cbar - Cp) / ws;
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      if (cross & (1u << i)) gt[i] = r * sw<Q>(i);
+  } else if (o.sstyle == SOL_ADIABATIC) {
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      if (cross & (1u << i)) gt[i] = gt[sopp<Q>(i)];
+  } else if (o.sstyle == SOL_FLUX) {
+    // inward normal: xlo +x, xhi -x, ylo +y, yhi -y
+    const int xi = wrapi(x + (o.wall == 0 ? 1 : o.wall == 1 ? -1 : 0), p.g.nx);
+    const int yi = wrapi(y + (o.wall == 2 ? 1 : o.wall == 3 ? -1 : 0), p.g.ny);
+    const float C1 = solute_streamed_C<Q>(p, xi, yi);
+    const float v = o.sv, C0 = o.Cbar, D = p.D;
+    Cflux = (o.kind == 0) ? (v * C0 + D * C1) / (D + v) : (v * C0 - D * C1) / (v - D);
+    return true;
+  }
+  return false;
+}
+
+// g_eq(C, u) of Eq. (3) (D2Q4) or w_i C (1 + 3 e.u) (D2Q9)
+template <int Q>
+__device__ __forceinline__ void solute_geq(float C, float ux, float uy, float (&geq)[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const float eu = (float)sex<Q>(i) * ux + (float)sey<Q>(i) * uy;
@@ -113,7 +150,7 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   }
   if (Q == 9) {
     // the rounded D2Q9 weights would bias sum g_eq and sum g_eq e (see
-    // equilibrium_exact); restore C and C u
+    // equilibrium_pairs); restore C and C u
     const float mx = geq[1] - geq[3] + geq[5] - geq[6] - geq[7] + geq[8];
     const float my = geq[2] - geq[4] + geq[5] + geq[6] - geq[7] - geq[8];
     const float cx = 0.5f * (C * ux - mx), cy = 0.5f * (C * uy - my);
@@ -125,6 +162,85 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
 #pragma unroll
     for (int i = 1; i < Q; i++) m += geq[i];
     geq[0] = C - m;
+  }
+}
+
+// intersolute pseudopotential psi = psi0 exp(-C0/C); 0 on solid nodes and
+// where C <= 0
+__device__ __forceinline__ float solute_psi(const SoluteArgs &p, float C) {
+  return C > 0.f ? p.ispsi0 * expf(-p.isC0 / C) : 0.f;
+}
+
+// first pass of an intersolute iteration: every node's concentration after
+// streaming and the opening rules (the C its collision will use)
+template <int Q>
+__global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geometry &g = p.g;
+  if (x >= g.nx || y >= g.ny) return;
+  const size_t self = (size_t)y * g.pitch + x;
+  if (solid_at(p.mask, g.mw, x, y)) {
+    p.Cpre_out[self] = 0.f;
+    return;
+  }
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  float gt[Q], Cw, Cflux = 0.f;
+  int nU;
+  uint32_t U, cross;
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
+  bool flux = false;
+  if (k >= 0) flux = solute_openings<Q>(p, p.op[k], x, y, gt, cross, Cflux);
+  float C = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) C += gt[i];
+  p.Cpre_out[self] = flux ? Cflux : C;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geometry &g = p.g;
+  if (x >= g.nx || y >= g.ny) return;
+  if (solid_at(p.mask, g.mw, x, y)) return;
+  const size_t self = (size_t)y * g.pitch + x;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  float gt[Q], Cw, Cflux = 0.f;
+  int nU;
+  uint32_t U, cross;
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
+  bool flux = false;
+  if (k >= 0) flux = solute_openings<Q>(p, p.op[k], x, y, gt, cross, Cflux);
+  float C = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) C += gt[i];
+  if (flux) C = Cflux;
+  float ux = __ldg(p.u + self), uy = __ldg(p.u + g.plane + self);
+  if (p.inter && C > 0.f) {
+    // intersolute: u_s = u + tau_s F / C, F = -G psi(x) sum_{i=1..4}
+    // psi(x + e_i) e_i over the D2Q4 neighbours (their concentrations of
+    // this step, from the first pass)
+    float Fx = 0.f, Fy = 0.f;
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      const int xn = wrapi(x + EX4(d), g.nx), yn = wrapi(y + EY4(d), g.ny);
+      const float psin = solid_at(p.mask, g.mw, xn, yn)
+                             ? 0.f
+                             : solute_psi(p, __ldg(p.Cpre + (size_t)yn * g.pitch + xn));
+      Fx += psin * (float)EX4(d);
+      Fy += psin * (float)EY4(d);
+    }
+    const float f = -p.isG * solute_psi(p, C);
+    ux += p.taus * f * Fx / C;
+    uy += p.taus * f * Fy / C;
+  }
+  const float om = p.omega;
+  float geq[Q];
+  solute_geq<Q>(C, ux, uy, geq);
+  if (flux) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) gt[i] = geq[i];
   }
   float gs[Q];
 #pragma unroll
@@ -217,9 +333,16 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
 
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
   dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  int n = 0;
+  if (a.inter) {
+    if (q == 4) k_solute_pre<4><<<grd, blk, 0, s>>>(a);
+    else k_solute_pre<9><<<grd, blk, 0, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    n++;
+  }
   if (q == 4) k_solute<4><<<grd, blk, 0, s>>>(a);
   else k_solute<9><<<grd, blk, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return cudaGetLastError() == cudaSuccess ? n + 1 : -1;
 }
 
 int launch_growth(const GrowthArgs &a, cudaStream_t s) {

@@ -32,7 +32,7 @@ struct Opening {
   int style[2] = {OPEN_NONE, OPEN_NONE};
   double v[2] = {0, 0}, rho[2] = {1, 1};
   int sstyle = SOL_NONE;
-  double C = 0;
+  double C = 0, sv = 0;  // dirichlet C or flux C0; flux velocity
 };
 
 const double W9D[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
@@ -85,6 +85,8 @@ struct lb_ctx {
   std::vector<Opening> open;
   bool react = false;
   double kr = 0, Cs = 0, b0 = 0, bmax = 0;
+  bool inter = false;  // intersolute command
+  double isG = 0, ispsi0 = 0, isC0 = 0;
   uint64_t seed = 0;
   int nf = 0;
 
@@ -94,7 +96,7 @@ struct lb_ctx {
   int cur = 0;
   uint32_t *mask = nullptr;
   float *fields = nullptr, *u = nullptr, *gbuf[2] = {nullptr, nullptr};
-  float *Cfield = nullptr, *db = nullptr;
+  float *Cfield = nullptr, *db = nullptr, *Cpre = nullptr;
   double *b = nullptr, *removed = nullptr;
   uint8_t *flip = nullptr;
   unsigned long long *nflips = nullptr;
@@ -203,6 +205,7 @@ OpenDesc desc_of(const lb_ctx *ctx, const Opening &o) {
   }
   d.sstyle = o.sstyle;
   d.Cbar = (float)o.C;
+  d.sv = (float)o.sv;
   return d;
 }
 
@@ -234,7 +237,10 @@ int validate(lb_ctx *ctx) {
     return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built");
   for (const Opening &o : ctx->open) {
     for (int c = 0; c < ctx->nc; c++) {
-      if (o.style[c] == OPEN_NONE)
+      // without a momentum style the fluid stays periodic across the
+      // opening's wall (boundary_style command); only a solute rule may
+      // then make it an opening
+      if (o.style[c] == OPEN_NONE && !(ctx->qs && o.sstyle != SOL_NONE))
         return ctx->fail(LB_E_ARG, "opening '%s' has no momentum style for fluid %d",
                          o.label[0].c_str(), c + 1);
       if ((o.style[c] == OPEN_UNIFORM || o.style[c] == OPEN_POISEUILLE) && !(std::fabs(o.v[c]) < 1.0))
@@ -257,6 +263,13 @@ int validate(lb_ctx *ctx) {
     }
     if (ctx->qs && o.sstyle == SOL_NONE)
       return ctx->fail(LB_E_ARG, "opening '%s' has no solute style", o.label[0].c_str());
+    if (ctx->qs && o.sstyle == SOL_FLUX) {
+      const double D = (ctx->taus - 0.5) / (ctx->qs == 4 ? 2.0 : 3.0);
+      if (o.kind == 1 && !(std::fabs(o.sv - D) > 1e-12))
+        return ctx->fail(LB_E_ARG, "outlet flux style needs v != D = %g", D);
+      if (o.kind == 0 && !(std::fabs(o.sv + D) > 1e-12))
+        return ctx->fail(LB_E_ARG, "inlet flux style needs v != -D = %g", -D);
+    }
   }
   if (ctx->react) {
     // App. C rule 1: two opposite unknown modes cannot occur
@@ -301,6 +314,7 @@ int commit(lb_ctx *ctx) {
   if (ctx->qs) {
     TRY(dalloc(ctx, &ctx->u, 2 * g.plane));
     for (int k = 0; k < 2; k++) TRY(dalloc(ctx, &ctx->gbuf[k], (size_t)ctx->qs * g.plane));
+    if (ctx->inter) TRY(dalloc(ctx, &ctx->Cpre, g.plane));
     TRY(dalloc(ctx, &ctx->Cfield, g.plane));
     TRY(dalloc(ctx, &ctx->db, g.plane));
     TRY(dalloc(ctx, &ctx->flip, g.plane));
@@ -513,6 +527,14 @@ int one_step(lb_ctx *ctx, bool fields) {
     sa.Cfield = fields ? ctx->Cfield : nullptr;
     sa.nopen = (int)ctx->open.size();
     for (int k = 0; k < sa.nopen; k++) sa.op[k] = desc_of(ctx, ctx->open[k]);
+    sa.D = (float)((ctx->taus - 0.5) / (ctx->qs == 4 ? 2.0 : 3.0));
+    sa.inter = ctx->inter ? 1 : 0;
+    sa.isG = (float)ctx->isG;
+    sa.ispsi0 = (float)ctx->ispsi0;
+    sa.isC0 = (float)ctx->isC0;
+    sa.taus = (float)ctx->taus;
+    sa.Cpre = ctx->Cpre;
+    sa.Cpre_out = ctx->Cpre;
     LAUNCH(launch_solute(ctx->qs, sa, s));
     if (ctx->react) {
       GrowthArgs ga2{};
@@ -589,7 +611,7 @@ int lb_destroy(lb_ctx *ctx) {
   void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
-                  ctx->errw};
+                  ctx->errw,    ctx->Cpre};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -820,7 +842,8 @@ int lb_outlet_momentum(lb_ctx *ctx, const char *label, const char *style, double
   return set_momentum(ctx, 1, label, style, v, rho);
 }
 
-static int set_solute_open(lb_ctx *ctx, int kind, const char *label, const char *style, double C) {
+static int set_solute_open(lb_ctx *ctx, int kind, const char *label, const char *style, double C,
+                           double v) {
   if (!ctx->qs) return ctx->fail(LB_E_ORDER, "inlet_solute/outlet_solute need the solute command");
   int comp = 0;
   int k = find_label(ctx, label, kind, &comp);
@@ -828,20 +851,34 @@ static int set_solute_open(lb_ctx *ctx, int kind, const char *label, const char 
   if (!style) return ctx->fail(LB_E_ARG, "no style");
   if (!strcmp(style, "dirichlet")) ctx->open[k].sstyle = SOL_DIRICHLET;
   else if (!strcmp(style, "adiabatic")) ctx->open[k].sstyle = SOL_ADIABATIC;
-  else if (!strcmp(style, "flux")) return ctx->fail(LB_E_UNSUPPORTED, "solute flux style is not built");
+  else if (!strcmp(style, "flux")) ctx->open[k].sstyle = SOL_FLUX;
   else return ctx->fail(LB_E_ARG, "unknown solute style '%s'", style);
   ctx->open[k].C = C;
+  ctx->open[k].sv = v;
   return LB_OK;
 }
 
-int lb_inlet_solute(lb_ctx *ctx, const char *label, const char *style, double C) {
+int lb_inlet_solute(lb_ctx *ctx, const char *label, const char *style, double C, double v) {
   NEED_CTX();
-  return set_solute_open(ctx, 0, label, style, C);
+  return set_solute_open(ctx, 0, label, style, C, v);
 }
 
-int lb_outlet_solute(lb_ctx *ctx, const char *label, const char *style, double C) {
+int lb_outlet_solute(lb_ctx *ctx, const char *label, const char *style, double C, double v) {
   NEED_CTX();
-  return set_solute_open(ctx, 1, label, style, C);
+  return set_solute_open(ctx, 1, label, style, C, v);
+}
+
+int lb_intersolute(lb_ctx *ctx, double G, double psi0, double C0) {
+  NEED_CTX();
+  TRY(paint_check(ctx));
+  if (!ctx->qs) return ctx->fail(LB_E_ORDER, "intersolute needs the solute command");
+  if (!std::isfinite(G) || !std::isfinite(psi0) || !std::isfinite(C0))
+    return ctx->fail(LB_E_ARG, "intersolute parameters must be finite");
+  ctx->inter = true;
+  ctx->isG = G;
+  ctx->ispsi0 = psi0;
+  ctx->isC0 = C0;
+  return LB_OK;
 }
 
 int lb_surface_reaction(lb_ctx *ctx, double kr, double Cs, const char *style, double b0, double bmax,

@@ -12,7 +12,7 @@ namespace lbk {
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
 enum { OPEN_NONE = 0, OPEN_POISEUILLE = 1, OPEN_UNIFORM = 2, OPEN_DIRICHLET = 3,
        OPEN_GRADIENT = 4 };
-enum { SOL_NONE = 0, SOL_DIRICHLET = 1, SOL_ADIABATIC = 2 };
+enum { SOL_NONE = 0, SOL_DIRICHLET = 1, SOL_ADIABATIC = 2, SOL_FLUX = 3 };
 
 constexpr int MAX_OPEN = 8;
 constexpr int NFIELD = 4;   // per component: drho, px, py, drho_eq
@@ -27,7 +27,8 @@ struct OpenDesc {
   float rho[2];  // density held by dirichlet
   float drho[2]; // that density minus the component's rho_ref (from FP64)
   int sstyle;    // SOL_* for the solute
-  float Cbar;    // dirichlet concentration
+  float Cbar;    // dirichlet concentration, or C0 of the flux style
+  float sv;      // velocity v of the flux style
 };
 
 struct Geometry {
@@ -95,6 +96,13 @@ struct SoluteArgs {
   float *Cfield;          // or nullptr
   int nopen;
   OpenDesc op[MAX_OPEN];
+  float D;                // diffusion coefficient (tau_s - 1/2)/2 or /3
+  // intersolute: concentrations after streaming and the opening rules,
+  // written by a first pass (Cpre_out) and read by the update (Cpre)
+  int inter;
+  float isG, ispsi0, isC0, taus;
+  const float *Cpre;
+  float *Cpre_out;
 };
 
 // precipitation gather and growth decisions / flips
@@ -140,6 +148,7 @@ int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
 // device word the kernel sets when an mbarrier wait times out
 bool tma_supported(int storage, const Geometry &g);
 int launch_fluid_tma(int storage, const FluidArgs &a, int *err, cudaStream_t s, int sms);
+// one solute iteration (two kernels with intersolute: concentrations, then the update)
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
 int launch_growth(const GrowthArgs &a, cudaStream_t s);
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);

@@ -75,8 +75,8 @@ SIGNATURES = {
     "lb_outlet": (I, [P, S, I, I, S, S]),
     "lb_inlet_momentum": (I, [P, S, S, D, D]),
     "lb_outlet_momentum": (I, [P, S, S, D, D]),
-    "lb_inlet_solute": (I, [P, S, S, D]),
-    "lb_outlet_solute": (I, [P, S, S, D]),
+    "lb_inlet_solute": (I, [P, S, S, D, D]),
+    "lb_outlet_solute": (I, [P, S, S, D, D]),
     "lb_surface_reaction": (I, [P, D, D, S, D, D, U64]),
     "lb_position0_rect": (I, [P, I, I, I, I]),
     "lb_position0_circle": (I, [P, I, I, I]),
@@ -92,6 +92,7 @@ SIGNATURES = {
     "lb_aveacceleration": (I, [P, I, D, I]),
     "lb_aveacceleration_xy": (I, [P, D, D, I]),
     "lb_interforce": (I, [P, D, D, D]),
+    "lb_intersolute": (I, [P, D, D, D]),
     "lb_adhesiveforce": (I, [P, D, D, D, I]),
     "lb_set_kernel": (I, [P, S]),
     "lb_thermo": (I, [P, I]),
@@ -229,11 +230,11 @@ class Lattice:
     def outlet_momentum(self, label, style, v=0.0, rho=1.0):
         self._ck(self._L.lb_outlet_momentum(self._h, _b(label), _b(style), v, rho))
 
-    def inlet_solute(self, label, style, C=0.0):
-        self._ck(self._L.lb_inlet_solute(self._h, _b(label), _b(style), C))
+    def inlet_solute(self, label, style, C=0.0, v=0.0):
+        self._ck(self._L.lb_inlet_solute(self._h, _b(label), _b(style), C, v))
 
-    def outlet_solute(self, label, style, C=0.0):
-        self._ck(self._L.lb_outlet_solute(self._h, _b(label), _b(style), C))
+    def outlet_solute(self, label, style, C=0.0, v=0.0):
+        self._ck(self._L.lb_outlet_solute(self._h, _b(label), _b(style), C, v))
 
     def surface_reaction(self, kr, Cs, b0, bmax, seed=1, style="growth"):
         self._ck(self._L.lb_surface_reaction(self._h, kr, Cs, _b(style), b0, bmax, seed & (2 ** 64 - 1)))
@@ -291,6 +292,9 @@ class Lattice:
 
     def interforce(self, G: float, psi0: float = 0.0, rho0: float = 0.0):
         self._ck(self._L.lb_interforce(self._h, G, psi0, rho0))
+
+    def intersolute(self, G: float, psi0: float, C0: float):
+        self._ck(self._L.lb_intersolute(self._h, G, psi0, C0))
 
     def adhesiveforce(self, G: float, psi0: float = 0.0, rho0: float = 0.0, fluid: int = 1):
         self._ck(self._L.lb_adhesiveforce(self._h, G, psi0, rho0, fluid))
@@ -455,7 +459,8 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
         for s, (style, v, rho) in enumerate(op.momentum):
             (lt.inlet_momentum if op.kind == "inlet" else lt.outlet_momentum)(labels[s], style, v, rho)
         if op.solute is not None and w.solute_q:
-            (lt.inlet_solute if op.kind == "inlet" else lt.outlet_solute)(labels[0], op.solute[0], op.solute[1])
+            sv = op.solute[2] if len(op.solute) > 2 else 0.0
+            (lt.inlet_solute if op.kind == "inlet" else lt.outlet_solute)(labels[0], op.solute[0], op.solute[1], sv)
     if w.reaction is not None and w.solute_q:
         kr, Cs, b0, bmax, seed = w.reaction
         lt.surface_reaction(kr, Cs, b0, bmax, seed)
@@ -471,6 +476,8 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
             lt.adhesiveforce(ad[0], ad[1], ad[2], s + 1)
     if w.interforce is not None:
         lt.interforce(*w.interforce)
+    if getattr(w, "intersolute", None) is not None and w.solute_q:
+        lt.intersolute(*w.intersolute)
     lt.thermo(thermo)
     lt.set_kernel(kernel)
     for s in range(w.ncomp):

@@ -50,8 +50,8 @@ class Opening:
     kind: str                      # "inlet" | "outlet"
     # per component: (style, v, rho); style in poiseuille/uniform/dirichlet/gradient
     momentum: List[Tuple[str, float, float]] = field(default_factory=list)
-    # (style, C) with style in dirichlet/adiabatic, or None
-    solute: Optional[Tuple[str, float]] = None
+    # (style, C) with style in dirichlet/adiabatic, ("flux", C0, v), or None
+    solute: Optional[Tuple] = None
 
 
 @dataclass
@@ -74,6 +74,7 @@ class Workload:
     taus: float = 1.0
     C: Optional[np.ndarray] = None                      # initial concentration
     reaction: Optional[Tuple[float, float, float, float, int]] = None  # kr, Cs, b0, bmax, seed
+    intersolute: Optional[Tuple[float, float, float]] = None    # (G, psi0, C0)
     steps: int = 1
     rho_ref: Sequence[float] = (1.0,)                   # typical density per component
     info: dict = field(default_factory=dict)

@@ -1,0 +1,315 @@
+"""Long runs: every workload at its stated iteration count, the GPU library
+against the FP64 oracle.
+
+The oracle needs minutes to hours for these (config 4 alone about two
+hours on one core), so this is a script run by hand, not part of the
+pytest suites:
+
+    python tests/long_parity.py gpu <dir> [case ...]      # on a GPU
+    python tests/long_parity.py oracle <dir> [case ...]   # on CPU cores
+    python tests/long_parity.py compare <gpu_dir> <oracle_dir>
+    python tests/long_parity.py report <dir>              # config 3 at 2048^2, GPU only
+
+`gpu` runs the library (one lattice, or the batched launch for the batch
+case) and writes <dir>/<case>_<storage>.npz; `oracle` runs the oracle,
+one process per case, and writes <dir>/<case>.npz; `compare` prints one
+markdown table row per (case, storage): relative errors in rho and u,
+masks, mass drift of both sides, and the case's own physics numbers.
+No value produced here is stored as an expected value anywhere.
+"""
+from __future__ import annotations
+
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_1202_0442_gb300 import synth  # noqa: E402
+
+BATCH_PICK = (0, 37, 73, 109, 146, 182, 219, 255)
+
+
+def _batch_workloads():
+    ws = synth.batch()
+    return [ws[k] for k in BATCH_PICK]
+
+
+CASES = {
+    # name: (workload factory, iterations, storages, checkpoints)
+    "channel": (lambda: synth.channel(), 2000, ("fp32", "fp16", "bf16"), ()),
+    "porous": (lambda: synth.porous(), 10000, ("fp32", "fp16", "bf16"), ()),
+    "shan_chen2_256": (lambda: synth.shan_chen2(256), 20000, ("fp32", "fp16"), (2000,)),
+    "reactive_q9": (lambda: synth.reactive(q=9), 50000, ("fp32",), ()),
+    "reactive_q4": (lambda: synth.reactive(q=4), 50000, ("fp32",), ()),
+    "batch8": (_batch_workloads, 5000, ("fp32", "fp16"), ()),
+}
+H_MAX = {"channel": 2e-3, "porous": 2e-3, "shan_chen2_256": 1.2, "batch8": 5e-3}
+
+
+def _snapshot_gpu(lt, w):
+    out = {"mask": lt.mask().astype(np.uint8)}
+    for c in range(1, w.ncomp + 1):
+        r, px, py, _ = lt.fields(c)
+        out[f"rho{c}"] = r.astype(np.float32)
+    ux, uy = lt.velocity()
+    out["ux"], out["uy"] = ux.astype(np.float32), uy.astype(np.float32)
+    if w.solute_q:
+        _, Cf, b = lt.solute_state(g=False)
+        out["C"], out["b"] = Cf.astype(np.float32), b
+    out["thermo"] = np.array(json.dumps(lt.get_thermo()))
+    return out
+
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+
+
+def _snapshot_pops(f, mask, w):
+    """Density, velocity (j + F/2)/rho and mass from the populations of a
+    single-component lattice with aveforce/aveacceleration (the batched
+    lattices, whose kernel writes no field planes)."""
+    fl = mask == 0
+    rho = np.where(fl, f.sum(0), 0.0)
+    fx, fy = w.aveforce[0] if w.aveforce else (0.0, 0.0)
+    ax, ay = w.aveacceleration[0] if w.aveacceleration else (0.0, 0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ux = np.where(fl, (np.tensordot(EX, f, 1) + 0.5 * (fx + rho * ax)) / np.where(fl, rho, 1), 0.0)
+        uy = np.where(fl, (np.tensordot(EY, f, 1) + 0.5 * (fy + rho * ay)) / np.where(fl, rho, 1), 0.0)
+    return {"mask": mask.astype(np.uint8), "rho1": rho, "ux": ux, "uy": uy,
+            "thermo": np.array(json.dumps({"mass1": float(rho[fl].sum())}))}
+
+
+def _snapshot_oracle(o, w):
+    out = {"mask": o.solid().astype(np.uint8)}
+    for c in range(w.ncomp):
+        out[f"rho{c + 1}"] = o.fields(c)[0]
+    out["ux"], out["uy"] = o.velocity()
+    if w.solute_q:
+        out["C"], out["b"] = o.solute_C(), o.b()
+    out["thermo"] = np.array(json.dumps(o.thermo()))
+    return out
+
+
+def run_gpu(outdir, names):
+    import torch
+    from paper_1202_0442_gb300 import build, lb2d
+    build.build()
+    torch.cuda.set_device(0)
+    os.makedirs(outdir, exist_ok=True)
+    for name in names:
+        make, steps, storages, cps = CASES[name]
+        for st in storages:
+            kw = {"h_max": H_MAX.get(name, 0.0)}
+            if st != "fp32":
+                kw["rounding"] = "stochastic"
+            t0 = time.time()
+            if name == "batch8":
+                ws = make()
+                lts = [lb2d.from_workload(w, st, thermo=0, **kw) for w in ws]
+                b = lb2d.Batch(lts)
+                b.iteration(steps)
+                torch.cuda.synchronize()
+                res = {}
+                for k, (w, lt) in enumerate(zip(ws, lts)):
+                    snap = _snapshot_pops(lt.populations(), lt.mask(), w)
+                    for key, v in snap.items():
+                        res[f"l{k}_{key}"] = v
+            else:
+                w = make()
+                lt = lb2d.from_workload(w, st, thermo=0, **kw)
+                res, done = {}, 0
+                for cp in tuple(cps) + (steps,):
+                    lt.iteration(cp - done)
+                    done = cp
+                    tag = "" if cp == steps else f"t{cp}_"
+                    for key, v in _snapshot_gpu(lt, w).items():
+                        res[tag + key] = v
+            torch.cuda.synchronize()
+            res = {k: (v.astype(np.float32) if v.dtype == np.float64 and not k.endswith("b") else v)
+                   for k, v in res.items()}
+            res["seconds"] = np.array(time.time() - t0)
+            np.savez_compressed(os.path.join(outdir, f"{name}_{st}.npz"), **res)
+            print(f"{name} {st}: {steps} iterations, {time.time() - t0:.1f} s", flush=True)
+
+
+def _oracle_one(args):
+    name, outdir = args
+    sys.path.insert(0, ROOT)
+    from oracle.drive import oracle_from_workload
+    make, steps, _, cps = CASES[name]
+    t0 = time.time()
+    res = {}
+    if name == "batch8":
+        for k, w in enumerate(make()):
+            o = oracle_from_workload(w)
+            o.step(steps)
+            for key, v in _snapshot_pops(o.f(0), o.solid(), w).items():
+                res[f"l{k}_{key}"] = v
+    else:
+        w = make()
+        o = oracle_from_workload(w)
+        done = 0
+        for cp in tuple(cps) + (steps,):
+            o.step(cp - done)
+            done = cp
+            tag = "" if cp == steps else f"t{cp}_"
+            for key, v in _snapshot_oracle(o, w).items():
+                res[tag + key] = v
+    res["seconds"] = np.array(time.time() - t0)
+    np.savez_compressed(os.path.join(outdir, f"{name}.npz"), **res)
+    return name, time.time() - t0
+
+
+def run_oracle(outdir, names):
+    os.makedirs(outdir, exist_ok=True)
+    with mp.get_context("spawn").Pool(len(names)) as pool:
+        for name, dt in pool.imap_unordered(_oracle_one, [(n, outdir) for n in names]):
+            print(f"oracle {name}: {dt:.0f} s", flush=True)
+
+
+def _rel(a, b, fl):
+    den = max(float(np.max(np.abs(b[fl]))), 1e-300)
+    return float(np.max(np.abs(a[fl].astype(np.float64) - b[fl])) / den)
+
+
+def _compare_one(g, o, w, prefix=""):
+    mg, mo = g[prefix + "mask"], o[prefix + "mask"]
+    fl = (mo == 0) & (mg == 0)
+    row = {"mask_equal": bool(np.array_equal(mg, mo)), "mask_diff": int((mg != mo).sum())}
+    for c in range(1, w.ncomp + 1):
+        row[f"rho{c}"] = _rel(g[prefix + f"rho{c}"], o[prefix + f"rho{c}"], fl)
+    den = max(float(np.max(np.abs(o[prefix + "ux"][fl]))), float(np.max(np.abs(o[prefix + "uy"][fl]))), 1e-300)
+    row["u"] = max(float(np.max(np.abs(g[prefix + "ux"][fl] - o[prefix + "ux"][fl]))),
+                   float(np.max(np.abs(g[prefix + "uy"][fl] - o[prefix + "uy"][fl])))) / den
+    tg = json.loads(str(g[prefix + "thermo"]))
+    to = json.loads(str(o[prefix + "thermo"]))
+    m0 = [float(np.sum(np.where(w.solid != 0, 0.0, r))) for r in w.rho]
+    for c in range(1, w.ncomp + 1):
+        row[f"drift{c}_gpu"] = (tg[f"mass{c}"] - m0[c - 1]) / m0[c - 1]
+        row[f"drift{c}_oracle"] = (to[f"mass{c}"] - m0[c - 1]) / m0[c - 1]
+        row[f"mass{c}_vs_oracle"] = abs(tg[f"mass{c}"] - to[f"mass{c}"]) / abs(to[f"mass{c}"])
+    if w.solute_q:
+        row["C"] = _rel(g[prefix + "C"], o[prefix + "C"], fl)
+        row["b"] = float(np.max(np.abs(g[prefix + "b"] - o[prefix + "b"])) / max(float(np.max(o[prefix + "b"])), 1e-300))
+        row["flips_gpu"], row["flips_oracle"] = tg["flips"], to["flips"]
+        for k in ("solute", "bsum", "removed_solute"):
+            row[f"{k}_vs_oracle"] = abs(tg[k] - to[k]) / max(abs(to[k]), 1e-300)
+    return row
+
+
+def _laplace(d, w, prefix=""):
+    """Pressure p = (rho1 + rho2)/3 + G rho1 rho2 / 3 inside the free
+    droplet, inside the ring and far outside, for the Laplace report."""
+    G = w.interforce[0]
+    r1, r2 = d[prefix + "rho1"].astype(np.float64), d[prefix + "rho2"].astype(np.float64)
+    p = (r1 + r2) / 3 + G * r1 * r2 / 3
+    dc, _, dr = w.info["drop"]
+    n = w.nx
+    c = n // 2
+    return {"p_drop": float(p[dc, dc]), "p_ring_centre": float(p[c, c]),
+            "p_outside": float(p[(c + n // 2 - 2) % n, (c + n // 2 - 2) % n]),
+            "drop_r": dr}
+
+
+def compare(gdir, odir):
+    rows = []
+    for name, (make, steps, storages, cps) in CASES.items():
+        op = os.path.join(odir, f"{name}.npz")
+        if not os.path.exists(op):
+            continue
+        o = np.load(op)
+        for st in storages:
+            gp = os.path.join(gdir, f"{name}_{st}.npz")
+            if not os.path.exists(gp):
+                continue
+            g = np.load(gp)
+            if name == "batch8":
+                ws = make()
+                worst = {}
+                for k, w in enumerate(ws):
+                    r = _compare_one(g, o, w, prefix=f"l{k}_")
+                    for key, v in r.items():
+                        if isinstance(v, bool):
+                            worst[key] = worst.get(key, True) and v
+                        else:
+                            worst[key] = max(worst.get(key, v), v, key=abs) if "drift" in key else max(worst.get(key, 0), v)
+                rows.append((name, st, steps, worst))
+                continue
+            w = make()
+            for cp in cps:
+                rows.append((name, st, cp, _compare_one(g, o, w, prefix=f"t{cp}_")))
+            r = _compare_one(g, o, w)
+            if name.startswith("shan_chen"):
+                r.update({f"gpu_{k}": v for k, v in _laplace(g, w).items()})
+                r.update({f"oracle_{k}": v for k, v in _laplace(o, w).items()})
+            rows.append((name, st, steps, r))
+    for name, st, t, r in rows:
+        items = ", ".join(f"{k} {v:.3g}" if isinstance(v, float) else f"{k} {v}" for k, v in r.items())
+        print(f"| {name} | {st} | {t} | {items} |")
+
+
+def run_report(outdir):
+    """Config 3 at full size (2048^2, two components, 20000 iterations):
+    component masses, their drift, and the pressures of the Laplace
+    report, FP32 and FP16 storage.  GPU only (the oracle would need hours;
+    its parity is checked on the 256^2 version of the same recipe)."""
+    import torch
+    from paper_1202_0442_gb300 import build, lb2d
+    build.build()
+    torch.cuda.set_device(0)
+    os.makedirs(outdir, exist_ok=True)
+    out = {}
+    w = synth.shan_chen2(2048)
+    m0 = [float(np.sum(np.where(w.solid != 0, 0.0, r))) for r in w.rho]
+    for st in ("fp32", "fp16"):
+        kw = {"h_max": 1.2}
+        if st != "fp32":
+            kw["rounding"] = "stochastic"
+        lt = lb2d.from_workload(w, st, thermo=0, **kw)
+        t0 = time.time()
+        lt.iteration(w.steps)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        th = lt.get_thermo()
+        d = {"rho1": lt.fields(1)[0], "rho2": lt.fields(2)[0]}
+        rep = {"iterations": w.steps, "seconds": dt,
+               "mlups": w.nx * w.ny * w.steps / dt / 1e6,
+               "mass1": th["mass1"], "mass2": th["mass2"],
+               "drift1": (th["mass1"] - m0[0]) / m0[0], "drift2": (th["mass2"] - m0[1]) / m0[1]}
+        rep.update(_laplace(d, w))
+        out[st] = rep
+        print(st, rep, flush=True)
+    with open(os.path.join(outdir, "shan_chen2_2048_report.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
+def main(argv):
+    if len(argv) < 2:
+        print(__doc__)
+        return 2
+    mode = argv[0]
+    if mode == "compare":
+        compare(argv[1], argv[2])
+        return 0
+    if mode == "report":
+        run_report(argv[1])
+        return 0
+    names = argv[2:] or list(CASES)
+    if mode == "gpu":
+        run_gpu(argv[1], names)
+    elif mode == "oracle":
+        run_oracle(argv[1], names)
+    else:
+        print(__doc__)
+        return 2
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

@@ -724,6 +724,93 @@ def test_solute_dirichlet_and_adiabatic_openings():
         assert np.allclose(C[1:-1, :], 1.0, atol=1e-6), C[ny // 2]
 
 
+def _flux_channel(q, inlet, outlet, nx=32, ny=2):
+    """Solvent at rest, periodic in y, solute openings on the full x = 0
+    and x = nx-1 columns (no fluid rule: the fluid stays periodic)."""
+    solid = np.zeros((ny, nx), np.uint8)
+    return synth.Workload(name="flux", nx=nx, ny=ny, solid=solid, rho=[np.ones((ny, nx))], tau=(1.0,),
+                          openings=[synth.Opening("xlo", 0, ny - 1, "inlet", [], solute=inlet),
+                                    synth.Opening("xhi", 0, ny - 1, "outlet", [], solute=outlet)],
+                          solute_q=q, taus=1.0, C=np.zeros((ny, nx)))
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_solute_flux_inlet_exact_steady_state(q):
+    """inlet_solute flux (App. B): C = (v C0 + D C1)/(D + v) on the inlet,
+    every mode at equilibrium.  At tau_s = 1 with the solvent at rest and a
+    dirichlet C = 0 outlet, the lattice's steady state is exactly linear,
+    C(x) = s (L - x), and the rule closes it with s = v C0 / (v L + D),
+    D = 1/4 (D2Q4) or 1/6 (D2Q9): the inlet node balances the injected
+    flux v (C0 - C_in) against the lattice's diffusive flux D s.  (Half or
+    twice D in the rule moves C_in by > 5 %.)"""
+    v, C0 = 0.02, 1.0
+    w = _flux_channel(q, ("flux", C0, v), ("dirichlet", 0.0))
+    o = oracle_from_workload(w)
+    o.step(60000)
+    C = o.solute_C()[0]
+    L = w.nx - 1
+    D = 0.25 if q == 4 else 1.0 / 6.0
+    s = v * C0 / (v * L + D)
+    x = np.arange(w.nx)
+    assert np.max(np.abs(C - s * (L - x))) < 1e-9, (C[:3], s * L)
+
+
+def test_solute_flux_outlet_exact_steady_state():
+    """outlet_solute flux (App. B): C = (v C0 - D C1)/(v - D) on the
+    outlet, i.e. the outgoing flux v C + D (C1 - C) equals v C0.  With a
+    dirichlet C = Cb inlet the exact steady state at tau_s = 1 is
+    C(x) = Cb - s x with s (D - L v) = v (C0 - Cb).  As an explicit update
+    the rule multiplies C1's changes by -D/(v - D), so it settles only for
+    v > 2D (here v = 0.6, D = 1/4); for v < D it diverges."""
+    v, C0, Cb = 0.6, 0.5, 1.0
+    w = _flux_channel(4, ("dirichlet", Cb), ("flux", C0, v))
+    o = oracle_from_workload(w)
+    o.step(60000)
+    C = o.solute_C()[0]
+    L, D = w.nx - 1, 0.25
+    s = v * (C0 - Cb) / (D - L * v)
+    x = np.arange(w.nx)
+    assert np.max(np.abs(C - (Cb - s * x))) < 1e-9, (C[-3:], Cb - s * L)
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_intersolute_force_first_step(q):
+    """intersolute command: the collision adds F = -G psi(x) sum_{i=1..4}
+    psi(x + e_i) e_i to the solute flux sum_i g_i e_i (u_s = u + tau_s F / C
+    in g_eq), psi = psi0 exp(-C0/C) of this step's concentrations.  From
+    g = g_eq(C, 0) the streamed concentration is computed here by hand
+    (brute force), F from it, and compared with the difference of one
+    oracle step with and without the force."""
+    N, G, psi0, C0 = 12, -0.05, 1.0, 0.3
+    rng = np.random.default_rng(5)
+    Cinit = 0.5 + 0.5 * rng.uniform(size=(N, N))
+    outs = []
+    for on in (False, True):
+        o = Oracle(N, N, 1, q)
+        o.set_taus(0.8)
+        o.set_equilibrium(1.0)
+        o.set_solute_equilibrium(Cinit)
+        if on:
+            o.set_intersolute(G, psi0, C0)
+        o.step()
+        outs.append(o.g())
+    ex = np.array([1, 0, -1, 0]) if q == 4 else EX
+    ey = np.array([0, 1, 0, -1]) if q == 4 else EY
+    wts = np.full(4, 0.25) if q == 4 else np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    # streamed C(x) = sum_i w_i C(x - e_i) (each g_i starts at w_i C)
+    Cs = sum(wts[i] * np.roll(np.roll(Cinit, ey[i], 0), ex[i], 1) for i in range(len(wts)))
+    psi = psi0 * np.exp(-C0 / Cs)
+    Fx = -G * psi * (np.roll(psi, -1, 1) - np.roll(psi, 1, 1))
+    Fy = -G * psi * (np.roll(psi, -1, 0) - np.roll(psi, 1, 0))
+    d = outs[1] - outs[0]
+    jx = np.tensordot(ex.astype(float), d, 1)
+    jy = np.tensordot(ey.astype(float), d, 1)
+    assert np.max(np.abs(jx - Fx)) < 1e-15 + 1e-12 * np.max(np.abs(Fx))
+    assert np.max(np.abs(jy - Fy)) < 1e-15 + 1e-12 * np.max(np.abs(Fy))
+    assert np.max(np.abs(Fx)) > 1e-4
+    assert abs(d.sum()) < 1e-13
+
+
 # --------------------------------------------------------------------------
 # surface reaction, precipitation, growth (surface_reaction, App. C)
 # --------------------------------------------------------------------------
