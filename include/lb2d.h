@@ -131,9 +131,24 @@ int lb_solute(lb_ctx *ctx, double taus, int q);
 int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref,
                    double h_max);
 
-/* boundary_style command: "noslip" (half-way bounce-back).  "slip",
- * "mixed" and "hybrid" give LB_E_UNSUPPORTED.  Must precede obstacles. */
-int lb_boundary_style(lb_ctx *ctx, const char *style);
+/* boundary_style command: how fluid populations meet solid nodes.
+ *   "noslip": half-way bounce-back.
+ *   "slip": mirror reflection at flat walls (Fig. slip).  A diagonal mode
+ *     (a, b) of node x whose source x - (a, b) is solid arrives instead from
+ *     x - (2a, 0) as mode (a, -b) when x - (0, b), x - (2a, b) are solid and
+ *     x - (a, 0), x - (2a, 0) fluid (a wall along x), or from x - (0, 2b) as
+ *     mode (-a, b) when x - (a, 0), x - (a, 2b) are solid and x - (0, b),
+ *     x - (0, 2b) fluid (a wall along y); every other case, the axis modes,
+ *     and paths across an edge of the lattice that carries an opening are
+ *     bounced back.  Each reflection pairs with its reverse, so mass is kept.
+ *   "mixed": a fraction R (0 <= R <= 1) slips, 1 - R bounces back.
+ *   "hybrid": R per solid node and fluid, from lb_obstacle_*_styled or
+ *     lb_obstacle_mask_hybrid (plain obstacle calls give noslip nodes;
+ *     nodes that turn solid by growth are noslip).
+ * R is read by "mixed" only.  The solute always bounces back (or reacts).
+ * Must precede obstacles.  Slip styles run on the streaming kernels and
+ * are not available to batched lattices. */
+int lb_boundary_style(lb_ctx *ctx, const char *style, double R);
 
 /* obstacle command: mark nodes solid.  Rectangle with inclusive bounds;
  * circle (x-xc)^2 + (y-yc)^2 <= r^2 with periodic distance; mask: nx*ny
@@ -142,6 +157,21 @@ int lb_boundary_style(lb_ctx *ctx, const char *style);
 int lb_obstacle_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1);
 int lb_obstacle_circle(lb_ctx *ctx, int xc, int yc, int r);
 int lb_obstacle_mask(lb_ctx *ctx, const uint8_t *mask);
+
+/* obstacle command with the hybrid style's extra arguments: style1 for
+ * fluid 1 and style2 for fluid 2 ("noslip", "slip" or "mixed" with its
+ * coefficient arg; NULL style2 repeats style1; NULL style1 is noslip).
+ * Outside the hybrid style the styles are checked and otherwise ignored. */
+int lb_obstacle_rect_styled(lb_ctx *ctx, int x0, int x1, int y0, int y1,
+                            const char *style1, double arg1,
+                            const char *style2, double arg2);
+int lb_obstacle_circle_styled(lb_ctx *ctx, int xc, int yc, int r,
+                              const char *style1, double arg1,
+                              const char *style2, double arg2);
+/* mask form: R, if not NULL, holds [ncomp][ny][nx] reflection
+ * coefficients in [0, 1] read on the masked nodes (needs the hybrid
+ * style; LB_E_ORDER otherwise); NULL makes them noslip. */
+int lb_obstacle_mask_hybrid(lb_ctx *ctx, const uint8_t *mask, const double *R);
 
 /* inlet/outlet commands: an opening on wall "xlo", "xhi", "ylo" or "yhi"
  * spanning a0..a1 along it (y for x-walls, x for y-walls).  label1 names

@@ -28,6 +28,13 @@ def oracle_from_workload(w, solute_q=None) -> Oracle:
             o.set_adhesiveforce(ad[0], ad[1], ad[2], s)
     if w.interforce is not None:
         o.set_interforce(*w.interforce)
+    for s, R in enumerate(getattr(w, "slip", None) or ()):
+        if R is None:
+            continue
+        if np.ndim(R) == 0:
+            o.set_slip(float(R), None, s)
+        else:
+            o.set_slip(0.0, R, s)
     for op in w.openings:
         k = o.add_opening(op.wall, op.a0, op.a1, op.kind)
         for s, (style, v, rho) in enumerate(op.momentum):

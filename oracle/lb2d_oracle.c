@@ -76,6 +76,13 @@ static const double W9[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const int OPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
+/* index of the D2Q9 direction (ex, ey) */
+static int dir9(int ex, int ey) {
+  for (int i = 0; i < 9; i++)
+    if (EX9[i] == ex && EY9[i] == ey) return i;
+  return -1;
+}
+
 /* D2Q4 solute lattice (solute command): g1=+x, g2=+y, g3=-x, g4=-y at
  * storage index 0..3. */
 static const int EX4[4] = {1, 0, -1, 0};
@@ -111,6 +118,8 @@ struct orc {
   int *open_id;
   double *g, *gt, *C, *b, *db, *Cw;
   double *Cst, *Cpre; /* solute: C after streaming; after the opening rules */
+  double slipR[2];    /* boundary_style slip/mixed: R of every solid node */
+  double *Rmap[2];    /* hybrid: R per node (NULL: slipR) */
   int is_on;          /* intersolute */
   double isG, ispsi0, isC0;
   int *nU, *Ubits;
@@ -185,6 +194,7 @@ void orc_destroy(orc_t *o) {
   free(o->g); free(o->gt); free(o->C); free(o->db); free(o->b);
   free(o->Cw); free(o->nU); free(o->Ubits);
   free(o->Cst); free(o->Cpre);
+  free(o->Rmap[0]); free(o->Rmap[1]);
   free(o->solid); free(o->open_id); free(o->flip);
   free(o);
 }
@@ -368,6 +378,20 @@ int orc_set_adhesiveforce(orc_t *o, int comp, double G, double psi0,
   o->Gads[comp] = G;
   o->ads_psi0[comp] = psi0;
   o->ads_rho0[comp] = rho0;
+  return 0;
+}
+
+int orc_set_slip(orc_t *o, int comp, double R_all, const double *R_map) {
+  if (comp < 0 || comp >= o->nc || R_all < 0.0 || R_all > 1.0) return -1;
+  size_t nn = (size_t)o->nx * o->ny;
+  o->slipR[comp] = R_all;
+  free(o->Rmap[comp]);
+  o->Rmap[comp] = NULL;
+  if (R_map) {
+    o->Rmap[comp] = (double *)calloc(nn, sizeof(double));
+    for (size_t n = 0; n < nn; n++)
+      o->Rmap[comp][n] = o->solid[n] ? R_map[n] : 0.0;
+  }
   return 0;
 }
 
@@ -621,6 +645,57 @@ static double psi_sc(const orc_t *o, double rho) {
   return o->psi0 * exp(-o->rho0 / rho);
 }
 
+/* An edge of the domain is no longer periodic when an opening lies on
+ * either of its two walls (the x edge for xlo/xhi, the y edge for
+ * ylo/yhi); the slip rule must not reach across it. */
+static int edge_open(const orc_t *o, int xedge) {
+  for (int k = 0; k < o->nopen; k++)
+    if ((o->op[k].wall <= ORC_XHI) == (xedge != 0)) return 1;
+  return 0;
+}
+
+/* solid test of node (x, y) given in unwrapped coordinates: 1 if solid,
+ * 0 if fluid, -1 if it lies across an edge that has an opening */
+static int solid_u(const orc_t *o, int x, int y) {
+  if (((x < 0 || x >= o->nx) && edge_open(o, 1)) || ((y < 0 || y >= o->ny) && edge_open(o, 0)))
+    return -1;
+  return o->solid[(size_t)wrap(y, o->ny) * o->nx + wrap(x, o->nx)] ? 1 : 0;
+}
+
+/* boundary_style slip (Fig. slip): the diagonal mode i = (a, b) arriving at
+ * fluid node y = (x, y) whose source y - (a, b) is solid comes by mirror
+ * reflection from a wall of that source.  Horizontal wall (the nodes
+ * y - (0, b) and y - (2a, b) solid, y - (a, 0) and y - (2a, 0) fluid): the
+ * mode (a, -b) emitted by y - (2a, 0), as in f8(i+2, j) = f5(i, j).
+ * Vertical wall (y - (a, 0) and y - (a, 2b) solid, y - (0, b) and
+ * y - (0, 2b) fluid): the mode (-a, b) emitted by y - (0, 2b), as in
+ * f6(i, j+2) = f5(i, j).  The two arrangements exclude each other and
+ * each reflection maps onto its reverse, so every emitted population is
+ * used exactly once.  Returns 0 (bounce-back) in every other case,
+ * including a path across a wall with an opening. */
+static int slip_source(const orc_t *o, int s, int x, int y, int i, double *fs) {
+  const int a = EX9[i], b = EY9[i];
+  int s1 = solid_u(o, x, y - b), s2 = solid_u(o, x - 2 * a, y - b);
+  int f1 = solid_u(o, x - a, y), f2 = solid_u(o, x - 2 * a, y);
+  if (s1 == 1 && s2 == 1 && f1 == 0 && f2 == 0) {
+    int m = dir9(a, -b);
+    size_t ne = (size_t)wrap(y, o->ny) * o->nx + wrap(x - 2 * a, o->nx);
+    *fs = o->f[s][ne * 9 + m];
+    return 1;
+  }
+  s1 = solid_u(o, x - a, y);
+  s2 = solid_u(o, x - a, y - 2 * b);
+  f1 = solid_u(o, x, y - b);
+  f2 = solid_u(o, x, y - 2 * b);
+  if (s1 == 1 && s2 == 1 && f1 == 0 && f2 == 0) {
+    int m = dir9(-a, b);
+    size_t ne = (size_t)wrap(y - 2 * b, o->ny) * o->nx + wrap(x, o->nx);
+    *fs = o->f[s][ne * 9 + m];
+    return 1;
+  }
+  return 0;
+}
+
 int orc_step(orc_t *o) {
   const int nx = o->nx, ny = o->ny, nc = o->nc;
   const size_t nn = (size_t)nx * ny;
@@ -640,10 +715,17 @@ int orc_step(orc_t *o) {
         for (int i = 0; i < 9; i++) {
           int xs = wrap(x - EX9[i], nx), ys = wrap(y - EY9[i], ny);
           size_t ns = (size_t)ys * nx + xs;
-          if (o->solid[ns])
+          if (o->solid[ns]) {
             ft[i] = o->f[s][n * 9 + OPP9[i]];
-          else
+            double R = o->Rmap[s] ? o->Rmap[s][ns] : o->slipR[s];
+            if (R > 0.0 && i >= 5) {
+              double fs;
+              if (slip_source(o, s, x, y, i, &fs))
+                ft[i] = R * fs + (1.0 - R) * ft[i];
+            }
+          } else {
             ft[i] = o->f[s][ns * 9 + i];
+          }
         }
       }
   }

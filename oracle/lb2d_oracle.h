@@ -73,6 +73,13 @@ int orc_set_interforce(orc_t *o, double G, double psi0, double rho0);
 int orc_set_adhesiveforce(orc_t *o, int comp, double G, double psi0,
                           double rho0);
 
+/* boundary_style slip/mixed/hybrid: reflection coefficient R of the solid
+ * nodes for component comp (0 = noslip, 1 = slip, else mixed).  R_all
+ * applies to every solid node (also ones grown later) unless R_map is
+ * given ([ny][nx], read on solid nodes; nodes that turn solid later get
+ * R = 0). */
+int orc_set_slip(orc_t *o, int comp, double R_all, const double *R_map);
+
 int orc_add_opening(orc_t *o, int wall, int a0, int a1, int kind);
 int orc_set_opening_momentum(orc_t *o, int opening, int comp, int style,
                              double v, double rho);

@@ -84,6 +84,7 @@ def _load():
         "orc_set_opening_momentum": (I, [P, I, I, I, D, D]),
         "orc_set_opening_solute": (I, [P, I, I, D, D]),
         "orc_set_intersolute": (I, [P, D, D, D]),
+        "orc_set_slip": (I, [P, I, D, dp]),
         "orc_set_reaction": (I, [P, D, D, D, D, U64]),
         "orc_step": (I, [P]),
         "orc_time": (C.c_long, [P]),
@@ -226,6 +227,13 @@ class Oracle:
         style's velocity."""
         _check(self._l.orc_set_opening_solute(self._h, opening, SSTYLES[style],
                                               Cbar, v), "opening solute")
+
+    def set_slip(self, R_all: float = 0.0, R_map=None, comp: int = 0):
+        """boundary_style slip (R = 1), mixed (0 < R < 1) or, with R_map
+        ([ny][nx], read on solid nodes), hybrid."""
+        m = None if R_map is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(R_map, np.float64), (self.ny, self.nx)))
+        _check(self._l.orc_set_slip(self._h, comp, R_all, None if m is None else _dp(m)), "slip")
 
     def set_intersolute(self, G: float, psi0: float, C0: float):
         _check(self._l.orc_set_intersolute(self._h, G, psi0, C0), "intersolute")

@@ -53,6 +53,65 @@ __device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, i
   }
 }
 
+// solid test of node (x, y) given up to two nodes outside the lattice: 1
+// solid, 0 fluid, -1 across an edge that carries an opening
+__device__ __forceinline__ int solid_u(const FluidArgs &p, int x, int y) {
+  const Geometry &g = p.g;
+  if ((x < 0 || x >= g.nx) && p.edge_x) return -1;
+  if ((y < 0 || y >= g.ny) && p.edge_y) return -1;
+  x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
+  y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
+  return solid_at(p.mask, g.mw, x, y);
+}
+
+// boundary_style slip (Fig. slip), mixed and hybrid, after pull9 has
+// bounced back every mode with a solid source.  A diagonal mode i = (a, b)
+// whose source x - (a, b) is solid with coefficient R > 0 takes
+// R f_m(e) + (1 - R) (its bounce-back value), where e, m is the mirror
+// reflection at a flat wall of that source: horizontal wall (x - (0, b)
+// and x - (2a, b) solid, x - (a, 0) and x - (2a, 0) fluid): e = x - (2a, 0),
+// m = (a, -b), as in f8(i+2, j) = f5(i, j); vertical wall (x - (a, 0) and
+// x - (a, 2b) solid, x - (0, b) and x - (0, 2b) fluid): e = x - (0, 2b),
+// m = (-a, b), as in f6(i, j+2) = f5(i, j).  Each reflection is paired with
+// its reverse, so every population is used once and mass is kept; any
+// other arrangement, or a path across an edge with an opening, stays
+// bounce-back.  Axis modes always bounce back.
+template <class S>
+__device__ __forceinline__ void slip_fix(const FluidArgs &p, int c, const S *base, int x, int y,
+                                      uint32_t bits, float inv, float (&h)[9]) {
+  const Geometry &g = p.g;
+#pragma unroll
+  for (int i = 5; i < 9; i++) {
+    if (!nb(bits, OPP(i))) continue;
+    const int a = EX(i), b = EY(i);
+    const int sx = wrapi(x - a, g.nx), sy = wrapi(y - b, g.ny);
+    const float R = p.Rmap ? __ldg(p.Rmap + (size_t)c * g.plane + (size_t)sy * g.pitch + sx) : p.slipR[c];
+    if (!(R > 0.f)) continue;
+    int ex, ey, m;
+    if (solid_u(p, x, y - b) == 1 && solid_u(p, x - 2 * a, y - b) == 1 && solid_u(p, x - a, y) == 0 &&
+        solid_u(p, x - 2 * a, y) == 0) {
+      ex = x - 2 * a;
+      ey = y;
+      m = (-b > 0) ? (a > 0 ? 5 : 6) : (a > 0 ? 8 : 7);
+    } else if (solid_u(p, x - a, y) == 1 && solid_u(p, x - a, y - 2 * b) == 1 && solid_u(p, x, y - b) == 0 &&
+               solid_u(p, x, y - 2 * b) == 0) {
+      ex = x;
+      ey = y - 2 * b;
+      m = (b > 0) ? (-a > 0 ? 5 : 6) : (-a > 0 ? 8 : 7);
+    } else {
+      continue;
+    }
+    ex = wrapi(ex, g.nx);
+    ey = wrapi(ey, g.ny);
+    const float fs = Store<S>::ld(base, (size_t)m * g.plane + (size_t)ey * g.pitch + ex, inv);
+    h[i] = R * fs + (1.0f - R) * h[i];
+  }
+}
+
+// diagonal-neighbour bits of the 3 x 3 neighbourhood (sources of 5..8)
+constexpr uint32_t DIAG_BITS = (1u << NBPOS(-1, -1)) | (1u << NBPOS(1, -1)) | (1u << NBPOS(-1, 1)) |
+                               (1u << NBPOS(1, 1));
+
 constexpr int LOC_BY = 8;
 
 template <class S, int NC, bool ME>
@@ -107,6 +166,11 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid
 #pragma unroll
   for (int c = 0; c < NC; c++)
     pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
+  if (p.slip && (bits & DIAG_BITS)) {
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+      slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, p.inv_scale, h[c]);
+  }
   if (p.nopen) apply_openings<NC>(p, x, y, h);
   float F[NC][2];
 #pragma unroll
@@ -116,7 +180,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid
 
 constexpr int SC_TX = 32, SC_TY = 16;
 
-template <class S, int NC>
+template <class S, int NC, bool SLIP>
 __global__ void __launch_bounds__(SC_TX *SC_TY, 2) k_fluid_sc(const FluidArgs p) {
   // rho - rho_ref of every component for the tile and a one-node ring; slot
   // (ty + 1, tx + 1) holds node (x0 + tx, y0 + ty) wrapped periodically.
@@ -138,6 +202,8 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 2) k_fluid_sc(const FluidArgs p)
     float d = 0.f;
     if (!solid) {
       pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
+      if (SLIP && (bits & DIAG_BITS))
+        slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, p.inv_scale, h[c]);
 #pragma unroll
       for (int i = 0; i < 9; i++) d += h[c][i];
     }
@@ -163,6 +229,8 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 2) k_fluid_sc(const FluidArgs p)
       if (!hs) {
         float hh[9];
         pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, hx, hy, hb, p.inv_scale, hh);
+        if (SLIP && (hb & DIAG_BITS))
+          slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, hx, hy, hb, p.inv_scale, hh);
 #pragma unroll
         for (int i = 0; i < 9; i++) d += hh[i];
       }
@@ -254,8 +322,13 @@ template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
     dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.ny + SC_TY - 1) / SC_TY);
-    if (nc == 1) k_fluid_sc<S, 1><<<grd, blk, 0, s>>>(a);
-    else k_fluid_sc<S, 2><<<grd, blk, 0, s>>>(a);
+    if (a.slip) {
+      if (nc == 1) k_fluid_sc<S, 1, true><<<grd, blk, 0, s>>>(a);
+      else k_fluid_sc<S, 2, true><<<grd, blk, 0, s>>>(a);
+    } else {
+      if (nc == 1) k_fluid_sc<S, 1, false><<<grd, blk, 0, s>>>(a);
+      else k_fluid_sc<S, 2, false><<<grd, blk, 0, s>>>(a);
+    }
   } else {
     dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
     if (nc == 1) {

@@ -74,6 +74,12 @@ struct lb_ctx {
   double rho_ref[2] = {1, 1};
   float scale = 1.f, inv_scale = 1.f;
   std::vector<uint8_t> solid, region;
+  // boundary_style: 0 noslip, 1 slip, 2 mixed (slipR), 3 hybrid (Rh per
+  // solid node and component, from the styled obstacle calls)
+  int bstyle = 0;
+  double slipR = 0.0;
+  std::vector<float> Rh[2];
+  float *Rmap = nullptr;
   std::vector<double> paint_f[2], paint_C;
   bool painted_f[2] = {false, false}, painted_C = false;
   bool state_set[2] = {false, false}, solute_set = false;
@@ -335,6 +341,21 @@ int commit(lb_ctx *ctx) {
       if (ctx->solid[(size_t)y * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
   CK(cudaMemcpyAsync(ctx->mask, m.data(), m.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
 
+  // hybrid boundary style: per-node reflection coefficients (0 on fluid
+  // nodes, so nodes that grow solid later are noslip)
+  if (ctx->bstyle == 3) {
+    TRY(dalloc(ctx, &ctx->Rmap, (size_t)ctx->nc * g.plane));
+    std::vector<float> rh((size_t)ctx->nc * g.plane, 0.0f);
+    for (int c = 0; c < ctx->nc; c++)
+      for (int y = 0; y < g.ny; y++)
+        for (int x = 0; x < g.nx; x++) {
+          const size_t n = (size_t)y * g.nx + x;
+          if (ctx->solid[n]) rh[(size_t)c * g.plane + (size_t)y * g.pitch + x] = ctx->Rh[c][n];
+        }
+    CK(cudaMemcpyAsync(ctx->Rmap, rh.data(), rh.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+
   // initial deposit b0 on every solid node (surface_reaction command)
   if (ctx->react) {
     std::vector<double> bh(g.plane, 0.0);
@@ -429,6 +450,13 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;
   a.step_seed = (uint32_t)(z >> 32);
   if (ctx->sr) a.sr_seed = (uint32_t)z | 1u;
+  a.slip = ctx->bstyle != 0 ? 1 : 0;
+  a.slipR[0] = a.slipR[1] = (float)(ctx->bstyle == 1 ? 1.0 : ctx->bstyle == 2 ? ctx->slipR : 0.0);
+  a.Rmap = ctx->bstyle == 3 ? ctx->Rmap : nullptr;
+  for (const Opening &o : ctx->open) {
+    if (o.wall <= 1) a.edge_x = 1;
+    else a.edge_y = 1;
+  }
   return a;
 }
 
@@ -485,10 +513,10 @@ int one_step(lb_ctx *ctx, bool fields) {
   // two components and Shan-Chen runs keep |f - w rho_ref| large: their
   // collision is the mass-exact one
   const bool mass_exact = ctx->nc == 2 || ctx->sc;
-  const bool tma_ok = ctx->nc == 1 && !ctx->sc && tma_supported(ctx->storage, ctx->g);
+  const bool tma_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0 && tma_supported(ctx->storage, ctx->g);
   if (ctx->kernel == 2 && !tma_ok)
-    return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component lattices without interforce "
-                     "whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
+    return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component noslip lattices without "
+                     "interforce whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
   if (tma_ok && ctx->kernel == 2)
     LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, s, ctx->sms));
   else
@@ -611,7 +639,7 @@ int lb_destroy(lb_ctx *ctx) {
   void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
-                  ctx->errw,    ctx->Cpre};
+                  ctx->errw,    ctx->Cpre,    ctx->Rmap};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -712,15 +740,47 @@ int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref, double h_max
   return LB_OK;
 }
 
-int lb_boundary_style(lb_ctx *ctx, const char *style) {
+int lb_boundary_style(lb_ctx *ctx, const char *style, double R) {
   NEED_CTX();
   TRY(paint_check(ctx));
   if (!style) return ctx->fail(LB_E_ARG, "no style");
-  if (!strcmp(style, "slip") || !strcmp(style, "mixed") || !strcmp(style, "hybrid"))
-    return ctx->fail(LB_E_UNSUPPORTED, "boundary style '%s' is not built (noslip only)", style);
-  if (strcmp(style, "noslip")) return ctx->fail(LB_E_ARG, "unknown boundary style '%s'", style);
+  if (!strcmp(style, "noslip")) ctx->bstyle = 0;
+  else if (!strcmp(style, "slip")) ctx->bstyle = 1;
+  else if (!strcmp(style, "mixed")) {
+    if (!(R >= 0.0 && R <= 1.0)) return ctx->fail(LB_E_ARG, "reflection coefficient must lie in [0, 1]");
+    ctx->bstyle = 2;
+    ctx->slipR = R;
+  } else if (!strcmp(style, "hybrid")) {
+    ctx->bstyle = 3;
+    for (int c = 0; c < 2; c++) ctx->Rh[c].assign(ctx->solid.size(), 0.0f);
+  } else {
+    return ctx->fail(LB_E_ARG, "unknown boundary style '%s'", style);
+  }
   ctx->have_style = true;
   return LB_OK;
+}
+
+// style name and argument of the styled obstacle calls -> R
+static int style_R(lb_ctx *ctx, const char *style, double arg, float *R) {
+  if (!style || !strcmp(style, "noslip")) *R = 0.0f;
+  else if (!strcmp(style, "slip")) *R = 1.0f;
+  else if (!strcmp(style, "mixed")) {
+    if (!(arg >= 0.0 && arg <= 1.0)) return ctx->fail(LB_E_ARG, "reflection coefficient must lie in [0, 1]");
+    *R = (float)arg;
+  } else {
+    return ctx->fail(LB_E_ARG, "obstacle style must be noslip, slip or mixed");
+  }
+  return LB_OK;
+}
+
+// record R1 (fluid 1) and R2 (fluid 2) on the nodes a region marks
+static void paint_R(lb_ctx *ctx, const std::vector<uint8_t> &m, float R1, float R2) {
+  if (ctx->bstyle != 3) return;
+  for (size_t n = 0; n < m.size(); n++)
+    if (m[n]) {
+      ctx->Rh[0][n] = R1;
+      ctx->Rh[1][n] = R2;
+    }
 }
 
 static int obstacle_check(lb_ctx *ctx) {
@@ -729,13 +789,25 @@ static int obstacle_check(lb_ctx *ctx) {
   return LB_OK;
 }
 
-int lb_obstacle_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1) {
+int lb_obstacle_rect_styled(lb_ctx *ctx, int x0, int x1, int y0, int y1, const char *style1, double arg1,
+                            const char *style2, double arg2) {
   NEED_CTX();
   TRY(obstacle_check(ctx));
   if (x0 > x1 || y0 > y1) return ctx->fail(LB_E_ARG, "rectangle bounds must be ordered");
+  float R1, R2;
+  TRY(style_R(ctx, style1, arg1, &R1));
+  TRY(style_R(ctx, style2 ? style2 : style1, style2 ? arg2 : arg1, &R2));
+  std::vector<uint8_t> m(ctx->solid.size(), 0);
   for (int y = std::max(y0, 0); y <= std::min(y1, ctx->ny - 1); y++)
-    for (int x = std::max(x0, 0); x <= std::min(x1, ctx->nx - 1); x++) ctx->solid[(size_t)y * ctx->nx + x] = 1;
+    for (int x = std::max(x0, 0); x <= std::min(x1, ctx->nx - 1); x++) m[(size_t)y * ctx->nx + x] = 1;
+  for (size_t n = 0; n < m.size(); n++)
+    if (m[n]) ctx->solid[n] = 1;
+  paint_R(ctx, m, R1, R2);
   return LB_OK;
+}
+
+int lb_obstacle_rect(lb_ctx *ctx, int x0, int x1, int y0, int y1) {
+  return lb_obstacle_rect_styled(ctx, x0, x1, y0, y1, nullptr, 0.0, nullptr, 0.0);
 }
 
 static void circle_paint(lb_ctx *ctx, std::vector<uint8_t> &m, int xc, int yc, int r, uint8_t v) {
@@ -749,22 +821,49 @@ static void circle_paint(lb_ctx *ctx, std::vector<uint8_t> &m, int xc, int yc, i
     }
 }
 
-int lb_obstacle_circle(lb_ctx *ctx, int xc, int yc, int r) {
+int lb_obstacle_circle_styled(lb_ctx *ctx, int xc, int yc, int r, const char *style1, double arg1,
+                              const char *style2, double arg2) {
   NEED_CTX();
   TRY(obstacle_check(ctx));
   if (r < 0) return ctx->fail(LB_E_ARG, "negative radius");
-  circle_paint(ctx, ctx->solid, xc, yc, r, 1);
+  float R1, R2;
+  TRY(style_R(ctx, style1, arg1, &R1));
+  TRY(style_R(ctx, style2 ? style2 : style1, style2 ? arg2 : arg1, &R2));
+  std::vector<uint8_t> m(ctx->solid.size(), 0);
+  circle_paint(ctx, m, xc, yc, r, 1);
+  for (size_t n = 0; n < m.size(); n++)
+    if (m[n]) ctx->solid[n] = 1;
+  paint_R(ctx, m, R1, R2);
   return LB_OK;
 }
 
-int lb_obstacle_mask(lb_ctx *ctx, const uint8_t *mask) {
+int lb_obstacle_circle(lb_ctx *ctx, int xc, int yc, int r) {
+  return lb_obstacle_circle_styled(ctx, xc, yc, r, nullptr, 0.0, nullptr, 0.0);
+}
+
+int lb_obstacle_mask_hybrid(lb_ctx *ctx, const uint8_t *mask, const double *R) {
   NEED_CTX();
   TRY(obstacle_check(ctx));
   if (!mask) return ctx->fail(LB_E_ARG, "null mask");
-  for (size_t n = 0; n < ctx->solid.size(); n++)
-    if (mask[n]) ctx->solid[n] = 1;
+  const size_t nn = ctx->solid.size();
+  if (R) {
+    if (ctx->bstyle != 3) return ctx->fail(LB_E_ORDER, "per-node reflection coefficients need boundary_style hybrid");
+    for (size_t n = 0; n < (size_t)ctx->nc * nn; n++)
+      if (mask[n % nn] && !(R[n] >= 0.0 && R[n] <= 1.0))
+        return ctx->fail(LB_E_ARG, "reflection coefficient must lie in [0, 1]");
+  }
+  for (size_t n = 0; n < nn; n++)
+    if (mask[n]) {
+      ctx->solid[n] = 1;
+      if (ctx->bstyle == 3) {
+        ctx->Rh[0][n] = R ? (float)R[n] : 0.0f;
+        ctx->Rh[1][n] = R ? (float)R[(ctx->nc > 1 ? nn : 0) + n] : 0.0f;
+      }
+    }
   return LB_OK;
 }
+
+int lb_obstacle_mask(lb_ctx *ctx, const uint8_t *mask) { return lb_obstacle_mask_hybrid(ctx, mask, nullptr); }
 
 static int add_opening(lb_ctx *ctx, int kind, const char *wall, int a0, int a1, const char *l1,
                        const char *l2) {
@@ -1516,8 +1615,8 @@ int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out) {
     lb_ctx *c = ctxs[k];
     int rc = LB_OK;
     if (!c) rc = LB_E_ARG;
-    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0])
-      rc = c->fail(LB_E_UNSUPPORTED, "batched lattices are periodic single-component lattices with body forces");
+    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0] || c->bstyle != 0)
+      rc = c->fail(LB_E_UNSUPPORTED, "batched lattices are periodic single-component noslip lattices with body forces");
     else {
       for (int s = 0; s < c->nc && rc == LB_OK; s++)
         if (!c->painted_f[s] && !c->state_set[s]) rc = c->fail(LB_E_ORDER, "lattice %d has no initial state", k);

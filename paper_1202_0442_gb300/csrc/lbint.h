@@ -68,6 +68,13 @@ struct FluidArgs {
   uint32_t sr_seed;       // 16-bit stores: 0 = round to nearest, else the
                           // step's seed of the stochastic-rounding dither
   uint32_t step_seed;     // per-iteration seed of the mass-exact collision
+  // boundary_style slip/mixed/hybrid: reflection coefficient R of the solid
+  // nodes, uniform (slipR) or per node (Rmap [nc][plane], read on solid
+  // nodes); edge_x/edge_y: the x/y edge carries an opening (not periodic)
+  int slip;
+  float slipR[2];
+  const float *Rmap;
+  int edge_x, edge_y;
 };
 
 // gradient openings (after collision)

@@ -67,10 +67,13 @@ SIGNATURES = {
     "lb_fluids": (I, [P, D, D, D, D]),
     "lb_solute": (I, [P, D, I]),
     "lb_set_storage": (I, [P, I, DP, D]),
-    "lb_boundary_style": (I, [P, S]),
+    "lb_boundary_style": (I, [P, S, D]),
     "lb_obstacle_rect": (I, [P, I, I, I, I]),
     "lb_obstacle_circle": (I, [P, I, I, I]),
     "lb_obstacle_mask": (I, [P, U8P]),
+    "lb_obstacle_rect_styled": (I, [P, I, I, I, I, S, D, S, D]),
+    "lb_obstacle_circle_styled": (I, [P, I, I, I, S, D, S, D]),
+    "lb_obstacle_mask_hybrid": (I, [P, U8P, DP]),
     "lb_inlet": (I, [P, S, I, I, S, S]),
     "lb_outlet": (I, [P, S, I, I, S, S]),
     "lb_inlet_momentum": (I, [P, S, S, D, D]),
@@ -205,8 +208,20 @@ class Lattice:
         code = STORAGE[storage] | (LB_STOCHASTIC_ROUNDING if rounding == "stochastic" else 0)
         self._ck(self._L.lb_set_storage(self._h, code, _dp(r), h_max))
 
-    def boundary_style(self, style: str = "noslip"):
-        self._ck(self._L.lb_boundary_style(self._h, _b(style)))
+    def boundary_style(self, style: str = "noslip", R: float = 0.0):
+        self._ck(self._L.lb_boundary_style(self._h, _b(style), R))
+
+    def obstacle_rect_styled(self, x0, x1, y0, y1, style1=None, arg1=0.0, style2=None, arg2=0.0):
+        self._ck(self._L.lb_obstacle_rect_styled(self._h, x0, x1, y0, y1, _b(style1), arg1, _b(style2), arg2))
+
+    def obstacle_circle_styled(self, xc, yc, r, style1=None, arg1=0.0, style2=None, arg2=0.0):
+        self._ck(self._L.lb_obstacle_circle_styled(self._h, xc, yc, r, _b(style1), arg1, _b(style2), arg2))
+
+    def obstacle_mask_hybrid(self, mask: np.ndarray, R: Optional[np.ndarray] = None):
+        """mask [ny][nx]; R [ncomp][ny][nx] (or [ny][nx] for one component)"""
+        m = np.ascontiguousarray(mask, np.uint8).reshape(self.ny, self.nx)
+        r = None if R is None else np.ascontiguousarray(R, np.float64).reshape(-1, self.ny, self.nx)
+        self._ck(self._L.lb_obstacle_mask_hybrid(self._h, m.ctypes.data_as(U8P), _dp(r)))
 
     def obstacle_rect(self, x0, x1, y0, y1):
         self._ck(self._L.lb_obstacle_rect(self._h, x0, x1, y0, y1))
@@ -445,13 +460,27 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
     if w.ncomp == 2:
-        lt.fluids(w.tau[0], w.tau[1], w.alpha[0], w.alpha[1])
+        al = list(w.alpha) + [4.0 / 9.0] * (2 - len(w.alpha))
+        lt.fluids(w.tau[0], w.tau[1], al[0], al[1])
     if w.solute_q:
         lt.solute(w.taus, w.solute_q)
     lt.set_storage(storage, list(w.rho_ref), h_max, rounding)
-    lt.boundary_style("noslip")
-    if w.solid.any():
-        lt.obstacle_mask(w.solid)
+    slip = list(getattr(w, "slip", None) or ())
+    if any(np.ndim(R) > 0 for R in slip if R is not None):
+        # hybrid: per-node coefficients, per component
+        lt.boundary_style("hybrid")
+        Rm = np.stack([np.zeros((w.ny, w.nx)) if (s >= len(slip) or slip[s] is None)
+                       else np.broadcast_to(np.asarray(slip[s], np.float64), (w.ny, w.nx))
+                       for s in range(w.ncomp)])
+        lt.obstacle_mask_hybrid(w.solid, Rm)
+    else:
+        Rs = {float(R) for R in slip if R is not None}
+        if len(Rs) > 1 or (Rs and len([R for R in slip if R is not None]) != w.ncomp):
+            raise ValueError("components with different uniform coefficients need per-node maps")
+        R = Rs.pop() if Rs else 0.0
+        lt.boundary_style("noslip" if R == 0.0 else "slip" if R == 1.0 else "mixed", R)
+        if w.solid.any():
+            lt.obstacle_mask(w.solid)
     for k, op in enumerate(w.openings):
         labels = [f"o{k}f{s}" for s in range(w.ncomp)]
         (lt.inlet if op.kind == "inlet" else lt.outlet)(op.wall, op.a0, op.a1, labels[0],

@@ -75,6 +75,9 @@ class Workload:
     C: Optional[np.ndarray] = None                      # initial concentration
     reaction: Optional[Tuple[float, float, float, float, int]] = None  # kr, Cs, b0, bmax, seed
     intersolute: Optional[Tuple[float, float, float]] = None    # (G, psi0, C0)
+    # boundary_style per component: None (noslip), R (slip 1, mixed 0 < R < 1)
+    # or an [ny][nx] array of R on the solid nodes (hybrid)
+    slip: Optional[Sequence] = None
     steps: int = 1
     rho_ref: Sequence[float] = (1.0,)                   # typical density per component
     info: dict = field(default_factory=dict)

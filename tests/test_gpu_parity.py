@@ -319,6 +319,73 @@ def test_density_ratio_alpha(taus, alphas, G, init, storage):
 
 
 # ---------------------------------------------------------------------------
+# boundary_style slip / mixed / hybrid
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R", [1.0, 0.4, "map"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_slip_styles_random_media(R, storage):
+    """slip, mixed and hybrid (per-node coefficients) against the oracle on
+    a random medium with random populations, and mass kept."""
+    nx, ny = 72, 40
+    mask = synth.random_mask(nx, ny, 3, 0.25)
+    f = synth.random_populations(9, nx, ny, 4, W9, 0.2, mask)
+    slip = np.random.default_rng(2).choice([0.0, 0.3, 1.0], size=(ny, nx)) if R == "map" else R
+    w = synth.Workload(name="slip", nx=nx, ny=ny, solid=mask, rho=[np.where(mask, 0, 1.0)], tau=(0.8,),
+                       aveforce=((1e-4, -5e-5),), slip=[slip])
+    kw = {"h_max": 0.5, "rounding": "stochastic"} if storage != "fp32" else {}
+    lt = lb2d.from_workload(w, storage, **kw)
+    lt.set_populations(f)
+    o = oracle_from_workload(w)
+    o.set_f(f)
+    lt.iteration(60)
+    o.step(60)
+    e, _ = pop_err(lt, o)
+    assert e < (1e-5 if storage == "fp32" else 3e-3), e
+    errs, tg, to = thermo_err(lt, o, ["mass1"])
+    assert errs["mass1"] < (1e-9 if storage == "fp32" else 1e-5), errs
+
+
+def test_slip_channel_with_openings():
+    """Pressure-driven channel between slip walls with Zou-He openings: the
+    mirror paths that would cross the x edge (it carries the openings) are
+    bounced back, and the flow matches the oracle."""
+    nx, ny = 96, 26
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    solid[10:16, 40:46] = 1
+    w = synth.Workload(name="slipch", nx=nx, ny=ny, solid=solid, rho=[np.where(solid, 0, 1.0)], tau=(0.7,),
+                       openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("dirichlet", 0.0, 1.002)]),
+                                 synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0.0, 1.0)])],
+                       slip=[0.7])
+    lt, o = run_pair(w, 500)
+    assert rel_rho(lt, o, w) < TOL32
+    assert rel_u(lt, o) < TOL32
+
+
+@pytest.mark.parametrize("sc", [False, True])
+def test_slip_two_components(sc):
+    """hybrid per-component coefficients with two fluids, with and without
+    interforce (the Shan-Chen kernel's slip variant)."""
+    nx, ny = 64, 48
+    mask = synth.random_mask(nx, ny, 5, 0.15)
+    rng = np.random.default_rng(7)
+    R1 = rng.choice([0.0, 1.0], size=(ny, nx))
+    R2 = rng.choice([0.0, 0.5], size=(ny, nx))
+    r1 = np.where(mask, 0, synth.noise_field(nx, ny, 1, 0.6, 0.8))
+    r2 = np.where(mask, 0, synth.noise_field(nx, ny, 2, 0.2, 0.4))
+    w = synth.Workload(name="slip2", nx=nx, ny=ny, solid=mask, rho=[r1, r2], tau=(0.9, 1.2),
+                       aveforce=((1e-4, 0.0), (0.0, 1e-4)), interforce=(0.5, 0.0, 0.0) if sc else None,
+                       slip=[R1, R2], rho_ref=(0.7, 0.3))
+    lt, o = run_pair(w, 150)
+    for c in (1, 2):
+        assert rel_rho(lt, o, w, comp=c) < TOL32
+    assert rel_u(lt, o) < (1e-4 if sc else TOL32)
+    errs, tg, to = thermo_err(lt, o, ["mass1", "mass2"])
+    assert errs["mass1"] < 1e-9 and errs["mass2"] < 1e-9, errs
+
+
+# ---------------------------------------------------------------------------
 # solute, reaction, growth
 # ---------------------------------------------------------------------------
 
@@ -533,8 +600,11 @@ def test_order_and_argument_errors():
         lt.obstacle_rect(0, 3, 0, 3)
     assert ei.value.code == lb2d.LB_E_ORDER
     with pytest.raises(E) as ei:
-        lt.boundary_style("slip")
-    assert ei.value.code == lb2d.LB_E_UNSUPPORTED
+        lt.boundary_style("mixed", 1.5)
+    assert ei.value.code == lb2d.LB_E_ARG
+    with pytest.raises(E) as ei:
+        lt.boundary_style("rough")
+    assert ei.value.code == lb2d.LB_E_ARG
     with pytest.raises(E) as ei:
         lt.momentum0(0, 1.0)
     assert ei.value.code == lb2d.LB_E_ORDER

@@ -313,6 +313,125 @@ def test_taylor_green_decay(tau):
 
 
 # --------------------------------------------------------------------------
+# boundary_style slip / mixed / hybrid
+# --------------------------------------------------------------------------
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.mark.parametrize("R", [1.0, 0.4, "map"])
+def test_slip_conserves_mass(R):
+    """Slip and mixed reflection move every population to exactly one
+    place (each mirror reflection is paired with its reverse): sum f is
+    kept with random masks, random populations, slip, mixed and a random
+    per-node (hybrid) coefficient map."""
+    nx, ny = 40, 30
+    mask = synth.random_mask(nx, ny, 3, 0.25)
+    f = synth.random_populations(9, nx, ny, 4, W9, 0.3, mask)
+    o = Oracle(nx, ny)
+    o.set_solid(mask)
+    o.set_tau(0.8)
+    if R == "map":
+        o.set_slip(0.0, np.random.default_rng(2).choice([0.0, 0.3, 1.0], size=(ny, nx)))
+    else:
+        o.set_slip(R)
+    o.set_f(f)
+    m0 = o.f().sum()
+    o.step(60)
+    assert abs(o.f().sum() - m0) / m0 < 1e-13
+
+
+def test_slip_walls_exert_no_drag():
+    """A force-driven channel between flat slip (mirror) walls has no wall
+    friction: the state stays uniform across the channel and the reported
+    momentum after n steps is exactly N F (n - 1/2), as in a periodic box;
+    with noslip walls it is smaller."""
+    nx, ny, g, n = 16, 12, 1e-5, 300
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    out = {}
+    for R in (1.0, 0.0):
+        o = Oracle(nx, ny)
+        o.set_solid(solid)
+        o.set_tau(0.9)
+        o.set_aveforce(g, 0.0)
+        o.set_slip(R)
+        o.set_equilibrium(np.where(solid, 0.0, 1.0))
+        o.step(n)
+        r, px, py, _ = o.fields()
+        out[R] = px[1:-1]
+    N = nx * (ny - 2)
+    assert abs(out[1.0].sum() - N * g * (n - 0.5)) < 1e-12 * N * g * n
+    assert np.ptp(out[1.0]) < 1e-15
+    assert out[0.0].sum() < 0.9 * out[1.0].sum()
+
+
+def _transpose_pops(f):
+    """populations of the lattice mirrored about the diagonal x <-> y:
+    direction (a, b) becomes (b, a)"""
+    perm = [0, 2, 1, 4, 3, 5, 8, 7, 6]
+    return np.ascontiguousarray(np.transpose(f[perm], (0, 2, 1)))
+
+
+@pytest.mark.parametrize("R", [1.0, 0.6, "map"])
+def test_slip_is_symmetric_under_transposition(R):
+    """The slip rule's horizontal- and vertical-wall cases swap under the
+    mirror x <-> y: a run on the transposed lattice, from the transposed
+    state, must give the transposed result (a wrong index in either case
+    breaks this)."""
+    nx, ny = 36, 28
+    mask = synth.random_mask(nx, ny, 8, 0.2)
+    f = synth.random_populations(9, nx, ny, 9, W9, 0.2, mask)
+    Rm = np.random.default_rng(4).choice([0.0, 0.5, 1.0], size=(ny, nx)) if R == "map" else None
+    res = []
+    for tr in (False, True):
+        o = Oracle(ny, nx) if tr else Oracle(nx, ny)
+        o.set_solid(mask.T.copy() if tr else mask)
+        o.set_tau(0.7)
+        o.set_aveforce(*((2e-4, 1e-4)[::-1] if tr else (2e-4, 1e-4)))
+        if R == "map":
+            o.set_slip(0.0, Rm.T.copy() if tr else Rm)
+        else:
+            o.set_slip(R)
+        o.set_f(_transpose_pops(f) if tr else f)
+        o.step(40)
+        res.append(o.f())
+    assert np.max(np.abs(_transpose_pops(res[1]) - res[0])) < 1e-15
+
+
+def test_mixed_slip_channel_profile():
+    """mixed style, R = 0.5, force-driven channel: a steady profile that is
+    a parabola (second differences all equal to -g/nu, as with noslip)
+    whose value at the half-way wall is a slip velocity (noslip: ~0), and a
+    flux between the noslip and the (unbounded) slip cases."""
+    nx, ny, g, tau = 4, 22, 1e-6, 1.0
+    nu = (tau - 0.5) / 3
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    flux = {}
+    prof = {}
+    for R in (0.0, 0.5):
+        o = Oracle(nx, ny)
+        o.set_solid(solid)
+        o.set_tau(tau)
+        o.set_aveforce(g, 0.0)
+        o.set_slip(R)
+        o.set_equilibrium(np.where(solid, 0.0, 1.0))
+        o.step(30000)
+        r, px, py, _ = o.fields()
+        u = px[1:-1, 0] / r[1:-1, 0]
+        prof[R] = u
+        flux[R] = u.sum()
+    d2 = np.diff(prof[0.5], 2)
+    assert np.max(np.abs(d2 + g / nu)) < 1e-3 * g / nu
+    assert flux[0.5] > 1.1 * flux[0.0]
+    # the parabola through the profile, evaluated at the half-way wall
+    y = np.arange(1, ny - 1, dtype=float)
+    wall = {R: np.polyval(np.polyfit(y, prof[R], 2), 0.5) / prof[R].max() for R in prof}
+    assert abs(wall[0.0]) < 1e-2 and wall[0.5] > 0.05, wall
+
+
+# --------------------------------------------------------------------------
 # inlet/outlet openings (inlet_momentum/outlet_momentum, App. A)
 # --------------------------------------------------------------------------
 
