@@ -219,42 +219,80 @@ def variants(args, local, stream, flush, value_fp32):
                    "rounding": "stochastic", "tolerance_met": "2e-3 (FP16) / 1e-2 (BF16) rel. u, parity tests",
                    "kernel_ms": float(np.median(t))}
         del lt
-    # config 5: 256 periodic porous lattices, sides 64..512
+    # config 5: 256 periodic porous lattices, sides 64..512, one persistent
+    # launch per iteration against one launch per lattice, FP32 and FP16
     ws = synth.batch()
-    lats = [lb2d.from_workload(x, "fp32", device=local, stream=stream.cuda_stream) for x in ws]
-    for lt in lats:
-        lt.thermo(1 << 30)
     nodes = sum(x.nodes for x in ws)
-    b = lb2d.Batch(lats)
-    b.autotune(None)
-    b.iteration(20, use_graph=True)
-    torch.cuda.synchronize()
-    n = 100
+    fluid = sum(x.fluid_nodes for x in ws)
+    peak = peaks()[0]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.iteration(n, use_graph=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / n
-    for lt in lats:
-        lt.iteration(2)
-    torch.cuda.synchronize()
-    m = 10
-    e0.record(stream)
-    for _ in range(m):
+    for st in ("fp32", "fp16"):
+        kw = {"h_max": 5e-3, "rounding": "stochastic"} if st != "fp32" else {}
+        lats = [lb2d.from_workload(x, st, device=local, stream=stream.cuda_stream, **kw) for x in ws]
         for lt in lats:
-            lt.iteration(1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1) / m
-    out["batched"] = {"workload": f"{len(ws)} periodic porous lattices, sides 64-512 step 32, "
-                                  f"porosity 0.4-0.9, tau 0.6-1.5 ({nodes} nodes)",
-                      "mlups_one_launch": nodes / (ms_b * 1e-3) / 1e6,
-                      "mlups_one_launch_per_lattice": nodes / (ms_s * 1e-3) / 1e6,
-                      "speedup": ms_s / ms_b, "ms_per_iteration_batched": ms_b,
-                      "ms_per_iteration_per_lattice": ms_s, "graph": True,
-                      "state_bytes": int(2 * 36 * nodes)}
-    del b, lats
+            lt.thermo(1 << 30)
+        b = lb2d.Batch(lats)
+        b.autotune(None)
+        b.iteration(20, use_graph=True)
+        torch.cuda.synchronize()
+        n = 100
+        e0.record(stream)
+        b.iteration(n, use_graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / n
+        for lt in lats:
+            lt.iteration(2)
+        torch.cuda.synchronize()
+        m = 10
+        e0.record(stream)
+        for _ in range(m):
+            for lt in lats:
+                lt.iteration(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / m
+        bpn = BYTES_PER_FLUID_NODE[st]
+        out["batched" if st == "fp32" else "batched_fp16"] = {
+            "workload": f"{len(ws)} periodic porous lattices, sides 64-512 step 32, "
+                        f"porosity 0.4-0.9, tau 0.6-1.5 ({nodes} nodes, {fluid} fluid)",
+            "storage": st,
+            "mlups_one_launch": nodes / (ms_b * 1e-3) / 1e6,
+            "mlups_one_launch_per_lattice": nodes / (ms_s * 1e-3) / 1e6,
+            "speedup": ms_s / ms_b, "ms_per_iteration_batched": ms_b,
+            "ms_per_iteration_per_lattice": ms_s, "graph": True,
+            "roofline_frac": bpn * fluid / (ms_b * 1e-3) / 1e9 / peak,
+            "state_bytes": int(2 * bpn * nodes)}
+        del b, lats
+    out["batched_fp16"]["speedup_vs_fp32_batched"] = (out["batched"]["ms_per_iteration_batched"]
+                                                     / out["batched_fp16"]["ms_per_iteration_batched"])
+    # config 3: two components with interforce and adhesion, 2048^2
+    w3 = synth.shan_chen2(2048)
+    lt = lb2d.from_workload(w3, "fp32", device=local, stream=stream.cuda_stream)
+    lt.thermo(1 << 30)
+    time_steps(lt, 5, flush, stream)
+    t = time_steps(lt, min(args.steps, 40), flush, stream)
+    ms = float(t.mean())
+    out["shan_chen2_2048"] = {
+        "workload": "2048^2 periodic, two components, interforce G = 0.9, adhesive ring +-0.3",
+        "kernel": "k_fluid_sc", "value": w3.nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+        "ms_per_step": ms, "bytes_per_fluid_node": 144,
+        "roofline_frac": 144 * w3.fluid_nodes / (ms * 1e-3) / 1e9 / peak}
+    del lt
+    # config 4: fluid + D2Q9 solute + reaction + growth, 1024 x 512
+    w4 = synth.reactive()
+    lt = lb2d.from_workload(w4, "fp32", device=local, stream=stream.cuda_stream)
+    lt.thermo(1 << 30)
+    time_steps(lt, 5, flush, stream)
+    t = time_steps(lt, min(args.steps, 40), flush, stream)
+    ms = float(t.mean())
+    out["reactive_1024x512_q9"] = {
+        "workload": "1024 x 512 channel, 40 discs, velocity inlet 0.02, D2Q9 solute, reaction and growth",
+        "kernels": "k_fluid_local + k_solute<9> + k_gather_grow + k_apply_flips",
+        "value": w4.nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+        "bytes_per_fluid_node": 160,
+        "roofline_frac": 160 * w4.fluid_nodes / (ms * 1e-3) / 1e9 / peak}
+    del lt
     return out
 
 

@@ -20,9 +20,9 @@
 // k_gather_grow: every solid node adds its fluid neighbours' shares to its
 //   FP64 deposit b in a fixed order, and, if b > bmax, picks one fluid
 //   4-neighbour (SplitMix64 of seed ^ (t nx ny + node) mod the number of
-//   candidates, in the order +x, +y, -x, -y) and marks it; b := 0.
-// k_apply_flips: marked nodes become solid (mask bit), start with b0, and
-//   their fluid and solute mass is booked as removed.
+//   candidates, in the order +x, +y, -x, -y), flags and lists it; b := 0.
+// k_apply_flips: one CTA walks the list: the nodes become solid (mask bit),
+//   start with b0, and their fluid and solute mass is booked as removed.
 // The two growth kernels run back to back, so every decision sees the
 // state before any flip.
 #include "lbdev.cuh"
@@ -53,27 +53,33 @@ __device__ __forceinline__ int opening_of(const OpenDesc *op, int nopen, int x, 
 // bounce-back, or the reaction rule on that link (then Ci is added to Cw,
 // the link counted in nU and flagged in U).  Modes crossing the wall of an
 // opening node (wall >= 0) are left 0 and flagged in `cross`.
+// `bits`: the node's 3 x 3 solid neighbourhood (bit NBPOS(dx, dy)).
 template <int Q>
-__device__ __forceinline__ void solute_pull(const SoluteArgs &p, int x, int y, int wall, float (&gt)[Q],
-                                            float &Cw, int &nU, uint32_t &U, uint32_t &cross) {
+__device__ __forceinline__ void solute_pull(const SoluteArgs &p, int x, int y, int wall, uint32_t bits,
+                                            float (&gt)[Q], float &Cw, int &nU, uint32_t &U, uint32_t &cross) {
   const Geometry &g = p.g;
-  const size_t self = (size_t)y * g.pitch + x;
+  const int self = y * g.pitch + x;
+  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const int rm = (y ? y - 1 : g.ny - 1) * g.pitch, r0 = y * g.pitch, rp = ((y + 1 == g.ny) ? 0 : y + 1) * g.pitch;
+  const int P = (int)g.plane;
   Cw = 0.f;
   nU = 0;
   U = 0;
   cross = 0;
 #pragma unroll
   for (int i = 0; i < Q; i++) {
-    if (wall >= 0 && crosses_wall(wall, sex<Q>(i), sey<Q>(i))) {
+    const int ex = sex<Q>(i), ey = sey<Q>(i);
+    if (wall >= 0 && crosses_wall(wall, ex, ey)) {
       cross |= 1u << i;
       gt[i] = 0.f;
       continue;
     }
-    const int xs = wrapi(x - sex<Q>(i), g.nx), ys = wrapi(y - sey<Q>(i), g.ny);
-    if (solid_at(p.mask, g.mw, xs, ys)) {
-      const float gout = __ldg(p.gin + (size_t)sopp<Q>(i) * g.plane + self);
+    if ((bits >> NBPOS(-ex, -ey)) & 1u) {
+      const float gout = __ldg(p.gin + sopp<Q>(i) * P + self);
       if (p.react) {
-        const float Ci = (2.0f * gout + p.kr * p.Cs) / (p.kr + 2.0f * sw<Q>(i));
+        // (2 g_out + kr Cs) / (kr + 2 w_i), the denominator's reciprocal
+        // precomputed per weight class
+        const float Ci = (2.0f * gout + p.kr * p.Cs) * (Q == 4 ? p.rden[0] : (i < 5 ? p.rden[0] : p.rden[1]));
         gt[i] = -gout + 2.0f * sw<Q>(i) * Ci;
         Cw += Ci;
         nU++;
@@ -82,9 +88,39 @@ __device__ __forceinline__ void solute_pull(const SoluteArgs &p, int x, int y, i
         gt[i] = gout;
       }
     } else {
-      gt[i] = __ldg(p.gin + (size_t)i * g.plane + (size_t)ys * g.pitch + xs);
+      const int xs = ex > 0 ? xm : (ex < 0 ? xp : x);
+      const int rs = ey > 0 ? rm : (ey < 0 ? rp : r0);
+      gt[i] = __ldg(p.gin + i * P + rs + xs);
     }
   }
+}
+
+// 3 x 3 solid neighbourhood of any node, straight from the mask
+__device__ __forceinline__ uint32_t solute_bits(const SoluteArgs &p, int x, int y) {
+  const Geometry &g = p.g;
+  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  return nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
+}
+
+// the warp's mask words (rows y-1, y, y+1 of word column blockIdx.x, edge
+// lanes also the words beside them) and this lane's neighbourhood from
+// them (the lattice's first and last column read the mask directly)
+__device__ __forceinline__ uint32_t solute_warp_bits(const SoluteArgs &p, int x, int y) {
+  const Geometry &g = p.g;
+  const int lane = threadIdx.x, cw = blockIdx.x;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw, p.mask + (size_t)yp * g.mw};
+  uint32_t w[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    w[r][1] = __ldg(rows[r] + cw);
+    w[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
+    w[r][2] = (lane == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
+  }
+  if (x == 0 || x == g.nx - 1) return solute_bits(p, x, y);
+  return row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
+         (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
 }
 
 // concentration of node (x, y) right after streaming, before any opening
@@ -97,7 +133,7 @@ __device__ float solute_streamed_C(const SoluteArgs &p, int x, int y) {
   float gt[Q], Cw;
   int nU;
   uint32_t U, cross;
-  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, solute_bits(p, x, y), gt, Cw, nU, U, cross);
   float C = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; i++) C += gt[i];
@@ -178,9 +214,11 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
-  if (x >= g.nx || y >= g.ny) return;
+  if (y >= g.ny) return;
+  const uint32_t bits = solute_warp_bits(p, x, y);
+  if (x >= g.nx) return;
   const size_t self = (size_t)y * g.pitch + x;
-  if (solid_at(p.mask, g.mw, x, y)) {
+  if ((bits >> 4) & 1u) {
     p.Cpre_out[self] = 0.f;
     return;
   }
@@ -188,7 +226,7 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
   float gt[Q], Cw, Cflux = 0.f;
   int nU;
   uint32_t U, cross;
-  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, bits, gt, Cw, nU, U, cross);
   bool flux = false;
   if (k >= 0) flux = solute_openings<Q>(p, p.op[k], x, y, gt, cross, Cflux);
   float C = 0.f;
@@ -202,14 +240,15 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
-  if (x >= g.nx || y >= g.ny) return;
-  if (solid_at(p.mask, g.mw, x, y)) return;
+  if (y >= g.ny) return;
+  const uint32_t bits = solute_warp_bits(p, x, y);
+  if (x >= g.nx || ((bits >> 4) & 1u)) return;
   const size_t self = (size_t)y * g.pitch + x;
   const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
   float gt[Q], Cw, Cflux = 0.f;
   int nU;
   uint32_t U, cross;
-  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, gt, Cw, nU, U, cross);
+  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, bits, gt, Cw, nU, U, cross);
   bool flux = false;
   if (k >= 0) flux = solute_openings<Q>(p, p.op[k], x, y, gt, cross, Cflux);
   float C = 0.f;
@@ -246,7 +285,7 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
 #pragma unroll
   for (int i = 0; i < Q; i++) gs[i] = gt[i] + om * (geq[i] - gt[i]);
   if (p.react && nU) {
-    const float share_n = 1.0f / (float)nU;
+    const float share_n = nU == 1 ? 1.0f : nU == 2 ? 0.5f : nU == 3 ? (1.0f / 3.0f) : nU == 4 ? 0.25f : 1.0f / (float)nU;
     const float dB = p.kr * (Cw * share_n - p.Cs);
     float share = 0.f;
     if (dB > 0.f) {
@@ -266,67 +305,112 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   if (p.Cfield) p.Cfield[self] = Cn;
 }
 
+// the warp's 3 x 3 mask neighbourhoods (as solute_warp_bits)
+__device__ __forceinline__ uint32_t growth_warp_bits(const GrowthArgs &a, int x, int y) {
+  const Geometry &g = a.g;
+  const int lane = threadIdx.x, cw = blockIdx.x;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  const uint32_t *rows[3] = {a.mask + (size_t)ym * g.mw, a.mask + (size_t)y * g.mw, a.mask + (size_t)yp * g.mw};
+  uint32_t w[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    w[r][1] = rows[r][cw];
+    w[r][0] = (lane == 0 && cw > 0) ? rows[r][cw - 1] : 0u;
+    w[r][2] = (lane == 31 && cw + 1 < g.mw) ? rows[r][cw + 1] : 0u;
+  }
+  if (x == 0 || x == g.nx - 1) {
+    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+    return nbr_bits(a.mask, g.mw, x, y, xm, xp, ym, yp);
+  }
+  return row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
+         (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
+}
+
+// Every solid node with a fluid neighbour adds the shares its fluid
+// neighbours set aside for it (in index order, FP64), and if b > bmax picks
+// one fluid 4-neighbour that is not an opening node (SplitMix64 of
+// seed ^ (t nx ny + node) mod the number of candidates, candidates in the
+// order +x, +y, -x, -y); the pick is flagged once and listed.  Solid nodes
+// without a fluid neighbour are untouched (their b cannot change).
 __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = a.g;
-  if (x >= g.nx || y >= g.ny) return;
-  if (!solid_at(a.mask, g.mw, x, y)) return;
+  if (y >= g.ny) return;
+  const uint32_t bits = growth_warp_bits(a, x, y);
+  if (x >= g.nx || !((bits >> 4) & 1u) || (bits | (1u << 4)) == 0x1ffu) return;
+  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
   const size_t self = (size_t)y * g.pitch + x;
   double acc = 0.0;
   const int q = a.q;
   for (int i = (q == 4 ? 0 : 1); i < q; i++) {
     const int ex = q == 4 ? EX4(i) : EX(i), ey = q == 4 ? EY4(i) : EY(i);
-    const int xf = wrapi(x + ex, g.nx), yf = wrapi(y + ey, g.ny);
-    if (solid_at(a.mask, g.mw, xf, yf)) continue;
+    if ((bits >> NBPOS(ex, ey)) & 1u) continue;
+    const int xf = ex > 0 ? xp : (ex < 0 ? xm : x), yf = ey > 0 ? yp : (ey < 0 ? ym : y);
     const int k = a.nopen ? opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) : -1;
     if (k >= 0 && crosses_wall(a.op[k].wall, ex, ey)) continue;
     acc += (double)__ldg(a.db + (size_t)yf * g.pitch + xf);
   }
   double b = a.b[self] + acc;
   if (b > a.bmax) {
-    long long cand[4];
+    unsigned int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     int n = 0;
+#pragma unroll
     for (int d = 0; d < 4; d++) {
-      const int xf = wrapi(x + EX4(d), g.nx), yf = wrapi(y + EY4(d), g.ny);
-      if (solid_at(a.mask, g.mw, xf, yf)) continue;
+      const int ex = EX4(d), ey = EY4(d);
+      if ((bits >> NBPOS(ex, ey)) & 1u) continue;
+      const int xf = ex > 0 ? xp : (ex < 0 ? xm : x), yf = ey > 0 ? yp : (ey < 0 ? ym : y);
       if (a.nopen && opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) >= 0) continue;
-      cand[n++] = (long long)yf * g.pitch + xf;
+      const unsigned int off = (unsigned int)(yf * g.pitch + xf);
+      if (n == 0) c0 = off;
+      else if (n == 1) c1 = off;
+      else if (n == 2) c2 = off;
+      else c3 = off;
+      n++;
     }
     if (n) {
       const uint64_t node = (uint64_t)y * (uint64_t)g.nx + (uint64_t)x;
       const uint64_t key = a.seed ^ ((uint64_t)a.t * (uint64_t)g.nx * (uint64_t)g.ny + node);
       const int pick = (int)(splitmix64(key) % (uint64_t)n);
-      a.flip[cand[pick]] = 1;
+      const unsigned int off = pick == 0 ? c0 : pick == 1 ? c1 : pick == 2 ? c2 : c3;
+      if (atomicExch(a.flip + off, 1u) == 0u) a.flist[atomicAdd(a.fcount, 1u)] = off;
       b = 0.0;
     }
   }
   a.b[self] = b;
 }
 
+// One CTA turns the listed nodes solid: mask bit, b = b0, their fluid and
+// solute mass booked as removed; then clears the list.  Flips of one step
+// are independent of each other, so their order does not matter.
 template <class S>
 __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = a.g;
-  if (x >= g.nx || y >= g.ny) return;
-  const size_t self = (size_t)y * g.pitch + x;
-  if (!a.flip[self]) return;
-  a.flip[self] = 0;
-  atomicOr(a.mask + (size_t)y * g.mw + (x >> 5), 1u << (x & 31));
-  a.b[self] = a.b0;
-  for (int c = 0; c < a.nc; c++) {
-    const S *f = (const S *)a.f + (size_t)c * 9 * g.plane;
-    float d = 0.f;
-    for (int i = 0; i < 9; i++) d += Store<S>::ld(f, (size_t)i * g.plane + self, a.inv_scale);
-    a.removed[(size_t)c * g.plane + self] += (double)a.rho_ref[c] + (double)d;
+  const unsigned int n = *a.fcount;
+  for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) {
+    const size_t self = a.flist[k];
+    const int y = (int)(self / (size_t)g.pitch), x = (int)(self - (size_t)y * g.pitch);
+    a.flip[self] = 0u;
+    atomicOr(a.mask + (size_t)y * g.mw + (x >> 5), 1u << (x & 31));
+    a.b[self] = a.b0;
+    for (int c = 0; c < a.nc; c++) {
+      const S *f = (const S *)a.f + (size_t)c * 9 * g.plane;
+      float d = 0.f;
+      for (int i = 0; i < 9; i++) d += Store<S>::ld(f, (size_t)i * g.plane + self, a.inv_scale);
+      a.removed[(size_t)c * g.plane + self] += (double)a.rho_ref[c] + (double)d;
+    }
+    if (a.gpop) {
+      float m = 0.f;
+      for (int i = 0; i < a.q; i++) m += a.gpop[(size_t)i * g.plane + self];
+      a.removed[(size_t)a.nc * g.plane + self] += (double)m;
+    }
   }
-  if (a.gpop) {
-    float m = 0.f;
-    for (int i = 0; i < a.q; i++) m += a.gpop[(size_t)i * g.plane + self];
-    a.removed[(size_t)a.nc * g.plane + self] += (double)m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (n) atomicAdd(a.nflips, (unsigned long long)n);
+    *a.fcount = 0u;
   }
-  atomicAdd(a.nflips, 1ULL);
 }
 
 }  // namespace
@@ -353,11 +437,10 @@ int launch_growth(const GrowthArgs &a, cudaStream_t s) {
 }
 
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s) {
-  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
   switch (storage) {
-    case ST_FP16: k_apply_flips<__half><<<grd, blk, 0, s>>>(a); break;
-    case ST_BF16: k_apply_flips<__nv_bfloat16><<<grd, blk, 0, s>>>(a); break;
-    default: k_apply_flips<float><<<grd, blk, 0, s>>>(a); break;
+    case ST_FP16: k_apply_flips<__half><<<1, 256, 0, s>>>(a); break;
+    case ST_BF16: k_apply_flips<__nv_bfloat16><<<1, 256, 0, s>>>(a); break;
+    default: k_apply_flips<float><<<1, 256, 0, s>>>(a); break;
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

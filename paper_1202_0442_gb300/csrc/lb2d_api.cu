@@ -104,7 +104,7 @@ struct lb_ctx {
   float *fields = nullptr, *u = nullptr, *gbuf[2] = {nullptr, nullptr};
   float *Cfield = nullptr, *db = nullptr, *Cpre = nullptr;
   double *b = nullptr, *removed = nullptr;
-  uint8_t *flip = nullptr;
+  unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
   unsigned long long *nflips = nullptr;
   double *partials = nullptr, *tout = nullptr;
   int tblocks = 0;
@@ -324,6 +324,8 @@ int commit(lb_ctx *ctx) {
     TRY(dalloc(ctx, &ctx->Cfield, g.plane));
     TRY(dalloc(ctx, &ctx->db, g.plane));
     TRY(dalloc(ctx, &ctx->flip, g.plane));
+    TRY(dalloc(ctx, &ctx->flist, g.plane));
+    TRY(dalloc(ctx, &ctx->fcount, 1));
   }
   TRY(dalloc(ctx, &ctx->b, g.plane));
   TRY(dalloc(ctx, &ctx->removed, (size_t)(ctx->nc + 1) * g.plane));
@@ -551,6 +553,8 @@ int one_step(lb_ctx *ctx, bool fields) {
     sa.react = ctx->react ? 1 : 0;
     sa.kr = (float)ctx->kr;
     sa.Cs = (float)ctx->Cs;
+    sa.rden[0] = (float)(1.0 / (ctx->kr + 2.0 * (ctx->qs == 4 ? 0.25 : 1.0 / 9.0)));
+    sa.rden[1] = (float)(1.0 / (ctx->kr + 2.0 / 36.0));
     sa.db = ctx->db;
     sa.Cfield = fields ? ctx->Cfield : nullptr;
     sa.nopen = (int)ctx->open.size();
@@ -571,6 +575,8 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.db = ctx->db;
       ga2.b = ctx->b;
       ga2.flip = ctx->flip;
+      ga2.flist = ctx->flist;
+      ga2.fcount = ctx->fcount;
       ga2.bmax = ctx->bmax;
       ga2.b0 = ctx->b0;
       ga2.seed = ctx->seed;
@@ -639,7 +645,7 @@ int lb_destroy(lb_ctx *ctx) {
   void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
-                  ctx->errw,    ctx->Cpre,    ctx->Rmap};
+                  ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;

@@ -99,6 +99,7 @@ struct SoluteArgs {
   float omega;
   int react;
   float kr, Cs;
+  float rden[2];          // 1 / (kr + 2 w) for the axis (D2Q4: all) and diagonal weights
   float *db;              // deposit share per fluid node
   float *Cfield;          // or nullptr
   int nopen;
@@ -118,7 +119,9 @@ struct GrowthArgs {
   uint32_t *mask;
   const float *db;
   double *b;
-  uint8_t *flip;
+  unsigned int *flip;     // per node: chosen to turn solid this step
+  unsigned int *flist;    // the chosen nodes (plane offsets), *fcount of them
+  unsigned int *fcount;
   double bmax, b0;
   uint64_t seed;
   int64_t t;              // 1-based iteration number

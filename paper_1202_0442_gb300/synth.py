@@ -299,9 +299,15 @@ def reactive(nx: int = 1024, ny: int = 512, seed: int = 1, ndiscs: int = 40,
              rho_out: float = 1.0, q: int = 9, taus: float = 0.7,
              C_in: float = 1.0, kr: float = 1e-3, Cs: float = 0.0,
              b0: float = 0.0, bmax: float = 1.0, growth_seed: int = 1,
-             steps: int = 50000) -> Workload:
+             steps: int = 50000, inlet: str = "velocity", rho_in: float = 1.005,
+             C_init: Optional[float] = None) -> Workload:
     """Solute transport with surface reaction and growth in a disc-filled
-    channel (solid rows y = 0 and y = ny-1; openings on y = 1..ny-2)."""
+    channel (solid rows y = 0 and y = ny-1; openings on y = 1..ny-2).
+
+    inlet "velocity": uniform inlet speed u_in (the stated recipe);
+    "pressure": dirichlet rho_in at the inlet, the initial density linear
+    between rho_in and rho_out.  C_init: initial concentration of the fluid
+    nodes (default C_in)."""
     wall = np.zeros((ny, nx), np.uint8)
     wall[0, :] = 1
     wall[ny - 1, :] = 1
@@ -311,13 +317,21 @@ def reactive(nx: int = 1024, ny: int = 512, seed: int = 1, ndiscs: int = 40,
                                      gap=4, margin_x=5, margin_y=5,
                                      periodic_x=False, periodic_y=False,
                                      base=wall)
-    rho = np.where(solid, 0.0, 1.0)
-    C = np.where(solid, 0.0, C_in)
-    ops = [Opening("xlo", 1, ny - 2, "inlet", [("uniform", u_in, 1.0)],
+    if inlet == "velocity":
+        rho = np.where(solid, 0.0, 1.0)
+        mom_in = ("uniform", u_in, 1.0)
+    else:
+        x = np.arange(nx, dtype=np.float64)
+        prof = rho_in + (rho_out - rho_in) * x / max(nx - 1, 1)
+        rho = np.where(solid, 0.0, np.broadcast_to(prof, (ny, nx)))
+        mom_in = ("dirichlet", 0.0, rho_in)
+    C = np.where(solid, 0.0, C_in if C_init is None else C_init)
+    ops = [Opening("xlo", 1, ny - 2, "inlet", [mom_in],
                    solute=("dirichlet", C_in)),
            Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0.0, rho_out)],
                    solute=("adiabatic", C_in))]
-    return Workload(name=f"reactive_{nx}x{ny}_q{q}", nx=nx, ny=ny, solid=solid,
+    return Workload(name=f"reactive_{nx}x{ny}_q{q}" + ("" if inlet == "velocity" else "_pressure"),
+                    nx=nx, ny=ny, solid=solid,
                     rho=[rho], tau=(tau,), openings=ops, solute_q=q, taus=taus,
                     C=C, reaction=(kr, Cs, b0, bmax, growth_seed), steps=steps,
                     rho_ref=(1.0,),
