@@ -227,7 +227,9 @@ def variants(args, local, stream, flush, value_fp32):
     peak = peaks()[0]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for st in ("fp32", "fp16"):
-        kw = {"h_max": 5e-3, "rounding": "stochastic"} if st != "fp32" else {}
+        # FP32 with the exact momentum pair, which keeps the slowest lattices
+        # within 1e-5 of the oracle in u at 5000 iterations
+        kw = {"h_max": 5e-3, "rounding": "stochastic"} if st != "fp32" else {"precise": True}
         lats = [lb2d.from_workload(x, st, device=local, stream=stream.cuda_stream, **kw) for x in ws]
         for lt in lats:
             lt.thermo(1 << 30)
@@ -256,7 +258,7 @@ def variants(args, local, stream, flush, value_fp32):
         out["batched" if st == "fp32" else "batched_fp16"] = {
             "workload": f"{len(ws)} periodic porous lattices, sides 64-512 step 32, "
                         f"porosity 0.4-0.9, tau 0.6-1.5 ({nodes} nodes, {fluid} fluid)",
-            "storage": st,
+            "storage": st + (" + precise momentum" if st == "fp32" else " stochastic"),
             "mlups_one_launch": nodes / (ms_b * 1e-3) / 1e6,
             "mlups_one_launch_per_lattice": nodes / (ms_s * 1e-3) / 1e6,
             "speedup": ms_s / ms_b, "ms_per_iteration_batched": ms_b,

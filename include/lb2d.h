@@ -55,6 +55,13 @@ extern "C" {
  * from a hash of node, direction and iteration; reproducible) instead of
  * to nearest even */
 #define LB_STOCHASTIC_ROUNDING 0x100
+/* OR'd into any storage: form the momentum sum_i e_i f_i of single-component
+ * lattices as an exact FP32 pair (error-free additions).  A rounded moment
+ * feeds its rounding error back as a spurious force; in slow force-driven
+ * flows (|j| much larger than the force per step) that biases u by up to
+ * ~2e-5 relative in FP32.  Costs about 3 % (4096^2) to 9 % (1024^2) of the
+ * streaming kernel's time; applies to the streaming and batched kernels. */
+#define LB_PRECISE_MOMENTUM 0x200
 
 typedef struct lb_ctx lb_ctx;
 typedef struct lb_batch lb_batch;
@@ -121,7 +128,8 @@ int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1,
 int lb_solute(lb_ctx *ctx, double taus, int q);
 
 /* Population storage: LB_FP32, LB_FP16 or LB_BF16 (the 16-bit ones
- * optionally | LB_STOCHASTIC_ROUNDING).  Populations are kept
+ * optionally | LB_STOCHASTIC_ROUNDING; any | LB_PRECISE_MOMENTUM).
+ * Populations are kept
  * as deviations f_i - w_i rho_ref[c] from the rest state of reference
  * density rho_ref[c] (one per component; NULL = 1.0); FP16 stores them
  * multiplied by the power of two 2^s with s the largest integer such that

@@ -8,7 +8,7 @@
 // dynamically (an atomic counter hands out the next tile), so a launch
 // costs the same whatever the number and sizes of the lattices.  The tile
 // shape and the schedule are chosen by timing (lb_batch_autotune).
-#include "lbdev.cuh"
+#include "lbcollide.cuh"
 #include "lbbatch.h"
 
 namespace lbk {
@@ -33,12 +33,17 @@ __device__ __forceinline__ void batch_node(const BatchLat &L, const S *fin, S *f
       if (nb(bits, OPP(i))) h[i] = Store<S>::ld(fin, (size_t)OPP(i) * L.plane + self, L.inv_scale);
   }
   const float d = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-  const float jx = (h[1] - h[3]) + (h[5] - h[7]) + (h[8] - h[6]);
-  const float jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  float jx, jy, jxl = 0.f, jyl = 0.f;
+  if (L.pm) {
+    momentum_exact(h, jx, jxl, jy, jyl);
+  } else {
+    jx = (h[1] - h[3]) + (h[5] - h[7]) + (h[8] - h[6]);
+    jy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+  }
   const float rho = L.rho_ref + d;
   const float Fx = L.fx + rho * L.ax, Fy = L.fy + rho * L.ay;
   const float ir = 1.0f / rho;
-  const float mx = jx + L.tau * Fx, my = jy + L.tau * Fy;
+  const float mx = jx + (jxl + L.tau * Fx), my = jy + (jyl + L.tau * Fy);
   const float ux = mx * ir, uy = my * ir;
   float heq[9];
   equilibrium_pairs(d, rho, ux, uy, mx, my, 1.0f / 9.0f, 1.0f / 36.0f, heq);

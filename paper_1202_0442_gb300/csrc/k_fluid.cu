@@ -114,8 +114,8 @@ constexpr uint32_t DIAG_BITS = (1u << NBPOS(-1, -1)) | (1u << NBPOS(1, -1)) | (1
 
 constexpr int LOC_BY = 8;
 
-template <class S, int NC, bool ME>
-__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid_local(const FluidArgs p) {
+template <class S, int NC, bool ME, bool PM>
+__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
   const Geometry &g = p.g;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * LOC_BY + threadIdx.y;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME) ? 8 : 4) k_fluid
   float F[NC][2];
 #pragma unroll
   for (int c = 0; c < NC; c++) F[c][0] = F[c][1] = 0.f;
-  collide_store<S, NC, ME>(p, x, y, bits, h, F);
+  collide_store<S, NC, ME, PM>(p, x, y, bits, h, F);
 }
 
 constexpr int SC_TX = 32, SC_TY = 16;
@@ -332,10 +332,15 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
   } else {
     dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
     if (nc == 1) {
-      if (me) k_fluid_local<S, 1, true><<<grd, blk, 0, s>>>(a);
-      else k_fluid_local<S, 1, false><<<grd, blk, 0, s>>>(a);
+      if (a.pm) {
+        if (me) k_fluid_local<S, 1, true, true><<<grd, blk, 0, s>>>(a);
+        else k_fluid_local<S, 1, false, true><<<grd, blk, 0, s>>>(a);
+      } else {
+        if (me) k_fluid_local<S, 1, true, false><<<grd, blk, 0, s>>>(a);
+        else k_fluid_local<S, 1, false, false><<<grd, blk, 0, s>>>(a);
+      }
     } else {
-      k_fluid_local<S, 2, true><<<grd, blk, 0, s>>>(a);
+      k_fluid_local<S, 2, true, false><<<grd, blk, 0, s>>>(a);
     }
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;

@@ -71,6 +71,7 @@ struct lb_ctx {
   double taus = 1.0;
   int storage = ST_FP32;
   bool sr = false;
+  bool pm = false;  // LB_PRECISE_MOMENTUM
   double rho_ref[2] = {1, 1};
   float scale = 1.f, inv_scale = 1.f;
   std::vector<uint8_t> solid, region;
@@ -452,6 +453,7 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   z = (z ^ (z >> 31)) * 0xbf58476d1ce4e5b9ULL;
   a.step_seed = (uint32_t)(z >> 32);
   if (ctx->sr) a.sr_seed = (uint32_t)z | 1u;
+  a.pm = ctx->pm ? 1 : 0;
   a.slip = ctx->bstyle != 0 ? 1 : 0;
   a.slipR[0] = a.slipR[1] = (float)(ctx->bstyle == 1 ? 1.0 : ctx->bstyle == 2 ? ctx->slipR : 0.0);
   a.Rmap = ctx->bstyle == 3 ? ctx->Rmap : nullptr;
@@ -721,12 +723,14 @@ int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref, double h_max
   NEED_CTX();
   TRY(paint_check(ctx));
   const bool sr = (storage & LB_STOCHASTIC_ROUNDING) != 0;
-  storage &= ~LB_STOCHASTIC_ROUNDING;
+  const bool pm = (storage & LB_PRECISE_MOMENTUM) != 0;
+  storage &= ~(LB_STOCHASTIC_ROUNDING | LB_PRECISE_MOMENTUM);
   if (storage != LB_FP32 && storage != LB_FP16 && storage != LB_BF16)
     return ctx->fail(LB_E_ARG, "unknown storage %d", storage);
   if (sr && storage == LB_FP32) return ctx->fail(LB_E_ARG, "stochastic rounding applies to 16-bit storage");
   ctx->storage = storage;
   ctx->sr = sr;
+  ctx->pm = pm;
   double rmax = 0;
   for (int c = 0; c < 2; c++) {
     // a value FP32 holds exactly, so that the kernels and the FP64 host
@@ -1535,6 +1539,7 @@ int sync_descs(lb_batch *b) {
     L.inv_scale = c->inv_scale;
     L.tau = (float)c->tau[0];
     L.omega = (float)(1.0 / c->tau[0]);
+    L.pm = c->pm ? 1 : 0;
     L.fx = (float)c->fave[0][0];
     L.fy = (float)c->fave[0][1];
     L.ax = (float)c->acc[0][0];

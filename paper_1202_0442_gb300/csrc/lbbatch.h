@@ -15,6 +15,7 @@ struct BatchLat {
   int cur;             // buf[cur] is the input of the batch's parity-0 launch
   const uint32_t *mask;
   float rho_ref, scale, inv_scale, tau, omega, fx, fy, ax, ay;
+  int pm;              // momentum as an exact hi + lo sum
 };
 
 struct BatchLaunch {

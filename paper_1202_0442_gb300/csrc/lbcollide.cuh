@@ -17,23 +17,53 @@ __device__ __forceinline__ uint32_t rnd(uint32_t seed, int self, int c, int i) {
                (0x85ebca6bu * (uint32_t)(i + 1)));
 }
 
+// momentum sum_i e_i f_i of one component as an unevaluated sum hi + lo,
+// every addition error-free (two_sum): a moment rounded to FP32 feeds its
+// rounding error back into the state as a spurious force (the collision
+// relaxes toward the computed momentum), which in slow force-driven flows
+// is comparable with the force itself
+__device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, float &jxl, float &jy,
+                                               float &jyl) {
+  float a, ea, b, eb, d, ed, s, es, t, et;
+  two_sum(f[1], -f[3], a, ea);
+  two_sum(f[5], -f[7], b, eb);
+  two_sum(f[8], -f[6], d, ed);
+  two_sum(a, b, s, es);
+  two_sum(s, d, t, et);
+  jx = t;
+  jxl = ((ea + eb) + (ed + es)) + et;
+  two_sum(f[2], -f[4], a, ea);
+  two_sum(f[5], -f[7], b, eb);
+  two_sum(f[6], -f[8], d, ed);
+  two_sum(a, b, s, es);
+  two_sum(s, d, t, et);
+  jy = t;
+  jyl = ((ea + eb) + (ed + es)) + et;
+}
+
 // moments, forces, equilibrium velocity, BGK and the stores of one node.
 // Fsc: interforce already evaluated (zero when off).  ME: mass-exact
-// collision (see below).
-template <class S, int NC, bool ME>
+// collision (see below).  PM: the momentum as an exact hi + lo sum (single
+// component; the storage flag LB_PRECISE_MOMENTUM).
+template <class S, int NC, bool ME, bool PM = false>
 __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
                                               float (&h)[NC][9], const float (&Fsc)[NC][2]) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
   const int P = (int)g.plane;
-  float drho[NC], rho[NC], jx[NC], jy[NC], Fx[NC], Fy[NC];
+  float drho[NC], rho[NC], jx[NC], jy[NC], jxl[NC], jyl[NC], Fx[NC], Fy[NC];
 #pragma unroll
   for (int c = 0; c < NC; c++) {
     const float(&f)[9] = h[c];
     drho[c] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     rho[c] = p.rho_ref[c] + drho[c];
-    jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
-    jy[c] = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    if (PM && NC == 1) {
+      momentum_exact(f, jx[c], jxl[c], jy[c], jyl[c]);
+    } else {
+      jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+      jy[c] = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+      jxl[c] = jyl[c] = 0.f;
+    }
     Fx[c] = p.fx[c] + rho[c] * p.ax[c] + Fsc[c][0];
     Fy[c] = p.fy[c] + rho[c] * p.ay[c] + Fsc[c][1];
     if (p.ads[c]) {
@@ -48,8 +78,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
   // carries, the latter formed without a division
   float uex[NC], uey[NC], mxt[NC], myt[NC];
   if (NC == 1) {
-    mxt[0] = jx[0] + p.tau[0] * Fx[0];
-    myt[0] = jy[0] + p.tau[0] * Fy[0];
+    mxt[0] = PM ? jx[0] + (jxl[0] + p.tau[0] * Fx[0]) : jx[0] + p.tau[0] * Fx[0];
+    myt[0] = PM ? jy[0] + (jyl[0] + p.tau[0] * Fy[0]) : jy[0] + p.tau[0] * Fy[0];
     const float ir = 1.0f / rho[0];
     uex[0] = mxt[0] * ir;
     uey[0] = myt[0] * ir;
@@ -133,8 +163,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     if (p.fields) {
       float *fl = p.fields + (size_t)c * NFIELD * P;
       fl[self] = drho[c];
-      fl[P + self] = jx[c] + 0.5f * Fx[c];
-      fl[2 * P + self] = jy[c] + 0.5f * Fy[c];
+      fl[P + self] = jx[c] + (jxl[c] + 0.5f * Fx[c]);
+      fl[2 * P + self] = jy[c] + (jyl[c] + 0.5f * Fy[c]);
       // sum of the equilibrium populations (Mass_eq of the thermo command)
       fl[3 * P + self] = heq[0] + ((heq[1] + heq[3]) + (heq[2] + heq[4])) +
                          ((heq[5] + heq[7]) + (heq[6] + heq[8]));
@@ -144,8 +174,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     float pxs = 0.f, pys = 0.f, rs = 0.f;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      pxs += jx[c] + 0.5f * Fx[c];
-      pys += jy[c] + 0.5f * Fy[c];
+      pxs += jx[c] + (jxl[c] + 0.5f * Fx[c]);
+      pys += jy[c] + (jyl[c] + 0.5f * Fy[c]);
       rs += rho[c];
     }
     p.uout[self] = pxs / rs;

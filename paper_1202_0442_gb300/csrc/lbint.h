@@ -71,6 +71,7 @@ struct FluidArgs {
   // boundary_style slip/mixed/hybrid: reflection coefficient R of the solid
   // nodes, uniform (slipR) or per node (Rmap [nc][plane], read on solid
   // nodes); edge_x/edge_y: the x/y edge carries an opening (not periodic)
+  int pm;                 // momentum as an exact hi + lo sum (LB_PRECISE_MOMENTUM)
   int slip;
   float slipR[2];
   const float *Rmap;

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblb2d.so")
 LB_OK, LB_E_ORDER, LB_E_ARG, LB_E_UNSUPPORTED, LB_E_CUDA, LB_E_NAN, LB_E_NOMEM, LB_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LB_STOCHASTIC_ROUNDING = 0x100
+LB_PRECISE_MOMENTUM = 0x200
 _CODES = {LB_E_ORDER: "LB_E_ORDER", LB_E_ARG: "LB_E_ARG", LB_E_UNSUPPORTED: "LB_E_UNSUPPORTED",
           LB_E_CUDA: "LB_E_CUDA", LB_E_NAN: "LB_E_NAN", LB_E_NOMEM: "LB_E_NOMEM",
           LB_E_TIMEOUT: "LB_E_TIMEOUT"}
@@ -203,9 +204,10 @@ class Lattice:
         self.q = q
 
     def set_storage(self, storage: str = "fp32", rho_ref: Sequence[float] = (1.0,), h_max: float = 0.0,
-                    rounding: str = "nearest"):
+                    rounding: str = "nearest", precise: bool = False):
         r = np.array(list(rho_ref) + [rho_ref[0]] * (2 - len(rho_ref)), np.float64)
-        code = STORAGE[storage] | (LB_STOCHASTIC_ROUNDING if rounding == "stochastic" else 0)
+        code = (STORAGE[storage] | (LB_STOCHASTIC_ROUNDING if rounding == "stochastic" else 0)
+                | (LB_PRECISE_MOMENTUM if precise else 0))
         self._ck(self._L.lb_set_storage(self._h, code, _dp(r), h_max))
 
     def boundary_style(self, style: str = "noslip", R: float = 0.0):
@@ -455,7 +457,7 @@ class Batch:
 
 def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0,
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
-                  rounding: str = "nearest", kernel: str = "auto") -> Lattice:
+                  rounding: str = "nearest", kernel: str = "auto", precise: bool = False) -> Lattice:
     """Issue the command sequence that sets up workload ``w``."""
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
@@ -464,7 +466,7 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
         lt.fluids(w.tau[0], w.tau[1], al[0], al[1])
     if w.solute_q:
         lt.solute(w.taus, w.solute_q)
-    lt.set_storage(storage, list(w.rho_ref), h_max, rounding)
+    lt.set_storage(storage, list(w.rho_ref), h_max, rounding, precise)
     slip = list(getattr(w, "slip", None) or ())
     if any(np.ndim(R) > 0 for R in slip if R is not None):
         # hybrid: per-node coefficients, per component

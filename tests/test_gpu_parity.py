@@ -318,6 +318,37 @@ def test_density_ratio_alpha(taus, alphas, G, init, storage):
     assert errs["mass1"] < mtol and errs["mass2"] < mtol, errs
 
 
+def test_precise_momentum_removes_the_force_bias():
+    """LB_PRECISE_MOMENTUM: in a slow force-driven channel (tau = 0.55,
+    H = 48, g = 1e-6, |j| grown far above the force per step) the momentum
+    rounded to FP32 acts as a spurious force and u misses the oracle by
+    several 1e-5; formed as an exact FP32 pair it meets 1e-5."""
+    w = synth.channel(16, 50, 0.55, 1e-6)
+    o = oracle_from_workload(w)
+    o.step(3000)
+    errs = {}
+    for pm in (False, True):
+        lt = lb2d.from_workload(w, precise=pm)
+        lt.iteration(3000)
+        errs[pm] = rel_u(lt, o)
+        assert rel_rho(lt, o, w) < TOL32
+    assert errs[True] < TOL32 < errs[False], errs
+
+
+def test_precise_momentum_batched():
+    """The batched kernel honours the flag per lattice: batched precise
+    lattices equal the single-lattice precise ones."""
+    ws = synth.batch(count=4, smin=64, smax=128, step=32, steps=30)
+    singles = [lb2d.from_workload(w, precise=True) for w in ws]
+    batched = [lb2d.from_workload(w, precise=True) for w in ws]
+    b = lb2d.Batch(batched)
+    b.iteration(40, use_graph=False)
+    for lt in singles:
+        lt.iteration(40)
+    for s_, b_ in zip(singles, batched):
+        assert np.max(np.abs(s_.populations() - b_.populations())) < 1e-6
+
+
 # ---------------------------------------------------------------------------
 # boundary_style slip / mixed / hybrid
 # ---------------------------------------------------------------------------
