@@ -2,7 +2,8 @@
 //
 // Each lattice is a periodic single-component D2Q9 lattice with body
 // forces (pull streaming, half-way bounce-back at its solid nodes, velocity
-// shift, BGK; the same update as k_fluid_local).  The lattices are cut into
+// shift, BGK; the same update as k_fluid_local, with the same per-warp
+// mask words and one load per direction).  The lattices are cut into
 // TX x TY tiles listed in one array; a grid of (SM count x resident CTAs)
 // blocks walks that list either statically (tile k, k + grid, ...) or
 // dynamically (an atomic counter hands out the next tile), so a launch
@@ -15,22 +16,48 @@ namespace lbk {
 
 namespace {
 
+// One warp updates 32 consecutive nodes x0 .. x0+31 of row y (x0 a
+// multiple of 32, so the warp's solid bits are one mask word): mask words
+// of rows y-1, y, y+1 by broadcast loads (edge lanes also the words
+// beside them), pull with half-way bounce-back by one load per direction,
+// BGK with the velocity shift.  Solid and padding lanes of a warp that has
+// fluid lanes store zeros, so the warp writes whole sectors.
 template <class S>
-__device__ __forceinline__ void batch_node(const BatchLat &L, const S *fin, S *fout, int x, int y) {
-  if (solid_at(L.mask, L.mw, x, y)) return;
-  const int xm = x ? x - 1 : L.nx - 1, xp = (x + 1 == L.nx) ? 0 : x + 1;
+__device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *fout, int x, int y) {
+  const int lane = threadIdx.x, cw = x >> 5;
   const int ym = y ? y - 1 : L.ny - 1, yp = (y + 1 == L.ny) ? 0 : y + 1;
-  const uint32_t bits = nbr_bits(L.mask, L.mw, x, y, xm, xp, ym, yp);
-  const size_t r0 = (size_t)y * L.pitch, rm = (size_t)ym * L.pitch, rp = (size_t)yp * L.pitch;
-  const size_t self = r0 + x;
-  const size_t src[9] = {self, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+  const uint32_t *rows[3] = {L.mask + (size_t)ym * L.mw, L.mask + (size_t)y * L.mw, L.mask + (size_t)yp * L.mw};
+  uint32_t w[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    w[r][1] = __ldg(rows[r] + cw);
+    w[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
+    w[r][2] = (lane == 31 && cw + 1 < L.mw) ? __ldg(rows[r] + cw + 1) : 0u;
+  }
+  const int P = (int)L.plane;
+  const int self = y * L.pitch + x;
+  const bool idle = x >= L.nx || ((w[1][1] >> lane) & 1u);
+  const unsigned busy = __ballot_sync(0xffffffffu, !idle);
+  if (idle) {
+    if (busy) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) Store<S>::st(fout, i * P + self, 0.0f, 1.0f);
+    }
+    return;
+  }
+  const int xm = x ? x - 1 : L.nx - 1, xp = (x + 1 == L.nx) ? 0 : x + 1;
+  uint32_t bits;
+  if (x == 0 || x == L.nx - 1) bits = nbr_bits(L.mask, L.mw, x, y, xm, xp, ym, yp);
+  else
+    bits = row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
+           (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
+  const int r0 = y * L.pitch, rm = ym * L.pitch, rp = yp * L.pitch;
+  const int src[9] = {self, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
   float h[9];
 #pragma unroll
-  for (int i = 0; i < 9; i++) h[i] = Store<S>::ld(fin, (size_t)i * L.plane + src[i], L.inv_scale);
-  if (bits & ~(1u << 4)) {
-#pragma unroll
-    for (int i = 1; i < 9; i++)
-      if (nb(bits, OPP(i))) h[i] = Store<S>::ld(fin, (size_t)OPP(i) * L.plane + self, L.inv_scale);
+  for (int i = 0; i < 9; i++) {
+    const int k = (i && nb(bits, OPP(i))) ? OPP(i) * P + self : i * P + src[i];
+    h[i] = Store<S>::ld(fin, k, L.inv_scale);
   }
   const float d = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
   float jx, jy, jxl = 0.f, jyl = 0.f;
@@ -49,11 +76,11 @@ __device__ __forceinline__ void batch_node(const BatchLat &L, const S *fin, S *f
   equilibrium_pairs(d, rho, ux, uy, mx, my, 1.0f / 9.0f, 1.0f / 36.0f, heq);
 #pragma unroll
   for (int i = 0; i < 9; i++)
-    Store<S>::st(fout, (size_t)i * L.plane + self, h[i] + L.omega * (heq[i] - h[i]), L.scale);
+    Store<S>::st(fout, i * P + self, h[i] + L.omega * (heq[i] - h[i]), L.scale);
 }
 
 template <class S, int TX, int TY>
-__global__ void __launch_bounds__(256) k_batch(const BatchLat *__restrict__ lat,
+__global__ void __launch_bounds__(256, 4) k_batch(const BatchLat *__restrict__ lat,
                                                const int4 *__restrict__ tiles, int ntiles,
                                                int parity, int dynamic,
                                                unsigned int *counters) {
@@ -78,8 +105,8 @@ __global__ void __launch_bounds__(256) k_batch(const BatchLat *__restrict__ lat,
       if (y >= L.ny) break;
 #pragma unroll
       for (int dx = 0; dx < TX; dx += 32) {
-        const int x = t.y + dx + threadIdx.x;
-        if (x < L.nx) batch_node<S>(L, fin, fout, x, y);
+        if (t.y + dx >= L.pitch) break;  // warp-uniform: the tile runs past the row
+        batch_warp<S>(L, fin, fout, t.y + dx + threadIdx.x, y);
       }
     }
     if (dynamic) {
