@@ -351,8 +351,8 @@ int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b);
 int lb_get_mask(lb_ctx *ctx, uint8_t *mask);
 
 /* Raw state snapshot (checkpoint/resume): populations in their storage
- * format, mask, solute, precipitate, removed-mass tallies and step
- * counter.  lb_state_size gives the byte count; save/load copy to/from a
+ * format, mask, solute, step counter and, with surface_reaction, the
+ * precipitate, removed-mass tallies and flip count.  lb_state_size gives the byte count; save/load copy to/from a
  * host buffer of that size (pinned memory gives full copy bandwidth).
  * Loading a snapshot of the same setup resumes bit for bit. */
 int lb_state_size(lb_ctx *ctx, size_t *bytes);

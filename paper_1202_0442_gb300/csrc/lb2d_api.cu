@@ -1352,7 +1352,8 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
 }
 
 // snapshot layout: header, populations (current buffer), mask, solute
-// populations, precipitate, removed tallies, flip count
+// populations, and with surface_reaction the precipitate, removed tallies
+// and flip count (without it they stay zero and are not part of the state)
 struct SnapHeader {
   uint64_t magic, nx, ny, nc, qs, storage, t;
 };
@@ -1364,9 +1365,11 @@ static void snap_parts(lb_ctx *ctx, std::vector<std::pair<void *, size_t>> &part
   parts.push_back({ctx->fbuf[ctx->cur], (size_t)ctx->nc * 9 * g.plane * storage_bytes(ctx->storage)});
   parts.push_back({ctx->mask, (size_t)g.ny * g.mw * 4});
   if (ctx->qs) parts.push_back({ctx->gbuf[ctx->cur], (size_t)ctx->qs * g.plane * 4});
-  parts.push_back({ctx->b, g.plane * 8});
-  parts.push_back({ctx->removed, (size_t)(ctx->nc + 1) * g.plane * 8});
-  parts.push_back({ctx->nflips, 8});
+  if (ctx->react) {
+    parts.push_back({ctx->b, g.plane * 8});
+    parts.push_back({ctx->removed, (size_t)(ctx->nc + 1) * g.plane * 8});
+    parts.push_back({ctx->nflips, 8});
+  }
 }
 
 int lb_state_size(lb_ctx *ctx, size_t *bytes) {
