@@ -104,6 +104,7 @@ struct lb_ctx {
   uint32_t *mask = nullptr;
   float *fields = nullptr, *u = nullptr, *gbuf[2] = {nullptr, nullptr};
   float *Cfield = nullptr, *db = nullptr, *Cpre = nullptr;
+  float *vstage = nullptr;  // lb_get_velocity_f32 staging (3 planes, kept)
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
   unsigned long long *nflips = nullptr;
@@ -647,7 +648,8 @@ int lb_destroy(lb_ctx *ctx) {
   void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
-                  ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount};
+                  ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
+                  ctx->vstage};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -1268,8 +1270,10 @@ int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy) {
   if (!rho || !ux || !uy) return ctx->fail(LB_E_ARG, "null output");
   TRY(set_device(ctx));
   const size_t nn = (size_t)ctx->nx * ctx->ny;
-  float *st = nullptr;
-  CK(cudaMallocAsync((void **)&st, 3 * nn * sizeof(float), ctx->stream));
+  // a staging buffer kept for the context's life: an allocation per call
+  // costs more than the copies
+  if (!ctx->vstage) TRY(dalloc(ctx, &ctx->vstage, 3 * nn));
+  float *st = ctx->vstage;
   float rr[2] = {(float)ctx->rho_ref[0], (float)ctx->rho_ref[1]};
   int n = launch_export_velocity(ctx->fields, ctx->nc, ctx->mask, ctx->g, rr, st, st + nn, st + 2 * nn,
                                  ctx->stream);
@@ -1278,7 +1282,6 @@ int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(rho, st, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ux, st + nn, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(uy, st + 2 * nn, nn * 4, cudaMemcpyDeviceToHost, ctx->stream);
-  cudaFreeAsync(st, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "velocity export");
   return LB_OK;

@@ -608,6 +608,30 @@ def test_determinism_and_snapshot_resume():
     assert np.array_equal(c.populations(), fa)
 
 
+def test_snapshot_resume_with_growth():
+    """A reactive lattice resumes bit for bit from a snapshot taken between
+    growth events: populations, solute, deposits, mask and removed masses
+    (the snapshot carries them only when surface_reaction is on)."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=9, kr=0.02, bmax=0.3, growth_seed=7)
+    a = lb2d.from_workload(w, thermo=20)
+    a.iteration(150)
+    buf = np.zeros(a.state_size(), np.uint8)
+    a.save_state(buf)
+    a.iteration(150)
+    b = lb2d.from_workload(w, thermo=20)
+    b.load_state(buf)
+    b.iteration(150)
+    assert np.array_equal(a.populations(), b.populations())
+    ga, Ca, ba = a.solute_state()
+    gb, Cb, bb = b.solute_state()
+    assert np.array_equal(ga, gb) and np.array_equal(ba, bb)
+    assert np.array_equal(a.mask(), b.mask())
+    assert a.get_thermo() == b.get_thermo()
+    assert a.get_thermo()["flips"] > 0
+    plain = lb2d.from_workload(synth.porous(64, 64, seed=2, rmin=3, rmax=8))
+    assert plain.state_size() < a.state_size() // 2
+
+
 def test_nan_is_reported():
     w = synth.channel(32, 16, 1.0, 0.0)
     lt = lb2d.from_workload(w)
