@@ -105,7 +105,9 @@ int lb_launch_count(const lb_ctx *ctx, uint64_t *out);
 
 /* lattice command: style "d2q9", nx x ny nodes, relaxation time tau > 1/2.
  * Must come first.  Boundaries are periodic until openings or obstacles
- * say otherwise. */
+ * say otherwise.  Any nx, ny >= 1 up to 9 x round_up(nx, 32) x ny < 2^31
+ * (about 238 M nodes; LB_E_UNSUPPORTED beyond: the kernels index a
+ * component's planes with 32-bit offsets). */
 int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau);
 
 /* processors command: accepted after lb_lattice and ignored (one GPU runs

@@ -668,8 +668,12 @@ int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau) {
   NEED_CTX();
   if (ctx->committed) return ctx->fail(LB_E_ORDER, "lattice is fixed after the first iteration");
   if (!style || strcmp(style, "d2q9")) return ctx->fail(LB_E_UNSUPPORTED, "lattice style must be d2q9");
-  if (nx < 1 || ny < 1 || (long long)nx * ny > (1LL << 31) / 16)
-    return ctx->fail(LB_E_ARG, "bad lattice size %d x %d", nx, ny);
+  if (nx < 1 || ny < 1) return ctx->fail(LB_E_ARG, "bad lattice size %d x %d", nx, ny);
+  // the kernels index one component's nine planes of (nx rounded up to 32)
+  // x ny slots with 32-bit offsets
+  if (9LL * (((long long)nx + 31) / 32 * 32) * ny > (long long)INT32_MAX)
+    return ctx->fail(LB_E_UNSUPPORTED, "lattice %d x %d exceeds the 32-bit plane indexing (9 x pitch x ny < 2^31)",
+                     nx, ny);
   if (!(tau > 0.5)) return ctx->fail(LB_E_ARG, "tau must exceed 1/2");
   ctx->have_lattice = true;
   ctx->nx = nx;
@@ -678,11 +682,13 @@ int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau) {
   const size_t nn = (size_t)nx * ny;
   ctx->solid.assign(nn, 0);
   ctx->region.assign(nn, 0);
+  // the painted initial state (position0/momentum0/concentration0) is
+  // allocated by the first command that paints
   for (int c = 0; c < 2; c++) {
-    ctx->paint_f[c].assign(9 * nn, 0.0);
+    ctx->paint_f[c].clear();
     ctx->painted_f[c] = false;
   }
-  ctx->paint_C.assign(nn, 0.0);
+  ctx->paint_C.clear();
   return LB_OK;
 }
 
@@ -1036,6 +1042,7 @@ int lb_momentum0(lb_ctx *ctx, int mode, double value, int fluid) {
   if (mode < 0 || mode > 8 || !fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad mode or fluid");
   const size_t nn = ctx->region.size();
   std::vector<double> &f = ctx->paint_f[fluid - 1];
+  if (f.empty()) f.assign(9 * nn, 0.0);
   for (size_t n = 0; n < nn; n++)
     if (ctx->region[n]) f[(size_t)mode * nn + n] += value;
   ctx->painted_f[fluid - 1] = true;
@@ -1048,6 +1055,7 @@ int lb_concentration0(lb_ctx *ctx, double value) {
   TRY(paint_check(ctx));
   if (!ctx->have_region) return ctx->fail(LB_E_ORDER, "concentration0 must follow position0");
   if (!ctx->qs) return ctx->fail(LB_E_ORDER, "concentration0 needs the solute command");
+  if (ctx->paint_C.empty()) ctx->paint_C.assign(ctx->region.size(), 0.0);
   for (size_t n = 0; n < ctx->region.size(); n++)
     if (ctx->region[n]) ctx->paint_C[n] += value;
   ctx->painted_C = true;

@@ -632,6 +632,39 @@ def test_snapshot_resume_with_growth():
     assert plain.state_size() < a.state_size() // 2
 
 
+@pytest.mark.parametrize("nx,ny", [(1, 24), (3, 5), (33, 2), (31, 17)])
+def test_degenerate_and_ragged_sizes(nx, ny):
+    """Lattices narrower than a warp, one node wide or two high (periodic
+    neighbours that are the node itself or coincide), and a row that is
+    one node longer than a warp, with obstacles and forces, against the
+    oracle."""
+    mask = synth.random_mask(nx, ny, nx * 7 + ny, 0.15) if nx * ny > 20 else np.zeros((ny, nx), np.uint8)
+    f = synth.random_populations(9, nx, ny, 3, W9, 0.2, mask)
+    w = synth.Workload(name="tiny", nx=nx, ny=ny, solid=mask, rho=[np.where(mask, 0, 1.0)], tau=(0.8,),
+                       aveforce=((1e-4, -2e-4),))
+    lt = lb2d.from_workload(w)
+    lt.set_populations(f)
+    o = oracle_from_workload(w)
+    o.set_f(f)
+    lt.iteration(25)
+    o.step(25)
+    e, _ = pop_err(lt, o)
+    assert e < TOL32, e
+
+
+def test_lattice_size_limit():
+    """Beyond 32-bit plane offsets the lattice call fails cleanly (before
+    any allocation) rather than indexing out of range."""
+    lt = lb2d.Lattice()
+    with pytest.raises(lb2d.LBError) as ei:
+        lt.lattice(70000, 40000, 1.0)
+    assert ei.value.code == lb2d.LB_E_UNSUPPORTED
+    with pytest.raises(lb2d.LBError) as ei:
+        lt.lattice(1, 8_000_000, 1.0)
+    assert ei.value.code == lb2d.LB_E_UNSUPPORTED
+    lt.lattice(16, 16, 1.0)
+
+
 def test_nan_is_reported():
     w = synth.channel(32, 16, 1.0, 0.0)
     lt = lb2d.from_workload(w)
