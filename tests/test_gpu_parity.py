@@ -1,8 +1,8 @@
 """GPU library vs FP64 oracle, element by element, through the C ABI.
 
-Tolerances: FP32 storage 1e-5 (max relative error in rho and u, the
-SURVEY's metric: max|u - u_ref| / max|u_ref|); 16-bit storage 2e-3 for FP16;
-masks and growth events exact.
+Tolerances: FP32 storage 1e-5 (max relative error in rho and u, measured
+as max|u - u_ref| / max|u_ref| over fluid nodes); 16-bit storage 2e-3 for
+FP16; masks and growth events exact.
 """
 import numpy as np
 import pytest
