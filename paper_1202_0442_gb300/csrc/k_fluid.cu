@@ -114,8 +114,12 @@ constexpr uint32_t DIAG_BITS = (1u << NBPOS(-1, -1)) | (1u << NBPOS(1, -1)) | (1
 
 constexpr int LOC_BY = 8;
 
-template <class S, int NC, bool ME, bool PM>
+// SR: 0 rounding read from p.sr_seed, 1 nearest, 2 stochastic (16-bit,
+// not ME).  Scaled 16-bit storage without ME runs folded (collide_store).
+template <class S, int NC, bool ME, bool PM, int SR>
 __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
+  constexpr bool FOLD = Store<S>::kScaled && !ME;
+  const float linv = FOLD ? 1.0f : p.inv_scale;
   const Geometry &g = p.g;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * LOC_BY + threadIdx.y;
@@ -165,17 +169,17 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
   float h[NC][9];
 #pragma unroll
   for (int c = 0; c < NC; c++)
-    pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
+    pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, linv, h[c]);
   if (p.slip && (bits & DIAG_BITS)) {
 #pragma unroll
     for (int c = 0; c < NC; c++)
-      slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, p.inv_scale, h[c]);
+      slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, linv, h[c]);
   }
-  if (p.nopen) apply_openings<NC>(p, x, y, h);
+  if (p.nopen) apply_openings<NC>(p, x, y, h, FOLD ? p.scale : 1.0f);
   float F[NC][2];
 #pragma unroll
   for (int c = 0; c < NC; c++) F[c][0] = F[c][1] = 0.f;
-  collide_store<S, NC, ME, PM>(p, x, y, bits, h, F);
+  collide_store<S, NC, ME, PM, FOLD, SR>(p, x, y, bits, h, F);
 }
 
 constexpr int SC_TX = 32, SC_TY = 16;
@@ -332,15 +336,18 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
   } else {
     dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
     if (nc == 1) {
-      if (a.pm) {
-        if (me) k_fluid_local<S, 1, true, true><<<grd, blk, 0, s>>>(a);
-        else k_fluid_local<S, 1, false, true><<<grd, blk, 0, s>>>(a);
+      if (me) {
+        if (a.pm) k_fluid_local<S, 1, true, true, 0><<<grd, blk, 0, s>>>(a);
+        else k_fluid_local<S, 1, true, false, 0><<<grd, blk, 0, s>>>(a);
+      } else if (a.sr_seed) {
+        if (a.pm) k_fluid_local<S, 1, false, true, 2><<<grd, blk, 0, s>>>(a);
+        else k_fluid_local<S, 1, false, false, 2><<<grd, blk, 0, s>>>(a);
       } else {
-        if (me) k_fluid_local<S, 1, true, false><<<grd, blk, 0, s>>>(a);
-        else k_fluid_local<S, 1, false, false><<<grd, blk, 0, s>>>(a);
+        if (a.pm) k_fluid_local<S, 1, false, true, 1><<<grd, blk, 0, s>>>(a);
+        else k_fluid_local<S, 1, false, false, 1><<<grd, blk, 0, s>>>(a);
       }
     } else {
-      k_fluid_local<S, 2, true, false><<<grd, blk, 0, s>>>(a);
+      k_fluid_local<S, 2, true, false, 0><<<grd, blk, 0, s>>>(a);
     }
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;

@@ -151,9 +151,13 @@ __device__ __forceinline__ uint32_t mask_word(const uint32_t *m, const Geometry 
   return (w >= 0 && w < g.mw) ? __ldg(m + (size_t)gy * g.mw + w) : 0u;
 }
 
-template <class S>
+template <class S, int SR>
 __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, int *err) {
   using L = TmaLayout<S>;
+  // the same arithmetic as the streaming kernel (scaled 16-bit storage
+  // folded, rounding mode SR), so the two agree bit for bit
+  constexpr bool FOLD = Store<S>::kScaled;
+  const float linv = FOLD ? 1.0f : p.inv_scale;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   // stage q: populations at stage0 + q * STAGE, mask words at msk0 + q *
   // ROWS * MW, barrier bar[q]
@@ -231,11 +235,11 @@ __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, 
       for (int i = 0; i < 9; i++) {
         const int off = (i && nb(bits, OPP(i))) ? OPP(i) * L::PLANE + cself
                                                 : i * L::PLANE + cself - EY(i) * L::COLS - EX(i);
-        h[0][i] = Store<S>::ld_smem(sb, off, p.inv_scale);
+        h[0][i] = Store<S>::ld_smem(sb, off, linv);
       }
-      if (p.nopen) apply_openings<1>(p, x, y, h);
+      if (p.nopen) apply_openings<1>(p, x, y, h, FOLD ? p.scale : 1.0f);
       const float F[1][2] = {{0.f, 0.f}};
-      collide_store<S, 1, false>(p, x, y, bits, h, F);
+      collide_store<S, 1, false, false, FOLD, SR>(p, x, y, bits, h, F);
     }
     if (kn < ntiles && tid < L::ROWS * L::MW) msk0[(s ^ 1) * L::ROWS * L::MW + tid] = mnext;
     __syncthreads();
@@ -251,18 +255,21 @@ int launch_tma_t(const FluidArgs &a, int *err, cudaStream_t s, int sms) {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return -1;
   if (!configured[dev]) {
-    if (cudaFuncSetAttribute(k_fluid_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_fluid_tma<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_fluid_tma<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM) !=
+            cudaSuccess)
       return -1;
     configured[dev] = true;
   }
   int per = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fluid_tma<S>, TT_THREADS, L::SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fluid_tma<S, 1>, TT_THREADS, L::SMEM);
   if (per < 1) per = 1;
   const int ntiles = ((a.g.nx + TT_W - 1) / TT_W) * ((a.g.ny + TT_H - 1) / TT_H);
   int grid = sms * per;
   if (grid > ntiles) grid = ntiles;
-  k_fluid_tma<S><<<grid, TT_THREADS, L::SMEM, s>>>(a, err);
+  if (a.sr_seed) k_fluid_tma<S, 2><<<grid, TT_THREADS, L::SMEM, s>>>(a, err);
+  else k_fluid_tma<S, 1><<<grid, TT_THREADS, L::SMEM, s>>>(a, err);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -518,7 +518,7 @@ int one_step(lb_ctx *ctx, bool fields) {
   // two components and Shan-Chen runs keep |f - w rho_ref| large: their
   // collision is the mass-exact one
   const bool mass_exact = ctx->nc == 2 || ctx->sc;
-  const bool tma_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0 && tma_supported(ctx->storage, ctx->g);
+  const bool tma_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0 && !ctx->pm && tma_supported(ctx->storage, ctx->g);
   if (ctx->kernel == 2 && !tma_ok)
     return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component noslip lattices without "
                      "interforce whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");

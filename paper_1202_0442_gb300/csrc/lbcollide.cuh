@@ -44,18 +44,24 @@ __device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, f
 // moments, forces, equilibrium velocity, BGK and the stores of one node.
 // Fsc: interforce already evaluated (zero when off).  ME: mass-exact
 // collision (see below).  PM: the momentum as an exact hi + lo sum (single
-// component; the storage flag LB_PRECISE_MOMENTUM).
-template <class S, int NC, bool ME, bool PM = false>
+// component; the storage flag LB_PRECISE_MOMENTUM).  FOLD (scaled 16-bit
+// storage, not ME): h arrives and leaves in the stored units 2^s h, so the
+// loads and stores skip their scale factors; the moments are unscaled once
+// and the equilibrium is formed directly in stored units.  SR: 0 read
+// p.sr_seed, 1 round to nearest, 2 stochastic rounding.
+template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0>
 __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
                                               float (&h)[NC][9], const float (&Fsc)[NC][2]) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
   const int P = (int)g.plane;
   float drho[NC], rho[NC], jx[NC], jy[NC], jxl[NC], jyl[NC], Fx[NC], Fy[NC];
+  // stored units -> physical units (a power of two: exact)
+  const float un = FOLD ? p.inv_scale : 1.0f;
 #pragma unroll
   for (int c = 0; c < NC; c++) {
     const float(&f)[9] = h[c];
-    drho[c] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    drho[c] = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]) * un;
     rho[c] = p.rho_ref[c] + drho[c];
     if (PM && NC == 1) {
       momentum_exact(f, jx[c], jxl[c], jy[c], jyl[c]);
@@ -64,6 +70,10 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
       jy[c] = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
       jxl[c] = jyl[c] = 0.f;
     }
+    jx[c] *= un;
+    jy[c] *= un;
+    jxl[c] *= un;
+    jyl[c] *= un;
     Fx[c] = p.fx[c] + rho[c] * p.ax[c] + Fsc[c][0];
     Fy[c] = p.fy[c] + rho[c] * p.ay[c] + Fsc[c][1];
     if (p.ads[c]) {
@@ -105,9 +115,32 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
   for (int c = 0; c < NC; c++) {
     S *out = (S *)p.fout + (size_t)c * 9 * P;
     float heq[9];
-    equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], p.wa[c], p.wd[c], heq);
+    if (FOLD) {
+      // the equilibrium is linear in (drho, rho, rho u): in stored units
+      // it takes 2^s drho, 2^s rho and 2^s rho u at the same velocity
+      const float sc = p.scale;
+      equilibrium_pairs(drho[c] * sc, rho[c] * sc, uex[c], uey[c], mxt[c] * sc, myt[c] * sc, p.wa[c],
+                        p.wd[c], heq);
+    } else {
+      equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], p.wa[c], p.wd[c], heq);
+    }
     const float om = p.omega[c];
-    if (!ME) {
+    if (!ME && SR != 0) {
+      // SR 2: one hash per node and component, then a linear congruential
+      // sequence whose high bits dither each store
+      uint32_t r = SR == 2 ? rnd(p.sr_seed, self, c, 0) : 0u;
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        const float v = h[c][i] + om * (heq[i] - h[c][i]);
+        if (SR == 2) {
+          r = r * 1664525u + 1013904223u;
+          if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
+          else Store<S>::st_dither(out, i * P + self, v * p.scale, r);
+        } else {
+          Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
+        }
+      }
+    } else if (!ME) {
       uint32_t r = p.sr_seed ? rnd(p.sr_seed, self, c, 0) : 0u;
 #pragma unroll
       for (int i = 0; i < 9; i++) {
@@ -166,8 +199,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
       fl[P + self] = jx[c] + (jxl[c] + 0.5f * Fx[c]);
       fl[2 * P + self] = jy[c] + (jyl[c] + 0.5f * Fy[c]);
       // sum of the equilibrium populations (Mass_eq of the thermo command)
-      fl[3 * P + self] = heq[0] + ((heq[1] + heq[3]) + (heq[2] + heq[4])) +
-                         ((heq[5] + heq[7]) + (heq[6] + heq[8]));
+      fl[3 * P + self] = (heq[0] + ((heq[1] + heq[3]) + (heq[2] + heq[4])) +
+                          ((heq[5] + heq[7]) + (heq[6] + heq[8]))) * un;
     }
   }
   if (p.uout) {
@@ -185,14 +218,14 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
 
 template <int NC>
 __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
-                                               float (&h)[NC][9]) {
+                                               float (&h)[NC][9], float sc = 1.0f) {
   const Geometry &g = p.g;
   if (!(x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1)) return;
 #pragma unroll 1
   for (int k = 0; k < p.nopen; k++) {
     if (!opening_has(p.op[k], x, y, g.nx, g.ny)) continue;
 #pragma unroll
-    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, y, p.rho_ref[c]);
+    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, y, p.rho_ref[c], sc);
     break;
   }
 }

@@ -46,6 +46,8 @@ __host__ __device__ constexpr int OPP4(int i) { return (i + 2) & 3; }
 // ---------------------------------------------------------------------
 template <class S> struct Store;
 template <> struct Store<float> {
+  static constexpr bool kScaled = false;  // stored values carry no 2^s factor
+  static __device__ __forceinline__ void st_dither(float *p, size_t k, float v, uint32_t) { p[k] = v; }
   static __device__ __forceinline__ float ld(const float *p, size_t k, float) {
     return __ldg(p + k);
   }
@@ -69,6 +71,12 @@ template <> struct Store<float> {
 // that stays nearly the same from step to step then no longer rounds the
 // same way every step, which would otherwise act as a steady bias.
 template <> struct Store<__half> {
+  static constexpr bool kScaled = true;
+  // v already scaled; d: a random word, its top 13 bits dither the 13
+  // fraction bits binary16 drops (stochastic rounding)
+  static __device__ __forceinline__ void st_dither(__half *p, size_t k, float v, uint32_t d) {
+    p[k] = __float2half_rz(__uint_as_float(__float_as_uint(v) + (d >> 19)));
+  }
   static __device__ __forceinline__ float ld(const __half *p, size_t k, float inv) {
     return __half2float(__ldg(p + k)) * inv;
   }
@@ -96,6 +104,12 @@ template <> struct Store<__half> {
   }
 };
 template <> struct Store<__nv_bfloat16> {
+  static constexpr bool kScaled = false;
+  // d: a random word, its top 16 bits dither the 16 fraction bits bfloat16
+  // drops (stochastic rounding)
+  static __device__ __forceinline__ void st_dither(__nv_bfloat16 *p, size_t k, float v, uint32_t d) {
+    p[k] = __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (d >> 16)));
+  }
   static __device__ __forceinline__ float ld(const __nv_bfloat16 *p, size_t k, float) {
     return __bfloat162float(__ldg(p + k));
   }
@@ -290,9 +304,11 @@ __device__ __forceinline__ float poiseuille(float vmax, int a0, int a1, int c) {
   return 4.0f * vmax / (L * L) * (0.25f * L * L - d * d);
 }
 
-// apply the velocity/dirichlet rule of opening o to component c's h
+// apply the velocity/dirichlet rule of opening o to component c's h; sc:
+// the units h is in (the rule is homogeneous of degree one in h, drho and
+// rho_ref, so scaled storage units take sc = 2^s)
 __device__ __forceinline__ void apply_opening(const OpenDesc &o, int c, float (&h)[9],
-                                              int x, int y, float rho_ref) {
+                                              int x, int y, float rho_ref, float sc = 1.0f) {
   const int st = o.style[c];
   if (st != OPEN_POISEUILLE && st != OPEN_UNIFORM && st != OPEN_DIRICHLET) return;
   const bool dir = (st == OPEN_DIRICHLET);
@@ -304,10 +320,10 @@ __device__ __forceinline__ void apply_opening(const OpenDesc &o, int c, float (&
   }
   const float dr = o.drho[c];
   switch (o.wall) {
-    case 0: zou_he<0>(h, dir, un, dr, rho_ref); break;
-    case 1: zou_he<1>(h, dir, un, dr, rho_ref); break;
-    case 2: zou_he<2>(h, dir, un, dr, rho_ref); break;
-    default: zou_he<3>(h, dir, un, dr, rho_ref); break;
+    case 0: zou_he<0>(h, dir, un, dr * sc, rho_ref * sc); break;
+    case 1: zou_he<1>(h, dir, un, dr * sc, rho_ref * sc); break;
+    case 2: zou_he<2>(h, dir, un, dr * sc, rho_ref * sc); break;
+    default: zou_he<3>(h, dir, un, dr * sc, rho_ref * sc); break;
   }
 }
 
