@@ -3,6 +3,7 @@
     python -m paper_1202_0442_gb300.profile_target porous4096 fp32
     python -m paper_1202_0442_gb300.profile_target shanchen2048 fp32
     python -m paper_1202_0442_gb300.profile_target reactive fp32
+    python -m paper_1202_0442_gb300.profile_target batch256 fp32
 
 Sets up the named workload on cuda:0, runs a fixed number of iterations
 (thermo off, so every launch is the same kernel sequence) and exits 0.
@@ -33,6 +34,19 @@ def main(argv=None) -> int:
         w = synth.shan_chen2(2048)
     elif name == "reactive":
         w = synth.reactive()
+    elif name == "batch256":
+        # the 256 lattices of the batched workload, one launch per iteration
+        ws = synth.batch()
+        kw = {"h_max": 5e-3, "rounding": "stochastic"} if storage != "fp32" else {"precise": True}
+        lats = [lb2d.from_workload(x, storage, **kw) for x in ws]
+        for lt in lats:
+            lt.thermo(1 << 30)
+        b = lb2d.Batch(lats)
+        b.iteration(iters, use_graph=False)
+        torch.cuda.synchronize()
+        print(f"batch256 {storage}: {iters} iterations, {sum(x.nodes for x in ws)} nodes, "
+              f"{b.launch_count()} launches")
+        return 0
     else:
         raise SystemExit(f"unknown workload {name}")
     lt = lb2d.from_workload(w, storage, h_max=2e-3,
