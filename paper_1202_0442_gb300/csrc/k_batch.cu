@@ -23,7 +23,8 @@ namespace {
 // BGK with the velocity shift.  Solid and padding lanes of a warp that has
 // fluid lanes store zeros, so the warp writes whole sectors.
 template <class S>
-__device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *fout, int x, int y) {
+__device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *fout, int x, int y,
+                                           uint32_t seed) {
   const int lane = threadIdx.x, cw = x >> 5;
   const int ym = y ? y - 1 : L.ny - 1, yp = (y + 1 == L.ny) ? 0 : y + 1;
   const uint32_t *rows[3] = {L.mask + (size_t)ym * L.mw, L.mask + (size_t)y * L.mw, L.mask + (size_t)yp * L.mw};
@@ -74,17 +75,31 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
   const float ux = mx * ir, uy = my * ir;
   float heq[9];
   equilibrium_pairs(d, rho, ux, uy, mx, my, 1.0f / 9.0f, 1.0f / 36.0f, heq);
+  if (L.sr) {
+    // stochastic rounding as in the single-lattice kernels: one hash per
+    // node and launch, a linear congruential sequence per direction
+    uint32_t r = rnd(seed, self, 0, 0);
 #pragma unroll
-  for (int i = 0; i < 9; i++)
-    Store<S>::st(fout, i * P + self, h[i] + L.omega * (heq[i] - h[i]), L.scale);
+    for (int i = 0; i < 9; i++) {
+      r = r * 1664525u + 1013904223u;
+      Store<S>::st_dither(fout, i * P + self, (h[i] + L.omega * (heq[i] - h[i])) * L.scale, r);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+      Store<S>::st(fout, i * P + self, h[i] + L.omega * (heq[i] - h[i]), L.scale);
+  }
 }
 
 template <class S, int TX, int TY>
 __global__ void __launch_bounds__(256, 4) k_batch(const BatchLat *__restrict__ lat,
                                                const int4 *__restrict__ tiles, int ntiles,
                                                int parity, int dynamic,
-                                               unsigned int *counters) {
+                                               unsigned int *counters, unsigned int *tick) {
   __shared__ int s_next;
+  // this launch's number (read by every block); block 0 numbers the next
+  const unsigned int launch_no = tick[parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) tick[1 - parity] = launch_no + 1u;
   if (dynamic && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
     counters[1 - parity] = 0;  // the other parity's counter is idle now
   int k = blockIdx.x;
@@ -106,7 +121,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchLat *__restrict__ l
 #pragma unroll
       for (int dx = 0; dx < TX; dx += 32) {
         if (t.y + dx >= L.pitch) break;  // warp-uniform: the tile runs past the row
-        batch_warp<S>(L, fin, fout, t.y + dx + threadIdx.x, y);
+        batch_warp<S>(L, fin, fout, t.y + dx + threadIdx.x, y, mix32(launch_no * 0x9e3779b9u + (uint32_t)t.x));
       }
     }
     if (dynamic) {
@@ -123,7 +138,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const BatchLat *__restrict__ l
 template <class S, int TX, int TY>
 int launch_t(const BatchLaunch &b, int parity, cudaStream_t s) {
   dim3 blk(32, 8);
-  k_batch<S, TX, TY><<<b.grid, blk, 0, s>>>(b.lat, b.tiles, b.ntiles, parity, b.dynamic, b.counters);
+  k_batch<S, TX, TY><<<b.grid, blk, 0, s>>>(b.lat, b.tiles, b.ntiles, parity, b.dynamic, b.counters, b.tick);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -1455,6 +1455,7 @@ struct lb_batch {
   BatchLat *d_lat = nullptr;
   int4 *d_tiles = nullptr;
   unsigned int *d_counters = nullptr;
+  unsigned int *d_tick = nullptr;
   std::vector<BatchLat> h_lat;
   int shape = 0, dynamic = 1, order = 1;
   int ntiles = 0, grid = 0;
@@ -1554,6 +1555,7 @@ int sync_descs(lb_batch *b) {
     L.tau = (float)c->tau[0];
     L.omega = (float)(1.0 / c->tau[0]);
     L.pm = c->pm ? 1 : 0;
+    L.sr = c->sr ? 1 : 0;
     L.fx = (float)c->fave[0][0];
     L.fy = (float)c->fave[0][1];
     L.ax = (float)c->acc[0][0];
@@ -1578,6 +1580,7 @@ BatchLaunch launch_desc(lb_batch *b) {
   L.shape = b->shape;
   L.dynamic = b->dynamic;
   L.counters = b->d_counters;
+  L.tick = b->d_tick;
   return L;
 }
 
@@ -1661,7 +1664,9 @@ int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out) {
   b->storage = ctxs[0]->storage;
   if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc((void **)&b->d_lat, n * sizeof(BatchLat)) != cudaSuccess ||
       cudaMalloc((void **)&b->d_counters, 2 * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess) {
+      cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_tick, 2 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemsetAsync(b->d_tick, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess) {
     lb_batch_destroy(b);
     return LB_E_CUDA;
   }
@@ -1685,6 +1690,7 @@ int lb_batch_destroy(lb_batch *b) {
   if (b->d_lat) cudaFree(b->d_lat);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_counters) cudaFree(b->d_counters);
+  if (b->d_tick) cudaFree(b->d_tick);
   delete b;
   return LB_OK;
 }

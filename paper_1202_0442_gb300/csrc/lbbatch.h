@@ -16,6 +16,7 @@ struct BatchLat {
   const uint32_t *mask;
   float rho_ref, scale, inv_scale, tau, omega, fx, fy, ax, ay;
   int pm;              // momentum as an exact hi + lo sum
+  int sr;              // 16-bit stores rounded stochastically
 };
 
 struct BatchLaunch {
@@ -26,6 +27,8 @@ struct BatchLaunch {
   int shape;             // tile shape id (batch_shape_tx/ty)
   int dynamic;           // 0: static round robin, 1: atomic work counter
   unsigned int *counters; // two work counters (one per parity)
+  unsigned int *tick;     // two launch counters (one per parity): the
+                          // stochastic-rounding dither changes every launch
 };
 
 constexpr int BATCH_SHAPES = 6;

@@ -51,7 +51,7 @@ CASES = {
     # entering from the inlet
     "reactive_q9": (lambda: synth.reactive(q=9, inlet="pressure", C_init=0.0), 50000, ("fp32",), ()),
     "reactive_q4": (lambda: synth.reactive(q=4, inlet="pressure", C_init=0.0), 50000, ("fp32",), ()),
-    "batch8": (_batch_workloads, 5000, ("fp32", "fp16"), ()),
+    "batch8": (_batch_workloads, 5000, ("fp32", "fp32+pm", "fp16"), ()),
 }
 H_MAX = {"channel": 2e-3, "porous": 2e-3, "shan_chen2_256": 1.2, "batch8": 5e-3}
 
@@ -109,13 +109,15 @@ def run_gpu(outdir, names):
     for name in names:
         make, steps, storages, cps = CASES[name]
         for st in storages:
-            kw = {"h_max": H_MAX.get(name, 0.0)}
-            if st != "fp32":
+            # "+pm": exact FP32 momentum pairs (LB_PRECISE_MOMENTUM)
+            kw = {"h_max": H_MAX.get(name, 0.0), "precise": st.endswith("+pm")}
+            if not st.startswith("fp32"):
                 kw["rounding"] = "stochastic"
+            storage = st.split("+")[0]
             t0 = time.time()
             if name == "batch8":
                 ws = make()
-                lts = [lb2d.from_workload(w, st, thermo=0, **kw) for w in ws]
+                lts = [lb2d.from_workload(w, storage, thermo=0, **kw) for w in ws]
                 b = lb2d.Batch(lts)
                 b.iteration(steps)
                 torch.cuda.synchronize()
@@ -126,7 +128,7 @@ def run_gpu(outdir, names):
                         res[f"l{k}_{key}"] = v
             else:
                 w = make()
-                lt = lb2d.from_workload(w, st, thermo=0, **kw)
+                lt = lb2d.from_workload(w, storage, thermo=0, **kw)
                 res, done = {}, 0
                 for cp in tuple(cps) + (steps,):
                     lt.iteration(cp - done)
