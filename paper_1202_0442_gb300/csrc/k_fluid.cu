@@ -198,7 +198,26 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 2) k_fluid_sc(const FluidArgs p)
   const int x = wrapi(xr, g.nx), y = wrapi(yr, g.ny);
   const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
   const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  const uint32_t bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
+  // the warp's mask words (a warp is one 32-node row segment of the tile,
+  // x0 a multiple of 32); lanes past the lattice edge or on its first and
+  // last column read the mask directly
+  uint32_t bits;
+  {
+    const int cw = x0 >> 5;
+    const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw, p.mask + (size_t)yp * g.mw};
+    uint32_t w[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      w[r][1] = __ldg(rows[r] + cw);
+      w[r][0] = (tx == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
+      w[r][2] = (tx == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
+    }
+    if (xr >= g.nx - 1 || xr == 0)
+      bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
+    else
+      bits = row3(w[0][0], w[0][1], w[0][2], tx) | (row3(w[1][0], w[1][1], w[1][2], tx) << 3) |
+             (row3(w[2][0], w[2][1], w[2][2], tx) << 6);
+  }
   const bool solid = (bits >> 4) & 1u;
   float h[NC][9];
 #pragma unroll
