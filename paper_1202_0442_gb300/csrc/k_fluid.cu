@@ -15,6 +15,8 @@
 //   stores per node.
 // k_gradient: gradient openings, f(wall) = 2 f(wall+n) - f(wall+2n) after
 //   the collision (inlet_momentum command).
+// slip_fix: the slip, mixed and hybrid boundary styles, applied after the
+//   bounce-back pull of either kernel.
 //
 // In k_fluid_local a warp covers one 32-node word of the solid mask: its
 // lanes read the words of rows y-1, y, y+1 (one broadcast load each; the two
