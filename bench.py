@@ -85,10 +85,15 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"],
+                                          "-i", str(self.index), "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region is short: let the first sample land before it
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 2.0:
+                time.sleep(0.01)
+            self.n0 = len(self.lines)
         except Exception:
             self.proc = None
 
@@ -99,6 +104,13 @@ class ClockSampler:
     def stop(self):
         if not self.proc:
             return None
+        # and one more right after it
+        try:
+            one = subprocess.run(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                  "-i", str(self.index)], capture_output=True, text=True, timeout=10)
+            self.lines.extend(x.strip() for x in one.stdout.splitlines() if x.strip())
+        except Exception:
+            pass
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
