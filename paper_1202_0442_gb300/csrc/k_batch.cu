@@ -92,7 +92,7 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
 }
 
 template <class S, int TX, int TY>
-__global__ void __launch_bounds__(256, 4) k_batch(const BatchLat *__restrict__ lat,
+__global__ void __launch_bounds__(256, 5) k_batch(const BatchLat *__restrict__ lat,
                                                const int4 *__restrict__ tiles, int ntiles,
                                                int parity, int dynamic,
                                                unsigned int *counters, unsigned int *tick) {
