@@ -351,6 +351,13 @@ int lb_get_populations(lb_ctx *ctx, int fluid, double *f);
 int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b);
 /* Solid mask (host [ny][nx] bytes, 1 = solid). */
 int lb_get_mask(lb_ctx *ctx, uint8_t *mask);
+/* Nodes that surface growth turned solid in the last iteration executed
+ * (the last of the Nt steps of lb_iteration; growth rule of App. C):
+ * *count = their number, and the first min(count, cap) node indices
+ * y*nx + x, ascending, go to idx (cap = 0 with idx = NULL only counts).
+ * Without surface_reaction, before the first iteration and right after
+ * lb_load_state, *count = 0.  Synchronises the context's stream. */
+int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count);
 
 /* Raw state snapshot (checkpoint/resume): populations in their storage
  * format, mask, solute, step counter and, with surface_reaction, the

@@ -129,6 +129,12 @@ struct orc {
   uint8_t *flip;
   double removed[2], removed_solute;
   long nflips_last;
+  /* growth decisions taken within margin_eps * bmax of the threshold in
+   * the last iteration (trigger node, b - bmax) */
+  double margin_eps;
+  int nmargin, capmargin;
+  int64_t *margin_node;
+  double *margin_val;
   double thermo[ORC_T_COUNT];
 };
 
@@ -194,6 +200,7 @@ void orc_destroy(orc_t *o) {
   free(o->g); free(o->gt); free(o->C); free(o->db); free(o->b);
   free(o->Cw); free(o->nU); free(o->Ubits);
   free(o->Cst); free(o->Cpre);
+  free(o->margin_node); free(o->margin_val);
   free(o->Rmap[0]); free(o->Rmap[1]);
   free(o->solid); free(o->open_id); free(o->flip);
   free(o);
@@ -1080,9 +1087,18 @@ int orc_step(orc_t *o) {
 
       /* 11. growth (surface_reaction command; App. C rules 3 and 5) */
       memset(o->flip, 0, nn);
+      o->nmargin = 0;
       for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
           size_t n = (size_t)y * nx + x;
+          if (o->solid[n] && o->margin_eps > 0.0 &&
+              fabs(o->b[n] - o->bmax) <= o->margin_eps * fabs(o->bmax)) {
+            if (o->nmargin < o->capmargin) {
+              o->margin_node[o->nmargin] = (int64_t)n;
+              o->margin_val[o->nmargin] = o->b[n] - o->bmax;
+            }
+            o->nmargin++;
+          }
           if (!o->solid[n] || !(o->b[n] > o->bmax)) continue;
           size_t cand[4];
           int nc4 = 0;
@@ -1170,6 +1186,26 @@ int orc_get_solute_C(const orc_t *o, double *C) {
 int orc_get_thermo(const orc_t *o, double *out) {
   memcpy(out, o->thermo, sizeof(o->thermo));
   return 0;
+}
+
+int orc_set_margin_eps(orc_t *o, double eps, int cap) {
+  free(o->margin_node);
+  free(o->margin_val);
+  o->margin_eps = eps;
+  o->capmargin = cap > 0 ? cap : 0;
+  o->nmargin = 0;
+  o->margin_node = o->capmargin ? (int64_t *)calloc((size_t)o->capmargin, sizeof(int64_t)) : NULL;
+  o->margin_val = o->capmargin ? (double *)calloc((size_t)o->capmargin, sizeof(double)) : NULL;
+  return 0;
+}
+
+int orc_get_margin_events(const orc_t *o, int64_t *node, double *val, int cap) {
+  int n = o->nmargin < o->capmargin ? o->nmargin : o->capmargin;
+  for (int k = 0; k < n && k < cap; k++) {
+    node[k] = o->margin_node[k];
+    val[k] = o->margin_val[k];
+  }
+  return o->nmargin;
 }
 
 int orc_get_flips(const orc_t *o, int64_t *idx, int cap) {

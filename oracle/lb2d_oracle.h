@@ -105,6 +105,12 @@ int orc_get_thermo(const orc_t *o, double *out /* ORC_T_COUNT */);
 /* last step's growth events: number of flips, and the flipped node
  * indices (y*nx + x) in increasing order, up to cap */
 int orc_get_flips(const orc_t *o, int64_t *idx, int cap);
+/* growth decisions near the threshold: from now on every iteration
+ * records the solid nodes whose b lies within eps * |bmax| of bmax when the
+ * growth rule reads it (up to cap of them); get returns their number and
+ * copies (node index, b - bmax) */
+int orc_set_margin_eps(orc_t *o, double eps, int cap);
+int orc_get_margin_events(const orc_t *o, int64_t *node, double *val, int cap);
 
 /* single-node pieces, exposed for the analytic pin tests */
 void orc_feq(double rho, double ux, double uy, double alpha, double *feq);

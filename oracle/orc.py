@@ -85,6 +85,8 @@ def _load():
         "orc_set_opening_solute": (I, [P, I, I, D, D]),
         "orc_set_intersolute": (I, [P, D, D, D]),
         "orc_set_slip": (I, [P, I, D, dp]),
+        "orc_set_margin_eps": (I, [P, D, I]),
+        "orc_get_margin_events": (I, [P, C.POINTER(C.c_int64), dp, I]),
         "orc_set_reaction": (I, [P, D, D, D, D, U64]),
         "orc_step": (I, [P]),
         "orc_time": (C.c_long, [P]),
@@ -323,6 +325,18 @@ class Oracle:
         a = np.zeros(len(THERMO_KEYS))
         self._l.orc_get_thermo(self._h, _dp(a))
         return dict(zip(THERMO_KEYS, a.tolist()))
+
+    def set_margin_eps(self, eps: float, cap: int = 4096):
+        _check(self._l.orc_set_margin_eps(self._h, eps, cap), "margin eps")
+
+    def margin_events(self):
+        """(node indices, b - bmax) of the growth decisions of the last
+        iteration that lay within the margin set by set_margin_eps"""
+        n = self._l.orc_get_margin_events(self._h, None, None, 0)
+        idx = np.zeros(max(n, 1), np.int64)
+        val = np.zeros(max(n, 1))
+        self._l.orc_get_margin_events(self._h, idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(val), n)
+        return idx[:n], val[:n]
 
     def flips(self) -> np.ndarray:
         n = self._l.orc_get_flips(self._h, None, 0)

@@ -382,7 +382,8 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
 }
 
 // One CTA turns the listed nodes solid: mask bit, b = b0, their fluid and
-// solute mass booked as removed; then clears the list.  Flips of one step
+// solute mass booked as removed; then empties the list (the entries stay,
+// their number moves to fcount[1] for the host to read).  Flips of one step
 // are independent of each other, so their order does not matter.
 template <class S>
 __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
@@ -409,7 +410,8 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     if (n) atomicAdd(a.nflips, (unsigned long long)n);
-    *a.fcount = 0u;
+    a.fcount[0] = 0u;
+    a.fcount[1] = n;  // kept for reading back the step's flip list
   }
 }
 

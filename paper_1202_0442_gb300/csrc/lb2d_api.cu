@@ -327,7 +327,7 @@ int commit(lb_ctx *ctx) {
     TRY(dalloc(ctx, &ctx->db, g.plane));
     TRY(dalloc(ctx, &ctx->flip, g.plane));
     TRY(dalloc(ctx, &ctx->flist, g.plane));
-    TRY(dalloc(ctx, &ctx->fcount, 1));
+    TRY(dalloc(ctx, &ctx->fcount, 2));  // [0] running count, [1] last step's
   }
   TRY(dalloc(ctx, &ctx->b, g.plane));
   TRY(dalloc(ctx, &ctx->removed, (size_t)(ctx->nc + 1) * g.plane));
@@ -1362,6 +1362,31 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
   return LB_OK;
 }
 
+int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count) {
+  NEED_CTX();
+  if (!count || cap < 0 || (cap > 0 && !idx)) return ctx->fail(LB_E_ARG, "bad output");
+  *count = 0;
+  if (!ctx->committed || !ctx->react) return LB_OK;
+  TRY(set_device(ctx));
+  unsigned int n = 0;
+  CK(cudaMemcpyAsync(&n, ctx->fcount + 1, sizeof n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<unsigned int> off(n);
+  if (n) {
+    CK(cudaMemcpyAsync(off.data(), ctx->flist, n * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  std::vector<int64_t> node(n);
+  for (unsigned int k = 0; k < n; k++) {
+    const int64_t y = off[k] / ctx->g.pitch, x = off[k] - y * ctx->g.pitch;
+    node[k] = y * ctx->nx + x;
+  }
+  std::sort(node.begin(), node.end());
+  for (int k = 0; k < (int)n && k < cap; k++) idx[k] = node[k];
+  *count = (int)n;
+  return LB_OK;
+}
+
 // snapshot layout: header, populations (current buffer), mask, solute
 // populations, and with surface_reaction the precipitate, removed tallies
 // and flip count (without it they stay zero and are not part of the state)
@@ -1434,6 +1459,7 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
     off += p.second;
   }
   ctx->t = (int64_t)h.t;
+  if (ctx->fcount) CK(cudaMemsetAsync(ctx->fcount, 0, 2 * sizeof(unsigned int), ctx->stream));
   for (int c = 0; c < ctx->nc; c++) ctx->state_set[c] = true;
   if (ctx->qs) ctx->solute_set = true;
   return LB_OK;

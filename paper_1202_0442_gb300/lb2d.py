@@ -108,6 +108,7 @@ SIGNATURES = {
     "lb_get_populations": (I, [P, I, DP]),
     "lb_get_solute": (I, [P, DP, DP, DP]),
     "lb_get_mask": (I, [P, U8P]),
+    "lb_get_flips": (I, [P, C.POINTER(C.c_int64), I, C.POINTER(I)]),
     "lb_state_size": (I, [P, C.POINTER(C.c_size_t)]),
     "lb_save_state": (I, [P, P, SZ]),
     "lb_load_state": (I, [P, P, SZ]),
@@ -372,6 +373,15 @@ class Lattice:
         m = np.zeros((self.ny, self.nx), np.uint8)
         self._ck(self._L.lb_get_mask(self._h, m.ctypes.data_as(U8P)))
         return m
+
+    def flips(self) -> np.ndarray:
+        """Node indices (y*nx + x, ascending) that growth turned solid in
+        the last iteration executed."""
+        n = I()
+        self._ck(self._L.lb_get_flips(self._h, None, 0, C.byref(n)))
+        out = np.zeros(max(n.value, 1), np.int64)
+        self._ck(self._L.lb_get_flips(self._h, out.ctypes.data_as(C.POINTER(C.c_int64)), n.value, C.byref(n)))
+        return out[:n.value]
 
     def state_size(self) -> int:
         n = C.c_size_t()

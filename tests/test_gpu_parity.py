@@ -461,6 +461,29 @@ def test_reactive_growth_small(q):
     assert all(v < 1e-5 for v in errs.values()), errs
 
 
+@pytest.mark.parametrize("q", [4, 9])
+def test_growth_flips_each_step(q):
+    """The growth decisions themselves (App. C, rules 3 and 5), step by
+    step: the set of nodes turned solid in every iteration equals the
+    oracle's.  On a mismatch the message lists the oracle's trigger nodes
+    whose b lay within 1e-4 of bmax at that step."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3,
+                       growth_seed=7)
+    lt, o = run_pair(w, 0)
+    o.set_margin_eps(1e-4)
+    assert lt.flips().size == 0
+    steps_with, total = 0, 0
+    for t in range(1, 301):
+        lt.iteration(1)
+        o.step(1)
+        fg, fo = lt.flips(), o.flips()
+        assert np.array_equal(fg, fo), (t, np.setxor1d(fg, fo)[:10], o.margin_events())
+        steps_with += fg.size > 0
+        total += fg.size
+    print(f"q={q}: {total} flips in {steps_with} steps")
+    assert steps_with > 5
+
+
 def _flux_workload(q, inlet, outlet, nx=48, ny=6, flow=False, discs=False):
     solid = np.zeros((ny, nx), np.uint8)
     mom_in, mom_out = [], []
