@@ -18,11 +18,11 @@
 // slip_fix: the slip, mixed and hybrid boundary styles, applied after the
 //   bounce-back pull of either kernel.
 //
-// In k_fluid_local a warp covers one 32-node word of the solid mask: its
-// lanes read the words of rows y-1, y, y+1 (one broadcast load each; the two
-// edge lanes also read the words beside them) and every thread takes its
-// 3 x 3 solid neighbourhood from those, with no shared memory and no CTA
-// barrier.
+// k_fluid_local reads each node's 3 x 3 solid neighbourhood as one 16-bit
+// code (k_nbcode builds the codes from the mask once, k_apply_flips
+// refreshes them around nodes that grow solid): two bytes per node in place
+// of the mask-word arithmetic that otherwise dominates its instruction
+// count.
 #include "lbcollide.cuh"
 
 namespace lbk {
@@ -126,25 +126,12 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= g.ny) return;
-  // the warp's mask words: rows y-1, y, y+1 of its word column (broadcast
-  // loads), and for the two edge lanes the words beside them
-  uint32_t win[3][3];
-  {
-    const int lane = threadIdx.x, cw = blockIdx.x;
-    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-    const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw,
-                               p.mask + (size_t)yp * g.mw};
-#pragma unroll
-    for (int r = 0; r < 3; r++) {
-      win[r][1] = __ldg(rows[r] + cw);
-      win[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
-      win[r][2] = (lane == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
-    }
-  }
+  // x < pitch: the grid covers whole 32-node words
+  const uint32_t bits = __ldg(p.nbc + (size_t)y * g.pitch + x);
   // solid nodes (and the row padding past nx) hold no populations.  In a
   // warp that also has fluid lanes they still store zeros, so the warp
   // writes whole 32-byte sectors rather than partial ones.
-  const bool idle = x >= g.nx || ((win[1][1] >> threadIdx.x) & 1u);
+  const bool idle = (bits >> NBPOS(0, 0)) & 1u;
   const unsigned busy = __ballot_sync(0xffffffffu, !idle);
   if (idle) {
     if (busy) {
@@ -157,16 +144,6 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
       }
     }
     return;
-  }
-  uint32_t bits;
-  if (x == 0 || x == g.nx - 1) {
-    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
-    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-    bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
-  } else {
-    const int lane = threadIdx.x;
-    bits = row3(win[0][0], win[0][1], win[0][2], lane) | (row3(win[1][0], win[1][1], win[1][2], lane) << 3) |
-           (row3(win[2][0], win[2][1], win[2][2], lane) << 6);
   }
   float h[NC][9];
 #pragma unroll
@@ -345,6 +322,20 @@ __global__ void k_gradient(const GradArgs a) {
   }
 }
 
+// neighbour code of every node slot (periodic wrap, as the pull uses);
+// slots past nx are coded solid
+__global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (y >= g.ny || x >= g.pitch) return;
+  uint32_t b = 1u << NBPOS(0, 0);
+  if (x < g.nx) {
+    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+    const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+    b = nbr_bits(mask, g.mw, x, y, xm, xp, ym, yp);
+  }
+  nbc[(size_t)y * g.pitch + x] = (uint16_t)b;
+}
+
 template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
@@ -384,6 +375,12 @@ int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs 
     case ST_BF16: return launch_fluid_t<__nv_bfloat16>(nc, sc, mass_exact, a, s);
     default: return launch_fluid_t<float>(nc, sc, mass_exact, a, s);
   }
+}
+
+int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s) {
+  dim3 blk(32, 8), grd(g.pitch / 32, (g.ny + 7) / 8);
+  k_nbcode<<<grd, blk, 0, s>>>(mask, nbc, g);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s) {

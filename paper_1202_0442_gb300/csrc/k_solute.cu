@@ -408,6 +408,26 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
     }
   }
   __syncthreads();
+  // neighbour codes of the 3 x 3 neighbourhood of every flipped node, from
+  // the mask as it now stands (L2 reads: its words changed in this kernel).
+  // Overlapping neighbourhoods write the same value.
+  for (unsigned int k = threadIdx.x; k < 9u * n; k += blockDim.x) {
+    const size_t self = a.flist[k / 9];
+    const int y0 = (int)(self / (size_t)g.pitch), x0 = (int)(self - (size_t)y0 * g.pitch);
+    const int d = (int)(k % 9);
+    int x = x0 + d % 3 - 1, y = y0 + d / 3 - 1;
+    x = x < 0 ? g.nx - 1 : (x == g.nx ? 0 : x);
+    y = y < 0 ? g.ny - 1 : (y == g.ny ? 0 : y);
+    const int xs[3] = {x ? x - 1 : g.nx - 1, x, (x + 1 == g.nx) ? 0 : x + 1};
+    const int ys[3] = {y ? y - 1 : g.ny - 1, y, (y + 1 == g.ny) ? 0 : y + 1};
+    uint32_t b = 0;
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+        b |= ((__ldcg(a.mask + (size_t)ys[j] * g.mw + (xs[i] >> 5)) >> (xs[i] & 31)) & 1u) << (j * 3 + i);
+    a.nbc[(size_t)y * g.pitch + x] = (uint16_t)b;
+  }
   if (threadIdx.x == 0) {
     if (n) atomicAdd(a.nflips, (unsigned long long)n);
     a.fcount[0] = 0u;

@@ -107,6 +107,7 @@ struct lb_ctx {
   float *vstage = nullptr;  // lb_get_velocity_f32 staging (3 planes, kept)
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
+  uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
   unsigned long long *nflips = nullptr;
   double *partials = nullptr, *tout = nullptr;
   int tblocks = 0;
@@ -318,6 +319,7 @@ int commit(lb_ctx *ctx) {
   const size_t fbytes = (size_t)ctx->nc * 9 * g.plane * sb;
   for (int k = 0; k < 2; k++) TRY(dalloc(ctx, (uint8_t **)&ctx->fbuf[k], fbytes));
   TRY(dalloc(ctx, &ctx->mask, (size_t)g.ny * g.mw));
+  TRY(dalloc(ctx, &ctx->nbc, g.plane));
   TRY(dalloc(ctx, &ctx->fields, (size_t)ctx->nc * NFIELD * g.plane));
   if (ctx->qs) {
     TRY(dalloc(ctx, &ctx->u, 2 * g.plane));
@@ -344,6 +346,7 @@ int commit(lb_ctx *ctx) {
     for (int x = 0; x < g.nx; x++)
       if (ctx->solid[(size_t)y * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
   CK(cudaMemcpyAsync(ctx->mask, m.data(), m.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+  LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream));
 
   // hybrid boundary style: per-node reflection coefficients (0 on fluid
   // nodes, so nodes that grow solid later are noslip)
@@ -426,6 +429,7 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   a.fin = ctx->fbuf[ctx->cur];
   a.fout = ctx->fbuf[1 - ctx->cur];
   a.mask = ctx->mask;
+  a.nbc = ctx->nbc;
   a.scale = ctx->scale;
   a.inv_scale = ctx->inv_scale;
   for (int c = 0; c < 2; c++) {
@@ -577,6 +581,7 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.mask = ctx->mask;
       ga2.db = ctx->db;
       ga2.b = ctx->b;
+      ga2.nbc = ctx->nbc;
       ga2.flip = ctx->flip;
       ga2.flist = ctx->flist;
       ga2.fcount = ctx->fcount;
@@ -649,7 +654,7 @@ int lb_destroy(lb_ctx *ctx) {
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
                   ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
-                  ctx->vstage};
+                  ctx->vstage,  ctx->nbc};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -1460,6 +1465,7 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
   }
   ctx->t = (int64_t)h.t;
   if (ctx->fcount) CK(cudaMemsetAsync(ctx->fcount, 0, 2 * sizeof(unsigned int), ctx->stream));
+  LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
   for (int c = 0; c < ctx->nc; c++) ctx->state_set[c] = true;
   if (ctx->qs) ctx->solute_set = true;
   return LB_OK;

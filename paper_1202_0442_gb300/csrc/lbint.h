@@ -52,6 +52,9 @@ struct FluidArgs {
   const void *fin;        // populations before the step [nc][9][plane]
   void *fout;             // populations after the step
   const uint32_t *mask;
+  const uint16_t *nbc;    // per node slot [plane]: the solid bits of its 3 x 3
+                          // neighbourhood (NBPOS layout, periodic wrap);
+                          // slots past nx read as solid
   float rho_ref[2];
   float scale, inv_scale; // storage scale 2^s and 2^-s (FP16), else 1
   float tau[2], omega[2];
@@ -120,6 +123,7 @@ struct GrowthArgs {
   uint32_t *mask;
   const float *db;
   double *b;
+  uint16_t *nbc;          // neighbour codes, refreshed around every flip
   unsigned int *flip;     // per node: chosen to turn solid this step
   unsigned int *flist;    // the chosen nodes (plane offsets), *fcount of them
   unsigned int *fcount;
@@ -155,6 +159,8 @@ struct ThermoArgs {
 // launchers (return the kernel count launched, or -1 on a launch error)
 int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s);
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
+// neighbour codes of every node slot from the mask (after any mask upload)
+int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s);
 // persistent TMA-pipelined single-component kernel (k_tma.cu); err is a
 // device word the kernel sets when an mbarrier wait times out
 bool tma_supported(int storage, const Geometry &g);
