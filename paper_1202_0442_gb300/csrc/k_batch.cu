@@ -2,8 +2,8 @@
 //
 // Each lattice is a periodic single-component D2Q9 lattice with body
 // forces (pull streaming, half-way bounce-back at its solid nodes, velocity
-// shift, BGK; the same update as k_fluid_local, with the same per-warp
-// mask words and one load per direction).  The lattices are cut into
+// shift, BGK; the same update as k_fluid_local, with the same per-node
+// neighbour codes and one load per direction).  The lattices are cut into
 // TX x TY tiles listed in one array; a grid of (SM count x resident CTAs)
 // blocks walks that list either statically (tile k, k + grid, ...) or
 // dynamically (an atomic counter hands out the next tile), so a launch
@@ -17,27 +17,19 @@ namespace lbk {
 namespace {
 
 // One warp updates 32 consecutive nodes x0 .. x0+31 of row y (x0 a
-// multiple of 32, so the warp's solid bits are one mask word): mask words
-// of rows y-1, y, y+1 by broadcast loads (edge lanes also the words
-// beside them), pull with half-way bounce-back by one load per direction,
-// BGK with the velocity shift.  Solid and padding lanes of a warp that has
-// fluid lanes store zeros, so the warp writes whole sectors.
+// multiple of 32): each lane's 3 x 3 solid neighbourhood from its
+// neighbour code, pull with half-way bounce-back by one load per
+// direction, BGK with the velocity shift.  Solid and padding lanes of a
+// warp that has fluid lanes store zeros, so the warp writes whole sectors.
 template <class S>
 __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *fout, int x, int y,
                                            uint32_t seed) {
-  const int lane = threadIdx.x, cw = x >> 5;
   const int ym = y ? y - 1 : L.ny - 1, yp = (y + 1 == L.ny) ? 0 : y + 1;
-  const uint32_t *rows[3] = {L.mask + (size_t)ym * L.mw, L.mask + (size_t)y * L.mw, L.mask + (size_t)yp * L.mw};
-  uint32_t w[3][3];
-#pragma unroll
-  for (int r = 0; r < 3; r++) {
-    w[r][1] = __ldg(rows[r] + cw);
-    w[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
-    w[r][2] = (lane == 31 && cw + 1 < L.mw) ? __ldg(rows[r] + cw + 1) : 0u;
-  }
   const int P = (int)L.plane;
   const int self = y * L.pitch + x;
-  const bool idle = x >= L.nx || ((w[1][1] >> lane) & 1u);
+  // x < pitch; slots past nx are coded solid
+  const uint32_t bits = __ldg(L.nbc + self);
+  const bool idle = (bits >> NBPOS(0, 0)) & 1u;
   const unsigned busy = __ballot_sync(0xffffffffu, !idle);
   if (idle) {
     if (busy) {
@@ -47,11 +39,6 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
     return;
   }
   const int xm = x ? x - 1 : L.nx - 1, xp = (x + 1 == L.nx) ? 0 : x + 1;
-  uint32_t bits;
-  if (x == 0 || x == L.nx - 1) bits = nbr_bits(L.mask, L.mw, x, y, xm, xp, ym, yp);
-  else
-    bits = row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
-           (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
   const int r0 = y * L.pitch, rm = ym * L.pitch, rp = yp * L.pitch;
   const int src[9] = {self, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
   float h[9];

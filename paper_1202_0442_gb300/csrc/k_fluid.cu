@@ -177,28 +177,9 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
   const int xr = x0 + tx, yr = y0 + ty;
   const bool real = xr < g.nx && yr < g.ny;
   const int x = wrapi(xr, g.nx), y = wrapi(yr, g.ny);
-  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
-  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  // the warp's mask words (a warp is one 32-node row segment of the tile,
-  // x0 a multiple of 32); lanes past the lattice edge or on its first and
-  // last column read the mask directly
-  uint32_t bits;
-  {
-    const int cw = x0 >> 5;
-    const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw, p.mask + (size_t)yp * g.mw};
-    uint32_t w[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; r++) {
-      w[r][1] = __ldg(rows[r] + cw);
-      w[r][0] = (tx == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
-      w[r][2] = (tx == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
-    }
-    if (xr >= g.nx - 1 || xr == 0)
-      bits = nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
-    else
-      bits = row3(w[0][0], w[0][1], w[0][2], tx) | (row3(w[1][0], w[1][1], w[1][2], tx) << 3) |
-             (row3(w[2][0], w[2][1], w[2][2], tx) << 6);
-  }
+  // the node's 3 x 3 solid neighbourhood (lanes past the lattice edge take
+  // the wrapped node's)
+  const uint32_t bits = __ldg(p.nbc + (size_t)y * g.pitch + x);
   const bool solid = (bits >> 4) & 1u;
   float h[NC][9];
 #pragma unroll
@@ -223,9 +204,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
     else if (tid < 2 * (SC_TX + 2) + SC_TY) { sx = 0; sy = tid - 2 * (SC_TX + 2) + 1; }
     else { sx = SC_TX + 1; sy = tid - 2 * (SC_TX + 2) - SC_TY + 1; }
     const int hx = wrapi(x0 + sx - 1, g.nx), hy = wrapi(y0 + sy - 1, g.ny);
-    const int hxm = hx ? hx - 1 : g.nx - 1, hxp = (hx + 1 == g.nx) ? 0 : hx + 1;
-    const int hym = hy ? hy - 1 : g.ny - 1, hyp = (hy + 1 == g.ny) ? 0 : hy + 1;
-    const uint32_t hb = nbr_bits(p.mask, g.mw, hx, hy, hxm, hxp, hym, hyp);
+    const uint32_t hb = __ldg(p.nbc + (size_t)hy * g.pitch + hx);
     const bool hs = (hb >> 4) & 1u;
 #pragma unroll
     for (int c = 0; c < NC; c++) {

@@ -95,32 +95,10 @@ __device__ __forceinline__ void solute_pull(const SoluteArgs &p, int x, int y, i
   }
 }
 
-// 3 x 3 solid neighbourhood of any node, straight from the mask
+// 3 x 3 solid neighbourhood of node (x, y), x < pitch, y < ny: its
+// neighbour code (slots past nx read as solid)
 __device__ __forceinline__ uint32_t solute_bits(const SoluteArgs &p, int x, int y) {
-  const Geometry &g = p.g;
-  const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
-  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  return nbr_bits(p.mask, g.mw, x, y, xm, xp, ym, yp);
-}
-
-// the warp's mask words (rows y-1, y, y+1 of word column blockIdx.x, edge
-// lanes also the words beside them) and this lane's neighbourhood from
-// them (the lattice's first and last column read the mask directly)
-__device__ __forceinline__ uint32_t solute_warp_bits(const SoluteArgs &p, int x, int y) {
-  const Geometry &g = p.g;
-  const int lane = threadIdx.x, cw = blockIdx.x;
-  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  const uint32_t *rows[3] = {p.mask + (size_t)ym * g.mw, p.mask + (size_t)y * g.mw, p.mask + (size_t)yp * g.mw};
-  uint32_t w[3][3];
-#pragma unroll
-  for (int r = 0; r < 3; r++) {
-    w[r][1] = __ldg(rows[r] + cw);
-    w[r][0] = (lane == 0 && cw > 0) ? __ldg(rows[r] + cw - 1) : 0u;
-    w[r][2] = (lane == 31 && cw + 1 < g.mw) ? __ldg(rows[r] + cw + 1) : 0u;
-  }
-  if (x == 0 || x == g.nx - 1) return solute_bits(p, x, y);
-  return row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
-         (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
+  return __ldg(p.nbc + (size_t)y * p.g.pitch + x);
 }
 
 // concentration of node (x, y) right after streaming, before any opening
@@ -215,7 +193,7 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
   if (y >= g.ny) return;
-  const uint32_t bits = solute_warp_bits(p, x, y);
+  const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx) return;
   const size_t self = (size_t)y * g.pitch + x;
   if ((bits >> 4) & 1u) {
@@ -241,7 +219,7 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
   if (y >= g.ny) return;
-  const uint32_t bits = solute_warp_bits(p, x, y);
+  const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx || ((bits >> 4) & 1u)) return;
   const size_t self = (size_t)y * g.pitch + x;
   const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
@@ -305,25 +283,9 @@ __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   if (p.Cfield) p.Cfield[self] = Cn;
 }
 
-// the warp's 3 x 3 mask neighbourhoods (as solute_warp_bits)
-__device__ __forceinline__ uint32_t growth_warp_bits(const GrowthArgs &a, int x, int y) {
-  const Geometry &g = a.g;
-  const int lane = threadIdx.x, cw = blockIdx.x;
-  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  const uint32_t *rows[3] = {a.mask + (size_t)ym * g.mw, a.mask + (size_t)y * g.mw, a.mask + (size_t)yp * g.mw};
-  uint32_t w[3][3];
-#pragma unroll
-  for (int r = 0; r < 3; r++) {
-    w[r][1] = rows[r][cw];
-    w[r][0] = (lane == 0 && cw > 0) ? rows[r][cw - 1] : 0u;
-    w[r][2] = (lane == 31 && cw + 1 < g.mw) ? rows[r][cw + 1] : 0u;
-  }
-  if (x == 0 || x == g.nx - 1) {
-    const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
-    return nbr_bits(a.mask, g.mw, x, y, xm, xp, ym, yp);
-  }
-  return row3(w[0][0], w[0][1], w[0][2], lane) | (row3(w[1][0], w[1][1], w[1][2], lane) << 3) |
-         (row3(w[2][0], w[2][1], w[2][2], lane) << 6);
+// 3 x 3 solid neighbourhood of node (x, y) from its neighbour code
+__device__ __forceinline__ uint32_t growth_bits(const GrowthArgs &a, int x, int y) {
+  return __ldg(a.nbc + (size_t)y * a.g.pitch + x);
 }
 
 // Every solid node with a fluid neighbour adds the shares its fluid
@@ -337,7 +299,7 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = a.g;
   if (y >= g.ny) return;
-  const uint32_t bits = growth_warp_bits(a, x, y);
+  const uint32_t bits = growth_bits(a, x, y);
   if (x >= g.nx || !((bits >> 4) & 1u) || (bits | (1u << 4)) == 0x1ffu) return;
   const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
   const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;

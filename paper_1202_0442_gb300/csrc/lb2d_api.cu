@@ -555,6 +555,7 @@ int one_step(lb_ctx *ctx, bool fields) {
     sa.gin = ctx->gbuf[ctx->cur];
     sa.gout = ctx->gbuf[nxt];
     sa.mask = ctx->mask;
+    sa.nbc = ctx->nbc;
     sa.u = ctx->u;
     sa.omega = (float)(1.0 / ctx->taus);
     sa.react = ctx->react ? 1 : 0;
@@ -1581,6 +1582,7 @@ int sync_descs(lb_batch *b) {
     L.buf[1] = c->fbuf[1];
     L.cur = c->cur;
     L.mask = c->mask;
+    L.nbc = c->nbc;
     L.rho_ref = (float)c->rho_ref[0];
     L.scale = c->scale;
     L.inv_scale = c->inv_scale;

@@ -14,6 +14,7 @@ struct BatchLat {
   void *buf[2];        // the lattice's two population buffers
   int cur;             // buf[cur] is the input of the batch's parity-0 launch
   const uint32_t *mask;
+  const uint16_t *nbc; // per node slot: solid bits of the 3 x 3 neighbourhood
   float rho_ref, scale, inv_scale, tau, omega, fx, fy, ax, ay;
   int pm;              // momentum as an exact hi + lo sum
   int sr;              // 16-bit stores rounded stochastically

@@ -99,6 +99,7 @@ struct SoluteArgs {
   const float *gin;       // [q][plane]
   float *gout;
   const uint32_t *mask;
+  const uint16_t *nbc;    // neighbour codes (as FluidArgs::nbc)
   const float *u;         // [2][plane] solvent velocity of this step
   float omega;
   int react;
