@@ -401,6 +401,27 @@ def run_gb300(args, world, rank, local, dist):
 
     if rank != 0:
         return 0
+    # context for the roofline at this size: a plain device copy of the
+    # kernel's bytes (its populations in, its populations out) after the
+    # same L2 flush.  Outside the timed region; not a kernel of this library.
+    half = BYTES_PER_FLUID_NODE[storage] // 2 * nodes
+    csrc = torch.ones(half // 4, dtype=torch.float32, device=dev)
+    cdst = torch.empty_like(csrc)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(50)]
+    for _ in range(3):
+        flush()
+        cdst.copy_(csrc)
+    for a, b in cev:
+        flush()
+        a.record(stream)
+        cdst.copy_(csrc)
+        b.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = float(np.median([a.elapsed_time(b) for a, b in cev]))
+    copy_ctx = {"bytes": 2 * half, "gbs": 2 * half / (copy_ms * 1e-3) / 1e9, "ms": copy_ms,
+                "kernel_vs_copy": copy_ms / kernel_ms,
+                "what": "torch copy of the kernel's bytes (all node slots in and out) after the same flush"}
+    del csrc, cdst
     peak, peak_kind = peaks()
     alg_bytes = BYTES_PER_FLUID_NODE[storage] * fluid
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
@@ -419,6 +440,7 @@ def run_gb300(args, world, rank, local, dist):
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_fluid_local", "kernel_ms": kernel_ms,
                      "algorithmic_bytes_per_launch": alg_bytes},
+        "copy_same_bytes": copy_ctx,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "wall_s_timed_region": wall,

@@ -359,6 +359,35 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask);
  * lb_load_state, *count = 0.  Synchronises the context's stream. */
 int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count);
 
+/* ---- caller-owned device buffers ------------------------------------- */
+
+/* The state buffers a caller may supply instead of the library allocating
+ * them, by name:
+ *   "f0", "f1"  the two population buffers, [nc][9][ny][pitch] elements of
+ *               the storage type (FP32, or binary16 / bfloat16), each the
+ *               deviation h_i = f_i - s_i rho_ref of Eq. (2)'s rest state
+ *               (rho_ref as lb_set_storage holds it, rounded to FP32;
+ *               times 2^s for FP16); pitch = nx rounded up to 32; slots of
+ *               solid nodes and past nx are unspecified
+ *   "g0", "g1"  the two solute population buffers, [q][ny][pitch] FP32
+ *   "fields"    node fields of the last thermo step, [nc][4][ny][pitch]
+ *               FP32: rho - rho_ref, the physical momentum x and y
+ *               (j + F/2, Eq. (4)), sum of the equilibrium deviations
+ *   "u"         solvent velocity of the last step (with lb_solute),
+ *               [2][ny][pitch] FP32
+ * lb_buffer_size gives the bytes the current setup needs (0 for "u" without
+ * lb_solute).  lb_bind, after lb_lattice and before the first iteration,
+ * makes the library use dev (device memory of the context's device, 256-byte
+ * aligned, at least that many bytes) for the named buffer; dev = NULL
+ * unbinds.  The library zeroes and writes it but never frees it; the caller
+ * keeps it alive until lb_destroy.  A setup changed after binding
+ * (storage, fluids, solute) is checked against the bound size when the
+ * device state is created (first iteration or state upload: LB_E_ARG).  lb_current_buffer gives k such that f<k>
+ * and g<k> hold the current state (it alternates every iteration). */
+int lb_buffer_size(lb_ctx *ctx, const char *what, size_t *bytes);
+int lb_bind(lb_ctx *ctx, const char *what, void *dev, size_t bytes);
+int lb_current_buffer(lb_ctx *ctx, int *index);
+
 /* Raw state snapshot (checkpoint/resume): populations in their storage
  * format, mask, solute, step counter and, with surface_reaction, the
  * precipitate, removed-mass tallies and flip count.  lb_state_size gives the byte count; save/load copy to/from a

@@ -108,6 +108,9 @@ struct lb_ctx {
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
   uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
+  // caller-owned device buffers (lb_bind): f0, f1, g0, g1, fields, u
+  void *bound[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t bound_bytes[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long *nflips = nullptr;
   double *partials = nullptr, *tout = nullptr;
   int tblocks = 0;
@@ -225,11 +228,48 @@ int paint_check(lb_ctx *ctx) {
   return LB_OK;
 }
 
+// the state buffers a caller may supply (lb_bind), their sizes
+const char *const BUFFER_NAMES[6] = {"f0", "f1", "g0", "g1", "fields", "u"};
+
+int buffer_index(const char *what) {
+  if (!what) return -1;
+  for (int k = 0; k < 6; k++)
+    if (!strcmp(what, BUFFER_NAMES[k])) return k;
+  return -1;
+}
+
+size_t buffer_bytes(const lb_ctx *ctx, int k) {
+  const size_t plane = (size_t)ctx->ny * (size_t)((ctx->nx + 31) / 32 * 32);
+  switch (k) {
+    case 0:
+    case 1: return (size_t)ctx->nc * 9 * plane * storage_bytes(ctx->storage);
+    case 2:
+    case 3: return (size_t)ctx->qs * plane * sizeof(float);
+    case 4: return (size_t)ctx->nc * NFIELD * plane * sizeof(float);
+    case 5: return ctx->qs ? 2 * plane * sizeof(float) : 0;
+    default: return 0;
+  }
+}
+
 template <class T>
 int dalloc(lb_ctx *ctx, T **p, size_t n) {
   cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) ? n * sizeof(T) : 1);
   if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "cudaMalloc(%zu): %s", n * sizeof(T), cudaGetErrorString(e));
   e = cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
+  return LB_OK;
+}
+
+// a state buffer: the caller's (lb_bind) when bound, else allocated here;
+// either way zeroed
+template <class T>
+int dalloc_state(lb_ctx *ctx, T **p, size_t n, int k) {
+  if (!ctx->bound[k]) return dalloc(ctx, p, n);
+  if (ctx->bound_bytes[k] < n * sizeof(T))
+    return ctx->fail(LB_E_ARG, "bound buffer %s holds %zu bytes, the setup needs %zu", BUFFER_NAMES[k],
+                     ctx->bound_bytes[k], n * sizeof(T));
+  *p = (T *)ctx->bound[k];
+  const cudaError_t e = cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
   return LB_OK;
 }
@@ -317,13 +357,13 @@ int commit(lb_ctx *ctx) {
   g.plane = (size_t)g.ny * g.pitch;
   const size_t sb = storage_bytes(ctx->storage);
   const size_t fbytes = (size_t)ctx->nc * 9 * g.plane * sb;
-  for (int k = 0; k < 2; k++) TRY(dalloc(ctx, (uint8_t **)&ctx->fbuf[k], fbytes));
+  for (int k = 0; k < 2; k++) TRY(dalloc_state(ctx, (uint8_t **)&ctx->fbuf[k], fbytes, k));
   TRY(dalloc(ctx, &ctx->mask, (size_t)g.ny * g.mw));
   TRY(dalloc(ctx, &ctx->nbc, g.plane));
-  TRY(dalloc(ctx, &ctx->fields, (size_t)ctx->nc * NFIELD * g.plane));
+  TRY(dalloc_state(ctx, &ctx->fields, (size_t)ctx->nc * NFIELD * g.plane, 4));
   if (ctx->qs) {
-    TRY(dalloc(ctx, &ctx->u, 2 * g.plane));
-    for (int k = 0; k < 2; k++) TRY(dalloc(ctx, &ctx->gbuf[k], (size_t)ctx->qs * g.plane));
+    TRY(dalloc_state(ctx, &ctx->u, 2 * g.plane, 5));
+    for (int k = 0; k < 2; k++) TRY(dalloc_state(ctx, &ctx->gbuf[k], (size_t)ctx->qs * g.plane, 2 + k));
     if (ctx->inter) TRY(dalloc(ctx, &ctx->Cpre, g.plane));
     TRY(dalloc(ctx, &ctx->Cfield, g.plane));
     TRY(dalloc(ctx, &ctx->db, g.plane));
@@ -656,8 +696,11 @@ int lb_destroy(lb_ctx *ctx) {
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
                   ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
                   ctx->vstage,  ctx->nbc};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
+  for (void *p : ptrs) {
+    bool own = p != nullptr;
+    for (int k = 0; k < 6; k++) own = own && p != ctx->bound[k];
+    if (own) cudaFree(p);
+  }
   delete ctx;
   return LB_OK;
 }
@@ -1365,6 +1408,50 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
   for (int y = 0; y < ctx->ny; y++)
     for (int x = 0; x < ctx->nx; x++)
       mask[(size_t)y * ctx->nx + x] = (m[(size_t)y * ctx->g.mw + (x >> 5)] >> (x & 31)) & 1u;
+  return LB_OK;
+}
+
+int lb_buffer_size(lb_ctx *ctx, const char *what, size_t *bytes) {
+  NEED_CTX();
+  const int k = buffer_index(what);
+  if (k < 0 || !bytes) return ctx->fail(LB_E_ARG, "unknown buffer name or null output");
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  *bytes = buffer_bytes(ctx, k);
+  return LB_OK;
+}
+
+int lb_bind(lb_ctx *ctx, const char *what, void *dev, size_t bytes) {
+  NEED_CTX();
+  const int k = buffer_index(what);
+  if (k < 0) return ctx->fail(LB_E_ARG, "unknown buffer name");
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
+  if (ctx->committed) return ctx->fail(LB_E_ORDER, "buffers are fixed after the first iteration");
+  if (!dev) {
+    ctx->bound[k] = nullptr;
+    ctx->bound_bytes[k] = 0;
+    return LB_OK;
+  }
+  if ((uintptr_t)dev % 256 != 0) return ctx->fail(LB_E_ARG, "bound buffer must be 256-byte aligned");
+  if (bytes < buffer_bytes(ctx, k))
+    return ctx->fail(LB_E_ARG, "buffer %s needs %zu bytes, got %zu", what, buffer_bytes(ctx, k), bytes);
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx->fail(LB_E_ARG, "not a device pointer");
+  }
+  if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != ctx->device)
+    return ctx->fail(LB_E_ARG, "buffer %s is not device memory of device %d", what, ctx->device);
+  for (int j = 0; j < 6; j++)
+    if (j != k && ctx->bound[j] == dev) return ctx->fail(LB_E_ARG, "one buffer bound twice");
+  ctx->bound[k] = dev;
+  ctx->bound_bytes[k] = bytes;
+  return LB_OK;
+}
+
+int lb_current_buffer(lb_ctx *ctx, int *index) {
+  NEED_CTX();
+  if (!index) return ctx->fail(LB_E_ARG, "null output");
+  *index = ctx->cur;
   return LB_OK;
 }
 

@@ -109,6 +109,9 @@ SIGNATURES = {
     "lb_get_solute": (I, [P, DP, DP, DP]),
     "lb_get_mask": (I, [P, U8P]),
     "lb_get_flips": (I, [P, C.POINTER(C.c_int64), I, C.POINTER(I)]),
+    "lb_buffer_size": (I, [P, S, C.POINTER(SZ)]),
+    "lb_bind": (I, [P, S, P, SZ]),
+    "lb_current_buffer": (I, [P, C.POINTER(I)]),
     "lb_state_size": (I, [P, C.POINTER(C.c_size_t)]),
     "lb_save_state": (I, [P, P, SZ]),
     "lb_load_state": (I, [P, P, SZ]),
@@ -167,6 +170,7 @@ class Lattice:
             raise LBError(rc, "lb_create failed (no CUDA device?)")
         self._h = h
         self.device = device
+        self._bound = {}  # name -> caller tensor kept alive while bound
         self.nx = self.ny = 0
         self.ncomp = 1
         self.q = 0
@@ -179,6 +183,7 @@ class Lattice:
 
     def close(self):
         self.__del__()
+        self._bound = {}
 
     def _ck(self, rc: int):
         if rc != LB_OK:
@@ -374,6 +379,34 @@ class Lattice:
         self._ck(self._L.lb_get_mask(self._h, m.ctypes.data_as(U8P)))
         return m
 
+    def buffer_size(self, what: str) -> int:
+        """Bytes the named state buffer ("f0", "f1", "g0", "g1", "fields",
+        "u") needs under the current setup."""
+        n = SZ()
+        self._ck(self._L.lb_buffer_size(self._h, what.encode(), C.byref(n)))
+        return n.value
+
+    def bind(self, what: str, tensor) -> None:
+        """Use a caller-owned CUDA tensor (contiguous, on this device, at
+        least buffer_size(what) bytes) as the named state buffer; the
+        library writes it in place and the lattice keeps a reference.
+        ``None`` unbinds.  Before the first iteration."""
+        if tensor is None:
+            self._ck(self._L.lb_bind(self._h, what.encode(), None, 0))
+            self._bound.pop(what, None)
+            return
+        if not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("bind needs a contiguous CUDA tensor")
+        nbytes = tensor.numel() * tensor.element_size()
+        self._ck(self._L.lb_bind(self._h, what.encode(), C.c_void_p(tensor.data_ptr()), nbytes))
+        self._bound[what] = tensor
+
+    def current_buffer(self) -> int:
+        """k such that f<k> (and g<k>) hold the current state."""
+        k = I()
+        self._ck(self._L.lb_current_buffer(self._h, C.byref(k)))
+        return k.value
+
     def flips(self) -> np.ndarray:
         """Node indices (y*nx + x, ascending) that growth turned solid in
         the last iteration executed."""
@@ -467,8 +500,10 @@ class Batch:
 
 def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0,
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
-                  rounding: str = "nearest", kernel: str = "auto", precise: bool = False) -> Lattice:
-    """Issue the command sequence that sets up workload ``w``."""
+                  rounding: str = "nearest", kernel: str = "auto", precise: bool = False,
+                  bind: Optional[dict] = None) -> Lattice:
+    """Issue the command sequence that sets up workload ``w``.  ``bind``:
+    state buffer name -> caller-owned CUDA tensor (Lattice.bind)."""
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
     if w.ncomp == 2:
@@ -477,6 +512,8 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
     if w.solute_q:
         lt.solute(w.taus, w.solute_q)
     lt.set_storage(storage, list(w.rho_ref), h_max, rounding, precise)
+    for name, tensor in (bind or {}).items():
+        lt.bind(name, tensor)
     slip = list(getattr(w, "slip", None) or ())
     if any(np.ndim(R) > 0 for R in slip if R is not None):
         # hybrid: per-node coefficients, per component
