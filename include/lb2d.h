@@ -351,6 +351,15 @@ int lb_get_populations(lb_ctx *ctx, int fluid, double *f);
 int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b);
 /* Solid mask (host [ny][nx] bytes, 1 = solid). */
 int lb_get_mask(lb_ctx *ctx, uint8_t *mask);
+/* Set the count of iterations done to t >= 0 (any time).  The growth
+ * rule's random pick (seed and step, App. C) and the thermo schedule read
+ * it, so a state taken from another run at step t (with lb_set_populations,
+ * lb_set_solute_populations, lb_set_precipitate) continues with that run's
+ * decisions.  Called with t > 0 before the device state exists, it also
+ * admits a geometry that growth has made: fluid nodes with reactive links
+ * on two opposite sides, which a fresh lb_surface_reaction setup refuses
+ * (App. C rule 1), each link then taking the link rule on its own. */
+int lb_set_step(lb_ctx *ctx, int64_t t);
 /* Nodes that surface growth turned solid in the last iteration executed
  * (the last of the Nt steps of lb_iteration; growth rule of App. C):
  * *count = their number, and the first min(count, cap) node indices

@@ -320,8 +320,10 @@ int validate(lb_ctx *ctx) {
         return ctx->fail(LB_E_ARG, "inlet flux style needs v != -D = %g", -D);
     }
   }
-  if (ctx->react) {
-    // App. C rule 1: two opposite unknown modes cannot occur
+  if (ctx->react && ctx->t == 0) {
+    // App. C rule 1: two opposite unknown modes cannot occur in the initial
+    // geometry (growth can make them later; a lattice that continues a run,
+    // lb_set_step t > 0, may hold them, each link then taking its own rule)
     const int q = ctx->qs;
     for (int y = 0; y < ny; y++)
       for (int x = 0; x < nx; x++) {
@@ -1408,6 +1410,13 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
   for (int y = 0; y < ctx->ny; y++)
     for (int x = 0; x < ctx->nx; x++)
       mask[(size_t)y * ctx->nx + x] = (m[(size_t)y * ctx->g.mw + (x >> 5)] >> (x & 31)) & 1u;
+  return LB_OK;
+}
+
+int lb_set_step(lb_ctx *ctx, int64_t t) {
+  NEED_CTX();
+  if (t < 0) return ctx->fail(LB_E_ARG, "t must be >= 0");
+  ctx->t = t;
   return LB_OK;
 }
 

@@ -110,6 +110,7 @@ SIGNATURES = {
     "lb_get_mask": (I, [P, U8P]),
     "lb_get_flips": (I, [P, C.POINTER(C.c_int64), I, C.POINTER(I)]),
     "lb_buffer_size": (I, [P, S, C.POINTER(SZ)]),
+    "lb_set_step": (I, [P, C.c_int64]),
     "lb_bind": (I, [P, S, P, SZ]),
     "lb_current_buffer": (I, [P, C.POINTER(I)]),
     "lb_state_size": (I, [P, C.POINTER(C.c_size_t)]),
@@ -299,6 +300,10 @@ class Lattice:
     def set_precipitate(self, b):
         a = _f64(b, (self.ny, self.nx))
         self._ck(self._L.lb_set_precipitate(self._h, _dp(a)))
+
+    def set_step(self, t: int):
+        """Iterations done so far (the growth pick and thermo schedule use it)."""
+        self._ck(self._L.lb_set_step(self._h, int(t)))
 
     # -- force fields --------------------------------------------------------
     def aveforce(self, mode: int, value: float, fluid: int = 1):
@@ -501,11 +506,14 @@ class Batch:
 def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0,
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
                   rounding: str = "nearest", kernel: str = "auto", precise: bool = False,
-                  bind: Optional[dict] = None) -> Lattice:
+                  bind: Optional[dict] = None, step: int = 0) -> Lattice:
     """Issue the command sequence that sets up workload ``w``.  ``bind``:
-    state buffer name -> caller-owned CUDA tensor (Lattice.bind)."""
+    state buffer name -> caller-owned CUDA tensor (Lattice.bind); ``step``:
+    iterations already done (a state that continues another run)."""
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
+    if step:
+        lt.set_step(step)
     if w.ncomp == 2:
         al = list(w.alpha) + [4.0 / 9.0] * (2 - len(w.alpha))
         lt.fluids(w.tau[0], w.tau[1], al[0], al[1])

@@ -4,6 +4,8 @@ Tolerances: FP32 storage 1e-5 (max relative error in rho and u, measured
 as max|u - u_ref| / max|u_ref| over fluid nodes); 16-bit storage 2e-3 for
 FP16; masks and growth events exact.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -482,6 +484,61 @@ def test_growth_flips_each_step(q):
         total += fg.size
     print(f"q={q}: {total} flips in {steps_with} steps")
     assert steps_with > 5
+
+
+@pytest.mark.parametrize("q", [4, 9])
+def test_growth_flips_windowed(q):
+    """Growth decisions over a long run, the two sides kept together by
+    restarting the GPU from the oracle's state (populations, solute,
+    deposits, mask, step) every 250 iterations; nothing of the GPU run goes
+    into the oracle.  Inside a window every step's flip set must equal the
+    oracle's, except at a step where a trigger's b lies within 2e-6 bmax of
+    bmax in the oracle's arithmetic (FP32 fields feed the FP64 b): such a
+    step ends the window and is listed."""
+    # pressure-driven: with the uniform-velocity inlet, growth closes cells
+    # beside the inlet and the run diverges (oracle and GPU alike)
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3,
+                       growth_seed=7, inlet="pressure")
+    bmax = w.reaction[3]
+    T, WIN = 2500, 250
+    o = oracle_from_workload(w)
+    o.set_margin_eps(2e-6, 1 << 12)
+    states, oflips, margins = {}, {}, {}
+    for t in range(T):
+        if t % WIN == 0:
+            states[t] = (o.f(0).copy(), o.g().copy(), o.b().copy(), o.solid().copy())
+        o.step(1)
+        oflips[t + 1] = o.flips()
+        idx, val = o.margin_events()
+        margins[t + 1] = {int(i): float(v) / bmax for i, v in zip(idx, val)}
+    total = sum(f.size for f in oflips.values())
+    compared, matched, listed = 0, 0, []
+    for t0, (f, g, b, solid) in states.items():
+        ww = copy.copy(w)
+        ww.solid = solid.astype(np.uint8)
+        lt = lb2d.from_workload(ww, step=t0)
+        lt.set_populations(f)
+        lt.set_solute_populations(g)
+        lt.set_precipitate(b)
+        for t in range(t0 + 1, t0 + WIN + 1):
+            lt.iteration(1)
+            fg, fo = lt.flips(), oflips[t]
+            compared += 1
+            if np.array_equal(fg, fo):
+                matched += fg.size
+                continue
+            for n in np.setxor1d(fg, fo):
+                y, x = divmod(int(n), w.nx)
+                near = [m for m in ((yy % w.ny) * w.nx + (xx % w.nx) for yy in (y - 1, y, y + 1)
+                                    for xx in (x - 1, x, x + 1)) if m in margins[t]]
+                assert near, (t, int(n), "mismatch away from the threshold")
+            listed.append(t)
+            break
+    print(f"q={q}: {total} oracle flips in {T} steps, {matched} matched, {compared} steps compared, "
+          f"near-threshold stops at {listed}")
+    assert total > 100
+    assert compared >= 0.8 * T
+    assert len(listed) <= 2
 
 
 def _flux_workload(q, inlet, outlet, nx=48, ny=6, flow=False, discs=False):
