@@ -137,6 +137,84 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (ctypes, read-only
+    queries) every 2 ms on a thread while the timed region runs; the
+    GPU is found by its PCI address, so the CUDA and NVML numberings need
+    not agree."""
+    # clock-event reason bits of the NVML API
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, device: int):
+        import ctypes
+        import torch
+        self.C = ctypes
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        pr = torch.cuda.get_device_properties(device)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle for " + bus.decode())
+        self.reasons_fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM
+        self.max_mhz = float(mx.value)
+        self.samples = []
+        self.run = False
+        self._one()  # fails here, not in the thread, if a query is refused
+
+    def _one(self):
+        C = self.C
+        mhz, rs = C.c_uint(), C.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) != 0:
+            raise RuntimeError("clock query failed")
+        self.reasons_fn(self.h, C.byref(rs))
+        self.samples.append((float(mhz.value), int(rs.value)))
+
+    def _loop(self):
+        while self.run:
+            try:
+                self._one()
+            except Exception:
+                return
+            time.sleep(0.002)
+
+    def start(self):
+        self.samples = []
+        self.run = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 1.0:
+            time.sleep(0.0005)
+
+    def stop(self):
+        self.run = False
+        self.t.join(timeout=2)
+        try:
+            self._one()
+        except Exception:
+            pass
+        self.nv.nvmlShutdown()
+        if not self.samples:
+            return None
+        reasons = sorted({nm for _, r in self.samples for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": float(np.median([m for m, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml, every 2 ms"}
+
+
+def clock_sampler(device: int):
+    """NVML sampler where the driver's library loads, else nvidia-smi."""
+    try:
+        return NvmlSampler(device)
+    except Exception:
+        return ClockSampler(device)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -346,7 +424,7 @@ def run_gb300(args, world, rank, local, dist):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     thermo_step = []
-    sampler = ClockSampler(local) if local == 0 else None
+    sampler = clock_sampler(local) if local == 0 else None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
