@@ -1065,6 +1065,30 @@ def test_growth_single_trigger():
     assert np.isclose(th["solute"] + th["removed_solute"], g_before.sum(), rtol=1e-13)
 
 
+def test_growth_margin_records():
+    """The oracle's own record of growth decisions taken near the threshold
+    (used to place a GPU/oracle difference in growth): a trigger whose b is
+    within the margin of b_max is listed with b - b_max whichever way the
+    strict b > b_max rule (App. C rule 3) decides; one outside is not."""
+    for db, nflip in ((1e-7, 1), (-1e-7, 0)):
+        o, _ = _growth_case(seed=42)
+        b = o.b()
+        b[2, 2] = 1.0 + db
+        o.set_b(b)
+        o.set_margin_eps(1e-6)
+        o.step()
+        idx, val = o.margin_events()
+        assert list(idx) == [12] and abs(val[0] - db) < 1e-15
+        assert len(o.flips()) == nflip
+    o, _ = _growth_case(seed=42)
+    b = o.b()
+    b[2, 2] = 1.0 + 1e-3
+    o.set_b(b)
+    o.set_margin_eps(1e-6)
+    o.step()
+    assert len(o.margin_events()[0]) == 0 and len(o.flips()) == 1
+
+
 def test_growth_choice_is_equiprobable():
     """Every fluid 4-neighbour is equally likely (surface_reaction command;
     App. C rule 3): over 2000 seeds each of 4 candidates, and each of 2
