@@ -300,9 +300,13 @@ int lb_thermo(lb_ctx *ctx, int Nf);
  * on GB300), "tma" (a persistent kernel that streams 128 x 4 tiles into
  * shared memory with bulk asynchronous copies; same results bit for bit,
  * needs the width to be a multiple of 4 nodes for FP32 or 8 for 16-bit
- * storage) or "auto" (streaming, the default).  Other lattices always use
- * the streaming kernels.  A timed-out wait inside the TMA kernel is
- * reported as LB_E_TIMEOUT at the next thermo evaluation. */
+ * storage), "fused" (with a solute and without intersolute or exact
+ * momentum pairs: the fluid and the solute update in one kernel, the
+ * solvent velocity kept in registers; same results bit for bit) or "auto"
+ * (fused where it applies, else streaming; the default).  Other lattices
+ * always use the streaming kernels.  A timed-out wait inside the TMA kernel
+ * is reported as LB_E_TIMEOUT at the next thermo evaluation; a kernel that
+ * does not apply to the setup fails the iteration with LB_E_UNSUPPORTED. */
 int lb_set_kernel(lb_ctx *ctx, const char *name);
 
 /* iteration command: advance Nt iterations.  The first call validates the
@@ -383,7 +387,8 @@ int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count);
  *               FP32: rho - rho_ref, the physical momentum x and y
  *               (j + F/2, Eq. (4)), sum of the equilibrium deviations
  *   "u"         solvent velocity of the last step (with lb_solute),
- *               [2][ny][pitch] FP32
+ *               [2][ny][pitch] FP32 (the fused kernel writes it only
+ *               when it is bound)
  * lb_buffer_size gives the bytes the current setup needs (0 for "u" without
  * lb_solute).  lb_bind, after lb_lattice and before the first iteration,
  * makes the library use dev (device memory of the context's device, 256-byte

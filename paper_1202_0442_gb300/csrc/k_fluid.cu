@@ -24,15 +24,11 @@
 // of the mask-word arithmetic that otherwise dominates its instruction
 // count.
 #include "lbcollide.cuh"
+#include "lbsolute.cuh"
 
 namespace lbk {
 
 namespace {
-
-__device__ __forceinline__ int wrapi(int a, int n) {
-  a %= n;
-  return a < 0 ? a + n : a;
-}
 
 // pull the nine populations of node (x, y) from `base` (one component),
 // bouncing back from solid sources; `bits` is the node's neighbourhood.
@@ -118,16 +114,16 @@ constexpr int LOC_BY = 8;
 
 // SR: 0 rounding read from p.sr_seed, 1 nearest, 2 stochastic (16-bit,
 // not ME).  Scaled 16-bit storage without ME runs folded (collide_store).
+// The update of node (x, y) given its neighbour code (called by every lane
+// of a warp: the warp votes on its solid lanes).  Returns false on solid
+// nodes and row padding.  uo, if given, receives the node's solvent
+// velocity of Eq. (4).
 template <class S, int NC, bool ME, bool PM, int SR>
-__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
+__device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uint32_t bits,
+                                           float *uo = nullptr) {
   constexpr bool FOLD = Store<S>::kScaled && !ME;
   const float linv = FOLD ? 1.0f : p.inv_scale;
   const Geometry &g = p.g;
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * LOC_BY + threadIdx.y;
-  if (y >= g.ny) return;
-  // x < pitch: the grid covers whole 32-node words
-  const uint32_t bits = __ldg(p.nbc + (size_t)y * g.pitch + x);
   // solid nodes (and the row padding past nx) hold no populations.  In a
   // warp that also has fluid lanes they still store zeros, so the warp
   // writes whole 32-byte sectors rather than partial ones.
@@ -143,7 +139,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
         for (int i = 0; i < 9; i++) Store<S>::st(out, i * (int)g.plane + self, 0.0f, 1.0f);
       }
     }
-    return;
+    return false;
   }
   float h[NC][9];
 #pragma unroll
@@ -158,7 +154,32 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
   float F[NC][2];
 #pragma unroll
   for (int c = 0; c < NC; c++) F[c][0] = F[c][1] = 0.f;
-  collide_store<S, NC, ME, PM, FOLD, SR>(p, x, y, bits, h, F);
+  collide_store<S, NC, ME, PM, FOLD, SR>(p, x, y, bits, h, F, uo);
+  return true;
+}
+
+template <class S, int NC, bool ME, bool PM, int SR>
+__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.ny) return;
+  // x < pitch: the grid covers whole 32-node words
+  fluid_node<S, NC, ME, PM, SR>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
+}
+
+// One fluid and one solute iteration of a single-component lattice in one
+// pass (no intersolute): the solute update of a node needs only its own
+// solvent velocity of this iteration, which stays in registers, and the
+// previous iteration's solute populations around it.
+template <class S, int SR, int Q>
+__global__ void __launch_bounds__(32 * LOC_BY, 4) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.ny) return;
+  const uint32_t bits = __ldg(p.nbc + (size_t)y * p.g.pitch + x);
+  float u[2];
+  if (!fluid_node<S, 1, false, false, SR>(p, x, y, bits, u)) return;
+  solute_node<Q>(sp, x, y, bits, u[0], u[1]);
 }
 
 // 32 x 8 tiles, 4 CTAs/SM: measured fastest of 32 x {4, 8, 16, 32} (the
@@ -353,6 +374,25 @@ int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs 
     case ST_FP16: return launch_fluid_t<__half>(nc, sc, mass_exact, a, s);
     case ST_BF16: return launch_fluid_t<__nv_bfloat16>(nc, sc, mass_exact, a, s);
     default: return launch_fluid_t<float>(nc, sc, mass_exact, a, s);
+  }
+}
+
+template <class S, int SR>
+int launch_fluid_solute_t(int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
+  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
+  if (q == 4) k_fluid_solute<S, SR, 4><<<grd, blk, 0, s>>>(a, sa);
+  else k_fluid_solute<S, SR, 9><<<grd, blk, 0, s>>>(a, sa);
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_fluid_solute(int storage, int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
+  switch (storage) {
+    case ST_FP16:
+      return a.sr_seed ? launch_fluid_solute_t<__half, 2>(q, a, sa, s) : launch_fluid_solute_t<__half, 1>(q, a, sa, s);
+    case ST_BF16:
+      return a.sr_seed ? launch_fluid_solute_t<__nv_bfloat16, 2>(q, a, sa, s)
+                       : launch_fluid_solute_t<__nv_bfloat16, 1>(q, a, sa, s);
+    default: return launch_fluid_solute_t<float, 1>(q, a, sa, s);
   }
 }
 

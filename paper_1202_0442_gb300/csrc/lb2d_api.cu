@@ -568,31 +568,8 @@ int one_step(lb_ctx *ctx, bool fields) {
   if (ctx->kernel == 2 && !tma_ok)
     return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component noslip lattices without "
                      "interforce whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
-  if (tma_ok && ctx->kernel == 2)
-    LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, s, ctx->sms));
-  else
-    LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
-  // gradient openings
-  GradArgs ga{};
-  int ng = 0;
-  for (const Opening &o : ctx->open) {
-    bool grad = false;
-    for (int c = 0; c < ctx->nc; c++) grad |= o.style[c] == OPEN_GRADIENT;
-    if (grad) ga.op[ng++] = desc_of(ctx, o);
-  }
-  if (ng) {
-    ga.g = ctx->g;
-    ga.f = ctx->fbuf[nxt];
-    ga.fields = fields ? ctx->fields : nullptr;
-    ga.mask = ctx->mask;
-    ga.nc = ctx->nc;
-    ga.nopen = ng;
-    ga.inv_scale = ctx->inv_scale;
-    ga.scale = ctx->scale;
-    LAUNCH(launch_gradient(ctx->storage, ga, s));
-  }
+  SoluteArgs sa{};
   if (ctx->qs) {
-    SoluteArgs sa{};
     sa.g = ctx->g;
     sa.gin = ctx->gbuf[ctx->cur];
     sa.gout = ctx->gbuf[nxt];
@@ -617,7 +594,46 @@ int one_step(lb_ctx *ctx, bool fields) {
     sa.taus = (float)ctx->taus;
     sa.Cpre = ctx->Cpre;
     sa.Cpre_out = ctx->Cpre;
-    LAUNCH(launch_solute(ctx->qs, sa, s));
+  }
+  // fluid and solute in one kernel where the solute needs nothing of other
+  // nodes' fluid update (no intersolute) and the fluid kernel is the plain
+  // streaming one
+  const bool fuse_ok = ctx->qs && !ctx->inter && ctx->nc == 1 && !ctx->sc && !ctx->pm;
+  if (ctx->kernel == 3 && !fuse_ok)
+    return ctx->fail(LB_E_UNSUPPORTED, "the fused kernel runs single-component lattices with a solute, "
+                     "without interforce, intersolute or exact momentum pairs");
+  const bool fused = fuse_ok && (ctx->kernel == 0 || ctx->kernel == 3);
+  if (fused) {
+    // the solvent velocity stays in registers; the plane is written only
+    // when the caller bound it
+    fa.uout = ctx->bound[5] ? ctx->u : nullptr;
+    LAUNCH(launch_fluid_solute(ctx->storage, ctx->qs, fa, sa, s));
+  } else if (tma_ok && ctx->kernel == 2) {
+    LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, s, ctx->sms));
+  } else {
+    LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
+  }
+  // gradient openings
+  GradArgs ga{};
+  int ng = 0;
+  for (const Opening &o : ctx->open) {
+    bool grad = false;
+    for (int c = 0; c < ctx->nc; c++) grad |= o.style[c] == OPEN_GRADIENT;
+    if (grad) ga.op[ng++] = desc_of(ctx, o);
+  }
+  if (ng) {
+    ga.g = ctx->g;
+    ga.f = ctx->fbuf[nxt];
+    ga.fields = fields ? ctx->fields : nullptr;
+    ga.mask = ctx->mask;
+    ga.nc = ctx->nc;
+    ga.nopen = ng;
+    ga.inv_scale = ctx->inv_scale;
+    ga.scale = ctx->scale;
+    LAUNCH(launch_gradient(ctx->storage, ga, s));
+  }
+  if (ctx->qs) {
+    if (!fused) LAUNCH(launch_solute(ctx->qs, sa, s));
     if (ctx->react) {
       GrowthArgs ga2{};
       ga2.g = ctx->g;
@@ -1265,7 +1281,8 @@ int lb_set_kernel(lb_ctx *ctx, const char *name) {
   if (!strcmp(name, "auto")) ctx->kernel = 0;
   else if (!strcmp(name, "streaming")) ctx->kernel = 1;
   else if (!strcmp(name, "tma")) ctx->kernel = 2;
-  else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming or tma");
+  else if (!strcmp(name, "fused")) ctx->kernel = 3;
+  else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming, tma or fused");
   return LB_OK;
 }
 

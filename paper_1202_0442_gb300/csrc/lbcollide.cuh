@@ -51,7 +51,8 @@ __device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, f
 // p.sr_seed, 1 round to nearest, 2 stochastic rounding.
 template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0>
 __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
-                                              float (&h)[NC][9], const float (&Fsc)[NC][2]) {
+                                              float (&h)[NC][9], const float (&Fsc)[NC][2],
+                                              float *uo = nullptr) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
   const int P = (int)g.plane;
@@ -209,7 +210,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
                           ((heq[5] + heq[7]) + (heq[6] + heq[8]))) * un;
     }
   }
-  if (p.uout) {
+  if (p.uout || uo) {
+    // the solvent velocity of Eq. (4)
     float pxs = 0.f, pys = 0.f, rs = 0.f;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
@@ -217,8 +219,15 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
       pys += jy[c] + (jyl[c] + 0.5f * Fy[c]);
       rs += rho[c];
     }
-    p.uout[self] = pxs / rs;
-    p.uout[P + self] = pys / rs;
+    const float vx = pxs / rs, vy = pys / rs;
+    if (uo) {
+      uo[0] = vx;
+      uo[1] = vy;
+    }
+    if (p.uout) {
+      p.uout[self] = vx;
+      p.uout[P + self] = vy;
+    }
   }
 }
 

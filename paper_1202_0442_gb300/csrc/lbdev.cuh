@@ -155,6 +155,12 @@ __device__ __forceinline__ int solid_at(const uint32_t *m, int mw, int x, int y)
   return (int)((__ldg(m + (size_t)y * mw + (x >> 5)) >> (x & 31)) & 1u);
 }
 
+// a mod n in [0, n)
+__device__ __forceinline__ int wrapi(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
 // Solid bits of the 3 x 3 neighbourhood of a node: bit (dy+1)*3 + (dx+1)
 // is node (x+dx, y+dy); bit 4 is the node itself.
 __host__ __device__ constexpr int NBPOS(int dx, int dy) { return (dy + 1) * 3 + (dx + 1); }

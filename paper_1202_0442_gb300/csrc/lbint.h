@@ -160,6 +160,9 @@ struct ThermoArgs {
 // launchers (return the kernel count launched, or -1 on a launch error)
 int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s);
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
+// fluid and solute iteration in one kernel (one component, no interforce,
+// no intersolute, no exact momentum pairs, streaming kernel)
+int launch_fluid_solute(int storage, int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s);
 // neighbour codes of every node slot from the mask (after any mask upload)
 int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s);
 // persistent TMA-pipelined single-component kernel (k_tma.cu); err is a

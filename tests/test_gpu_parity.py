@@ -464,6 +464,27 @@ def test_reactive_growth_small(q):
 
 
 @pytest.mark.parametrize("q", [4, 9])
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_fused_fluid_solute_bitwise(q, storage):
+    """The fused fluid-solute kernel (the default with a solute) gives the
+    separate streaming and solute kernels' results bit for bit, growth
+    included."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3,
+                       growth_seed=7)
+    kw = {"h_max": 2e-2, "rounding": "stochastic"} if storage != "fp32" else {}
+    out = []
+    for kern in ("streaming", "fused"):
+        lt = lb2d.from_workload(w, storage, kernel=kern, thermo=50, **kw)
+        lt.iteration(400)
+        g, _, b = lt.solute_state()
+        out.append((lt.populations(1), lt.mask(), g, b, lt.get_thermo(), lt.launch_count()))
+    for a, b in zip(out[0][:4], out[1][:4]):
+        assert np.array_equal(a, b)
+    assert out[0][4] == out[1][4]
+    assert out[1][5] < out[0][5]  # one launch fewer per iteration
+
+
+@pytest.mark.parametrize("q", [4, 9])
 def test_growth_flips_each_step(q):
     """The growth decisions themselves (App. C, rules 3 and 5), step by
     step: the set of nodes turned solid in every iteration equals the
