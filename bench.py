@@ -48,10 +48,15 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the code (line comments and blank lines dropped) of the
+    sources the streaming kernel is compiled from."""
     h = hashlib.sha256()
     for name in ("k_fluid.cu", "lbcollide.cuh", "lbdev.cuh", "lbint.h", "lbsolute.cuh"):
-        with open(os.path.join(ROOT, "paper_1202_0442_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1202_0442_gb300", "csrc", name)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

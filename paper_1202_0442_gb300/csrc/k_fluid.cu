@@ -7,6 +7,11 @@
 //   adhesiveforce), equilibrium velocity by velocity shift and BGK
 //   collision with Eq. (2) -- all in one pass, one thread per node, nine
 //   loads and nine stores per component.
+// k_fluid_solute: k_fluid_local's node update followed, in the same
+//   thread, by the solute node update of lbsolute.cuh (solute command,
+//   Eq. (3); surface_reaction, App. C) with the solvent velocity of Eq. (4)
+//   taken from registers: one pass for single-component runs with a solute
+//   and no intersolute.
 // k_fluid_sc: the same plus interforce, which needs the densities of the
 //   eight neighbours after this step's streaming.  Each CTA pulls the
 //   populations of its tile and of a one-node ring around it, stages
@@ -18,11 +23,13 @@
 // slip_fix: the slip, mixed and hybrid boundary styles, applied after the
 //   bounce-back pull of either kernel.
 //
-// k_fluid_local reads each node's 3 x 3 solid neighbourhood as one 16-bit
+// k_nbcode: every node slot's neighbour code from the mask.
+//
+// The kernels read each node's 3 x 3 solid neighbourhood as one 16-bit
 // code (k_nbcode builds the codes from the mask once, k_apply_flips
 // refreshes them around nodes that grow solid): two bytes per node in place
-// of the mask-word arithmetic that otherwise dominates its instruction
-// count.
+// of the mask-word arithmetic that otherwise dominated the streaming
+// kernel's instruction count.
 #include "lbcollide.cuh"
 #include "lbsolute.cuh"
 

@@ -1,5 +1,8 @@
 // k_solute.cu -- solute lattice, precipitation and surface growth.
 //
+// The per-node solute update lives in lbsolute.cuh, shared with the fused
+// fluid-solute kernel of k_fluid.cu (the default for single-component runs
+// without intersolute); the kernels here run it on their own:
 // k_solute<Q>: one iteration of the solute populations g (solute command,
 //   Eq. (3); Q = 4 is the paper's D2Q4, Q = 9 the D2Q9 variant): pull
 //   streaming; at a solid source either bounce-back or the reactive rule of
