@@ -19,8 +19,9 @@ namespace {
 // One warp updates 32 consecutive nodes x0 .. x0+31 of row y (x0 a
 // multiple of 32): each lane's 3 x 3 solid neighbourhood from its
 // neighbour code, pull with half-way bounce-back by one load per
-// direction, BGK with the velocity shift.  Solid and padding lanes of a
-// warp that has fluid lanes store zeros, so the warp writes whole sectors.
+// direction, BGK with the velocity shift.  Solid and padding lanes store
+// zeros where their 32-byte sector holds a fluid lane, so the warp writes
+// whole sectors and leaves sectors without fluid alone.
 template <class S>
 __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *fout, int x, int y,
                                            uint32_t seed) {
@@ -32,7 +33,8 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
   const bool idle = (bits >> NBPOS(0, 0)) & 1u;
   const unsigned busy = __ballot_sync(0xffffffffu, !idle);
   if (idle) {
-    if (busy) {
+    constexpr int LPS = 32 / (int)sizeof(S);  // lanes per 32-byte sector
+    if ((busy >> (threadIdx.x & ~(LPS - 1))) & ((1u << LPS) - 1u)) {
 #pragma unroll
       for (int i = 0; i < 9; i++) Store<S>::st(fout, i * P + self, 0.0f, 1.0f);
     }

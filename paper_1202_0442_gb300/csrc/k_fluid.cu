@@ -131,13 +131,17 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
   constexpr bool FOLD = Store<S>::kScaled && !ME;
   const float linv = FOLD ? 1.0f : p.inv_scale;
   const Geometry &g = p.g;
-  // solid nodes (and the row padding past nx) hold no populations.  In a
-  // warp that also has fluid lanes they still store zeros, so the warp
-  // writes whole 32-byte sectors rather than partial ones.
+  // solid nodes (and the row padding past nx) hold no populations: their
+  // slots are zero from the start and k_apply_flips clears grown nodes.  A
+  // solid lane still stores zeros when its 32-byte sector holds a fluid
+  // lane, so every sector the warp writes is written whole (a partial
+  // sector costs the memory system a read-modify-write); sectors without a
+  // fluid lane are left alone.
   const bool idle = (bits >> NBPOS(0, 0)) & 1u;
   const unsigned busy = __ballot_sync(0xffffffffu, !idle);
   if (idle) {
-    if (busy) {
+    constexpr int LPS = 32 / (int)sizeof(S);  // lanes per 32-byte sector
+    if ((busy >> (threadIdx.x & ~(LPS - 1))) & ((1u << LPS) - 1u)) {
       const int self = y * g.pitch + x;
 #pragma unroll
       for (int c = 0; c < NC; c++) {

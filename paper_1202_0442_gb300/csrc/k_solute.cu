@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
 }
 
 // One CTA turns the listed nodes solid: mask bit, b = b0, their fluid and
-// solute mass booked as removed; then empties the list (the entries stay,
+// solute mass booked as removed, their populations cleared; then empties
+// the list (the entries stay,
 // their number moves to fcount[1] for the host to read).  Flips of one step
 // are independent of each other, so their order does not matter.
 template <class S>
@@ -149,10 +150,17 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
     atomicOr(a.mask + (size_t)y * g.mw + (x >> 5), 1u << (x & 31));
     a.b[self] = a.b0;
     for (int c = 0; c < a.nc; c++) {
-      const S *f = (const S *)a.f + (size_t)c * 9 * g.plane;
+      S *f = (S *)a.f + (size_t)c * 9 * g.plane;
+      S *fp = (S *)a.f_prev + (size_t)c * 9 * g.plane;
       float d = 0.f;
       for (int i = 0; i < 9; i++) d += Store<S>::ld(f, (size_t)i * g.plane + self, a.inv_scale);
       a.removed[(size_t)c * g.plane + self] += (double)a.rho_ref[c] + (double)d;
+      // a solid node holds no populations: its slots read zero in both
+      // buffers, as the fluid kernels leave solid sectors untouched
+      for (int i = 0; i < 9; i++) {
+        Store<S>::st(f, (size_t)i * g.plane + self, 0.0f, 1.0f);
+        Store<S>::st(fp, (size_t)i * g.plane + self, 0.0f, 1.0f);
+      }
     }
     if (a.gpop) {
       float m = 0.f;

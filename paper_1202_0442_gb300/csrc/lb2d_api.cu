@@ -652,6 +652,7 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.nopen = sa.nopen;
       for (int k = 0; k < sa.nopen; k++) ga2.op[k] = sa.op[k];
       ga2.f = ctx->fbuf[nxt];
+      ga2.f_prev = ctx->fbuf[ctx->cur];
       ga2.nc = ctx->nc;
       ga2.rho_ref[0] = (float)ctx->rho_ref[0];
       ga2.rho_ref[1] = (float)ctx->rho_ref[1];

@@ -135,7 +135,8 @@ struct GrowthArgs {
   int nopen;
   OpenDesc op[MAX_OPEN];
   // flip application
-  const void *f;          // fluid populations after the step [nc][9][plane]
+  void *f;                // fluid populations after the step [nc][9][plane]
+  void *f_prev;           // the other population buffer
   int nc;
   float rho_ref[2];
   float inv_scale;
