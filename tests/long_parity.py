@@ -11,6 +11,8 @@ pytest suites:
     python tests/long_parity.py report <dir>              # config 3 at 2048^2, GPU only
     python tests/long_parity.py fliplog <dir> [case ...]  # GPU: every step's growth flips
     python tests/long_parity.py firstflip <gpu_dir> <dir> [case ...]  # oracle side of it
+    python tests/long_parity.py owindows <dir> [case ...]  # oracle states + flips for windows
+    python tests/long_parity.py gwindows <odir> <dir> [case ...]  # GPU restarted in each window
 
 `gpu` runs the library (one lattice, or the batched launch for the batch
 case) and writes <dir>/<case>_<storage>.npz; `oracle` runs the oracle,
@@ -26,6 +28,15 @@ every growth trigger whose b lay within 1e-3 bmax of bmax, and the two lists
 are compared step by step up to the first step where they differ.  The
 report gives that step, the nodes in question, and the distance of their
 triggering neighbours from the threshold in the oracle's FP64 arithmetic.
+
+`owindows` / `gwindows` compare growth decisions along the whole run by
+restarting the GPU from the oracle's state: the oracle saves, at a few
+window starts, its state as the GPU stores it (population deviations and
+solute populations rounded to FP32, FP64 deposits, the mask) together
+with its flips and near-threshold decisions for the next WINDOW steps;
+the GPU restarts there (`lb_set_step`) and every step's flip set is
+compared until the first difference, which must sit at a decision within
+rounding of the threshold.  Nothing of the GPU run enters the oracle.
 """
 from __future__ import annotations
 
@@ -388,6 +399,109 @@ def run_firstflip(gdir, outdir, names):
             print(name, json.dumps(rep)[:2000], flush=True)
 
 
+WINDOW_STARTS = (10000, 25000, 40000)
+WINDOW = 1000
+
+
+def _owindows_one(args):
+    name, outdir = args
+    sys.path.insert(0, ROOT)
+    from oracle.drive import oracle_from_workload
+    make = CASES[name][0]
+    w = make()
+    o = oracle_from_workload(w)
+    o.set_margin_eps(1e-4, 1 << 16)
+    bmax = abs(w.reaction[3])
+    s = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    rho_ref = float(np.float32(w.rho_ref[0]))
+    t0 = time.time()
+    for ws in WINDOW_STARTS:
+        o.step(ws - o.t)
+        f = o.f(0)
+        solid = o.solid()
+        # the state as the library holds it: deviations from s_i rho_ref and
+        # the solute populations in FP32, the deposits in FP64
+        h32 = np.where(solid[None] != 0, 0.0, f - s * rho_ref).astype(np.float32)
+        g32 = o.g().astype(np.float32)
+        b = o.b()
+        ts, nodes, mt, mn, mv = [], [], [], [], []
+        for t in range(ws + 1, ws + WINDOW + 1):
+            o.step(1)
+            fl = o.flips()
+            ts.append(np.full(fl.size, t, np.int32))
+            nodes.append(fl.astype(np.int32))
+            idx, val = o.margin_events()
+            mt.append(np.full(idx.size, t, np.int32))
+            mn.append(idx.astype(np.int32))
+            mv.append(val / bmax)
+        np.savez_compressed(os.path.join(outdir, f"{name}_w{ws}.npz"), h32=h32, g32=g32, b=b,
+                            solid=solid.astype(np.uint8), t0=np.array(ws), ft=np.concatenate(ts),
+                            fn=np.concatenate(nodes), mt=np.concatenate(mt), mn=np.concatenate(mn),
+                            mv=np.concatenate(mv))
+        print(f"oracle {name}: window {ws} saved, {time.time() - t0:.0f} s", flush=True)
+    return name, time.time() - t0
+
+
+def run_owindows(outdir, names):
+    os.makedirs(outdir, exist_ok=True)
+    names = [n for n in names if n in REACTIVE] or list(REACTIVE)
+    with mp.get_context("spawn").Pool(len(names)) as pool:
+        for name, dt in pool.imap_unordered(_owindows_one, [(n, outdir) for n in names]):
+            print(f"oracle {name}: {dt:.0f} s", flush=True)
+
+
+def run_gwindows(odir, outdir, names):
+    import copy as _copy
+    import torch
+    from paper_1202_0442_gb300 import build, lb2d
+    build.build()
+    torch.cuda.set_device(0)
+    os.makedirs(outdir, exist_ok=True)
+    names = [n for n in names if n in REACTIVE] or list(REACTIVE)
+    report = {}
+    for name in names:
+        w = CASES[name][0]()
+        s = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+        rho_ref = float(np.float32(w.rho_ref[0]))
+        for ws in WINDOW_STARTS:
+            path = os.path.join(odir, f"{name}_w{ws}.npz")
+            if not os.path.exists(path):
+                continue
+            d = np.load(path)
+            ww = _copy.copy(w)
+            ww.solid = d["solid"]
+            lt = lb2d.from_workload(ww, "fp32", thermo=0, step=int(d["t0"]))
+            # f = h + s rho_ref in FP64: the library's FP64 subtraction gives h back exactly
+            lt.set_populations(np.where(d["solid"][None] != 0, 0.0, d["h32"].astype(np.float64) + s * rho_ref))
+            lt.set_solute_populations(d["g32"].astype(np.float64))
+            lt.set_precipitate(d["b"])
+            ft, fn, mt, mn, mv = d["ft"], d["fn"], d["mt"], d["mn"], d["mv"]
+            rep = {"compared": 0, "matched_flips": 0, "oracle_flips": int(fn.size), "first_diff": None}
+            for t in range(ws + 1, ws + WINDOW + 1):
+                lt.iteration(1)
+                fg = lt.flips()
+                fo = np.sort(fn[ft == t]).astype(np.int64)
+                rep["compared"] += 1
+                if np.array_equal(fg, fo):
+                    rep["matched_flips"] += int(fo.size)
+                    continue
+                margins = {int(n): float(v) for n, v in zip(mn[mt == t], mv[mt == t])}
+                diff = []
+                for n in np.setxor1d(fg, fo):
+                    y, x = divmod(int(n), w.nx)
+                    near = {m: margins[m] for m in ((yy % w.ny) * w.nx + (xx % w.nx)
+                                                    for yy in (y - 1, y, y + 1) for xx in (x - 1, x, x + 1))
+                            if m in margins}
+                    diff.append({"node": int(n), "in": "gpu" if n in set(fg.tolist()) else "oracle",
+                                 "near_triggers": near})
+                rep["first_diff"] = {"t": t, "diff": diff}
+                break
+            report[f"{name}@{ws}"] = rep
+            print(name, ws, json.dumps(rep)[:1500], flush=True)
+    with open(os.path.join(outdir, "windows.json"), "w") as fh:
+        json.dump(report, fh, indent=1)
+
+
 def run_report(outdir):
     """Config 3 at full size (2048^2, two components, 20000 iterations):
     component masses, their drift, and the pressures of the Laplace
@@ -445,6 +559,12 @@ def main(argv):
         return 0
     if mode == "firstflip":
         run_firstflip(argv[1], argv[2], argv[3:])
+        return 0
+    if mode == "gwindows":
+        run_gwindows(argv[1], argv[2], argv[3:])
+        return 0
+    if mode == "owindows":
+        run_owindows(argv[1], argv[2:])
         return 0
     names = argv[2:] or list(CASES)
     if mode == "fliplog":
