@@ -324,7 +324,7 @@ int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out);
  * a loop cannot afford an allocation or the device-wide synchronisation a
  * cudaFree may imply, or when a program forbids allocation after start-up.
  * The FP64 partial sums go to one fixed device array of the library (room
- * for 1024 blocks of partial sums, 131,200 bytes, kept by every GPU that
+ * for 1024 blocks of partial sums, 131,220 bytes, kept by every GPU that
  * loads the library until the process exits) instead of a buffer of the
  * context; the result is the same, bit for bit, as lb_get_thermo's.
  * Inputs: ctx (its fields, mask and deposits on the device); output: *out
@@ -345,7 +345,10 @@ int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out);
 int lb_get_fields(lb_ctx *ctx, int fluid, double *rho, double *px,
                   double *py, double *rho_eq);
 /* Total density and solvent velocity u = sum(j + F/2)/sum(rho) (Eq. (4))
- * of the last thermo evaluation as FP32 host [ny][nx] arrays. */
+ * of the last thermo evaluation as FP32 host [ny][nx] arrays (zero on
+ * solid nodes).  Page-locked outputs (cudaHostAlloc, or pinned torch
+ * tensors) are written by the export kernel directly; other host memory
+ * through a staging buffer and copies.  Synchronises the stream. */
 int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy);
 /* Current populations of fluid `fluid` (host [9][ny][nx] FP64). */
 int lb_get_populations(lb_ctx *ctx, int fluid, double *f);

@@ -1,6 +1,6 @@
 // k_misc.cu -- thermo reduction and state conversion kernels.
 //
-// k_thermo_partial / k_thermo_final: the thermo command's sums (mass,
+// k_thermo_partial: the thermo command's sums (mass,
 //   momentum j + F/2, equilibrium mass, solute, deposit, removed mass,
 //   node counts) over the state at the end of an iteration.  The first
 //   kernel gives every thread a fixed, strided set of nodes; a thread sums
@@ -10,9 +10,10 @@
 //   pass ALU-bound), counts nodes in integers and adds the FP64 arrays in
 //   FP64; the block then reduces in FP64 with warp shuffles and one
 //   shared-memory pass into a per-block slot of a scratch array, and the
-//   second kernel reduces the slots in a fixed tree.  The order of every
-//   addition is fixed by the launch shape, so the result is the same bits
-//   on every run.
+//   last block to finish (a counter) reduces the slots in a fixed tree and
+//   appends the flip count and the error word, so the host reads one
+//   record.  The order of every addition is fixed by the launch shape, so
+//   the result is the same bits on every run.
 // Conversions between FP64 arrays in the caller's layout ([q][ny][nx],
 // dense) and the library's storage (deviations from w_i rho_ref, pitched,
 // FP32/FP16/BF16), equilibrium initialisation from rho and u, and field
@@ -40,6 +41,28 @@ __device__ __forceinline__ void pair_add(float &hi, float &lo, float v) {
   hi = s;
 }
 
+// The final sums of the per-block slots: one warp per quantity, lanes
+// striding over the blocks in a fixed order (four independent chains, so
+// the loads overlap), then a shuffle tree.  L2 reads: other blocks wrote
+// the slots during this launch.
+__device__ __forceinline__ void thermo_final(const double *partials, int nblocks, double *out) {
+  const int lane = threadIdx.x & 31;
+  for (int q = threadIdx.x >> 5; q < NTHERMO; q += TB / 32) {
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int k = lane;
+    for (; k + 96 < nblocks; k += 128) {
+      v0 += __ldcg(partials + (size_t)k * NTHERMO + q);
+      v1 += __ldcg(partials + (size_t)(k + 32) * NTHERMO + q);
+      v2 += __ldcg(partials + (size_t)(k + 64) * NTHERMO + q);
+      v3 += __ldcg(partials + (size_t)(k + 96) * NTHERMO + q);
+    }
+    for (; k < nblocks; k += 32) v0 += __ldcg(partials + (size_t)k * NTHERMO + q);
+    double v = (v0 + v1) + (v2 + v3);
+    v = warp_sum(v);
+    if (lane == 0) out[q] = v;
+  }
+}
+
 // Block b handles rows b, b + gridDim.x, ...; its threads stride over x.
 // Quantities 0..8 come from FP32 planes and are summed per thread as FP32
 // pairs; 9..12 are FP64 arrays (reaction runs only); 13, 14 are counts.
@@ -54,6 +77,7 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
   const float *f0 = a.fields;
   const float *f1 = a.nc > 1 ? a.fields + (size_t)NFIELD * P : nullptr;
   for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+#pragma unroll 4
     for (int x = threadIdx.x; x < g.nx; x += TB) {
       const size_t self = (size_t)y * g.pitch + x;
       if (solid_at(a.mask, g.mw, x, y)) {
@@ -117,26 +141,20 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
     for (int k = 0; k < TB / 32; k++) s += sm[k][threadIdx.x];
     a.partials[(size_t)blockIdx.x * NTHERMO + threadIdx.x] = s;
   }
-}
-
-// one warp per quantity: lanes stride over the blocks' partial sums in a
-// fixed order (four independent chains, so the loads overlap), then a
-// shuffle tree
-__global__ void __launch_bounds__(32 * NTHERMO) k_thermo_final(const double *partials, int nblocks,
-                                                               double *out) {
-  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-  int k = lane;
-  for (; k + 96 < nblocks; k += 128) {
-    v0 += partials[(size_t)k * NTHERMO + q];
-    v1 += partials[(size_t)(k + 32) * NTHERMO + q];
-    v2 += partials[(size_t)(k + 64) * NTHERMO + q];
-    v3 += partials[(size_t)(k + 96) * NTHERMO + q];
+  // the last block to finish reduces every block's slot
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  thermo_final(a.partials, gridDim.x, a.out);
+  if (threadIdx.x == 0) {
+    *a.done = 0u;
+    reinterpret_cast<unsigned long long *>(a.out)[NTHERMO] = a.nflips ? *a.nflips : 0ull;
+    a.out[NTHERMO + 1] = a.errw ? (double)*a.errw : 0.0;
   }
-  for (; k < nblocks; k += 32) v0 += partials[(size_t)k * NTHERMO + q];
-  double v = (v0 + v1) + (v2 + v3);
-  v = warp_sum(v);
-  if (lane == 0) out[q] = v;
 }
 
 __device__ __forceinline__ bool node_of(int idx, const Geometry &g, int &x, int &y) {
@@ -288,9 +306,7 @@ int thermo_blocks(const Geometry &g) {
 
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {
   k_thermo_partial<<<nblocks, TB, 0, s>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return -1;
-  k_thermo_final<<<1, 32 * NTHERMO, 0, s>>>(a.partials, nblocks, a.out);
-  return cudaGetLastError() == cudaSuccess ? 2 : -1;
+  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,

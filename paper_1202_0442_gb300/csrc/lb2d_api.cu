@@ -108,11 +108,16 @@ struct lb_ctx {
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
   uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
+  // host copy of the device mask words while the two are known to agree
+  // (lost once growth may have changed the device mask)
+  std::vector<uint32_t> mask_host;
+  bool mask_host_valid = false;
   // caller-owned device buffers (lb_bind): f0, f1, g0, g1, fields, u
   void *bound[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t bound_bytes[6] = {0, 0, 0, 0, 0, 0};
   unsigned long long *nflips = nullptr;
   double *partials = nullptr, *tout = nullptr;
+  unsigned int *tdone = nullptr;  // thermo blocks finished (reset by the last)
   int tblocks = 0;
   int64_t t = 0;
   int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline
@@ -380,7 +385,8 @@ int commit(lb_ctx *ctx) {
   CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->tblocks = thermo_blocks(g);
   TRY(dalloc(ctx, &ctx->partials, (size_t)ctx->tblocks * NTHERMO));
-  TRY(dalloc(ctx, &ctx->tout, NTHERMO));
+  TRY(dalloc(ctx, &ctx->tout, NTHERMO + 2));
+  TRY(dalloc(ctx, &ctx->tdone, 1));
 
   // bit-packed mask
   std::vector<uint32_t> m((size_t)g.ny * g.mw, 0u);
@@ -389,6 +395,8 @@ int commit(lb_ctx *ctx) {
       if (ctx->solid[(size_t)y * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
   CK(cudaMemcpyAsync(ctx->mask, m.data(), m.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
   LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream));
+  ctx->mask_host = m;
+  ctx->mask_host_valid = true;
 
   // hybrid boundary style: per-node reflection coefficients (0 on fluid
   // nodes, so nodes that grow solid later are noslip)
@@ -522,14 +530,18 @@ int run_thermo(lb_ctx *ctx) {
   ta.removed = ctx->react ? ctx->removed : nullptr;
   ta.partials = ctx->partials;
   ta.out = ctx->tout;
+  ta.done = ctx->tdone;
+  ta.nflips = ctx->nflips;
+  ta.errw = ctx->errw;
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
-  double h[NTHERMO];
-  unsigned long long nfl = 0;
-  int errw = 0;
-  CK(cudaMemcpyAsync(h, ctx->tout, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&nfl, ctx->nflips, sizeof nfl, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&errw, ctx->errw, sizeof errw, cudaMemcpyDeviceToHost, ctx->stream));
+  // one record: the sums, the flip count (64 bits), the TMA error word
+  double rec[NTHERMO + 2];
+  CK(cudaMemcpyAsync(rec, ctx->tout, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  const double *h = rec;
+  unsigned long long nfl = 0;
+  memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
+  const int errw = (int)rec[NTHERMO + 1];
   if (errw) return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
   lb_thermo_t &T = ctx->thermo;
   memset(&T, 0, sizeof T);
@@ -559,6 +571,7 @@ int run_thermo(lb_ctx *ctx) {
 int one_step(lb_ctx *ctx, bool fields) {
   cudaStream_t s = ctx->stream;
   ctx->t += 1;
+  if (ctx->react) ctx->mask_host_valid = false;  // growth may change the device mask
   const int nxt = 1 - ctx->cur;
   FluidArgs fa = fluid_args(ctx, fields);
   // two components and Shan-Chen runs keep |f - w rho_ref| large: their
@@ -712,7 +725,7 @@ int lb_destroy(lb_ctx *ctx) {
   if (ctx->committed) cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->fbuf[0], ctx->fbuf[1], ctx->mask,     ctx->fields,   ctx->u,
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
-                  ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout,
+                  ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout, ctx->tdone,
                   ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
                   ctx->vstage,  ctx->nbc};
   for (void *p : ptrs) {
@@ -1341,17 +1354,38 @@ int lb_get_fields(lb_ctx *ctx, int fluid, double *rho, double *px, double *py, d
   return LB_OK;
 }
 
+// a host buffer the device addresses directly (page-locked, mapped, with the
+// same address on both sides), else nullptr
+static float *device_view(float *h) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (at.type == cudaMemoryTypeHost && at.devicePointer == (void *)h) ? h : nullptr;
+}
+
 int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy) {
   NEED_CTX();
   if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
   if (!rho || !ux || !uy) return ctx->fail(LB_E_ARG, "null output");
   TRY(set_device(ctx));
   const size_t nn = (size_t)ctx->nx * ctx->ny;
+  float rr[2] = {(float)ctx->rho_ref[0], (float)ctx->rho_ref[1]};
+  if (device_view(rho) && device_view(ux) && device_view(uy)) {
+    // page-locked outputs: the export kernel writes them over the host link
+    // itself, with no staging buffer and no separate copies
+    int n = launch_export_velocity(ctx->fields, ctx->nc, ctx->mask, ctx->g, rr, rho, ux, uy, ctx->stream);
+    cudaError_t e = n < 0 ? cudaGetLastError() : cudaSuccess;
+    if (n > 0) ctx->launches += n;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "velocity export");
+    return LB_OK;
+  }
   // a staging buffer kept for the context's life: an allocation per call
   // costs more than the copies
   if (!ctx->vstage) TRY(dalloc(ctx, &ctx->vstage, 3 * nn));
   float *st = ctx->vstage;
-  float rr[2] = {(float)ctx->rho_ref[0], (float)ctx->rho_ref[1]};
   int n = launch_export_velocity(ctx->fields, ctx->nc, ctx->mask, ctx->g, rr, st, st + nn, st + 2 * nn,
                                  ctx->stream);
   cudaError_t e = n < 0 ? cudaGetLastError() : cudaSuccess;
@@ -1574,13 +1608,25 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
   std::vector<std::pair<void *, size_t>> parts;
   snap_parts(ctx, parts);
   size_t off = sizeof h;
+  const uint8_t *mask_src = nullptr;
   for (auto &p : parts) {
-    CK(cudaMemcpyAsync(p.first, (const uint8_t *)host + off, p.second, cudaMemcpyHostToDevice, ctx->stream));
+    if (p.first == (void *)ctx->mask)
+      mask_src = (const uint8_t *)host + off;  // below, once the other copies are queued
+    else
+      CK(cudaMemcpyAsync(p.first, (const uint8_t *)host + off, p.second, cudaMemcpyHostToDevice, ctx->stream));
     off += p.second;
+  }
+  // the mask and its neighbour codes only when the snapshot's mask differs
+  // from the one on the device (compared on the host while the copies run)
+  const size_t mbytes = ctx->mask_host.size() * 4;
+  if (!(ctx->mask_host_valid && !memcmp(mask_src, ctx->mask_host.data(), mbytes))) {
+    CK(cudaMemcpyAsync(ctx->mask, mask_src, mbytes, cudaMemcpyHostToDevice, ctx->stream));
+    LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
+    memcpy(ctx->mask_host.data(), mask_src, mbytes);
+    ctx->mask_host_valid = true;
   }
   ctx->t = (int64_t)h.t;
   if (ctx->fcount) CK(cudaMemsetAsync(ctx->fcount, 0, 2 * sizeof(unsigned int), ctx->stream));
-  LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
   for (int c = 0; c < ctx->nc; c++) ctx->state_set[c] = true;
   if (ctx->qs) ctx->solute_set = true;
   return LB_OK;
@@ -2006,15 +2052,19 @@ int lb_batch_autotune(lb_batch *b, const char *cache_json) {
 namespace {
 
 // room for the per-block partial sums of up to STATIC_THERMO_BLOCKS blocks
-// plus the NTHERMO final sums: (1024 + 1) * 16 doubles = 131,200 bytes,
-// held by every GPU that loads the library until the process exits
+// plus the final record (NTHERMO sums, flip count, error word) and the
+// blocks-finished counter: (1024 + 1) * 16 + 2 doubles and 4 bytes =
+// 131,220 bytes, held by every GPU that loads the library until the
+// process exits
 constexpr int STATIC_THERMO_BLOCKS = 1024;
-static __device__ __align__(256) double g_thermo_scratch[(STATIC_THERMO_BLOCKS + 1) * NTHERMO];
+static __device__ __align__(256) double g_thermo_scratch[(STATIC_THERMO_BLOCKS + 1) * NTHERMO + 2];
+static __device__ unsigned int g_thermo_done;
 
 // device address of g_thermo_scratch per device, looked up once per device
 // (the host-side name of a __device__ array is not a device address)
 constexpr int STATIC_MAX_DEVICES = 64;
 double *g_thermo_scratch_dev[STATIC_MAX_DEVICES] = {};
+unsigned int *g_thermo_done_dev[STATIC_MAX_DEVICES] = {};
 std::mutex g_thermo_scratch_mu;
 
 }  // namespace
@@ -2031,16 +2081,20 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
                      ctx->tblocks, STATIC_THERMO_BLOCKS);
   TRY(set_device(ctx));
   double *scratch = nullptr;
+  unsigned int *done = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_thermo_scratch_mu);
     if (!g_thermo_scratch_dev[ctx->device]) {
       cudaError_t e = cudaGetSymbolAddress((void **)&g_thermo_scratch_dev[ctx->device], g_thermo_scratch);
+      if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&g_thermo_done_dev[ctx->device], g_thermo_done);
       if (e != cudaSuccess) {
         g_thermo_scratch_dev[ctx->device] = nullptr;
+        g_thermo_done_dev[ctx->device] = nullptr;
         return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_thermo_scratch)");
       }
     }
     scratch = g_thermo_scratch_dev[ctx->device];
+    done = g_thermo_done_dev[ctx->device];
   }
   // every slot the kernels read is written by the same call first, so the
   // contents a previous call left behind need no clearing
@@ -2054,12 +2108,15 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   ta.removed = ctx->react ? ctx->removed : nullptr;
   ta.partials = scratch;
   ta.out = scratch + (size_t)STATIC_THERMO_BLOCKS * NTHERMO;
+  ta.done = done;  // zero at load; the last block of every call resets it
+  ta.nflips = ctx->nflips;
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
-  double h[NTHERMO];
-  unsigned long long nfl = 0;
-  CK(cudaMemcpyAsync(h, ta.out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&nfl, ctx->nflips, sizeof nfl, cudaMemcpyDeviceToHost, ctx->stream));
+  double rec[NTHERMO + 2];
+  CK(cudaMemcpyAsync(rec, ta.out, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  const double *h = rec;
+  unsigned long long nfl = 0;
+  memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
   lb_thermo_t T;
   memset(&T, 0, sizeof T);
   T.step = ctx->thermo.step;

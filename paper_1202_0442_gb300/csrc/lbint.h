@@ -155,7 +155,12 @@ struct ThermoArgs {
   const double *b;        // or nullptr
   const double *removed;  // [nc + 1][plane] or nullptr
   double *partials;       // [nblocks][NTHERMO]
-  double *out;            // [NTHERMO]
+  double *out;            // [NTHERMO + 2]: the sums, then the flip count
+                          // (its 64 bits) and the TMA error word
+  unsigned int *done;     // blocks finished (0 between calls): the last
+                          // block reduces the partial sums
+  const unsigned long long *nflips;  // or nullptr
+  const int *errw;        // or nullptr
 };
 
 // launchers (return the kernel count launched, or -1 on a launch error)

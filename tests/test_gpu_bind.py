@@ -107,3 +107,29 @@ def test_bind_errors():
     lt.set_storage("fp32", [1.0], 0.0)
     with pytest.raises(lb2d.LBError):
         lt.set_equilibrium(np.ones((48, 64)), np.zeros((48, 64)), np.zeros((48, 64)), 1)
+
+
+def test_velocity_f32_paths():
+    """lb_get_velocity_f32 into page-locked buffers (the export kernel writes
+    them directly) and into ordinary host arrays (staging copy) gives the
+    same bits, and both equal rho = rho_ref + drho, u = p / rho formed in
+    FP32 from the node fields."""
+    w = synth.porous(100, 70, seed=5)
+    lt = lb2d.from_workload(w, "fp32", thermo=0)
+    lt.iteration(17)
+    plain = lt.velocity_f32()
+    pinned = tuple(torch.zeros((w.ny, w.nx), dtype=torch.float32).pin_memory() for _ in range(3))
+    lt.velocity_f32(pinned)
+    for a, b in zip(plain, pinned):
+        assert np.array_equal(a, b.numpy())
+    rho64, px, py, _ = lt.fields()
+    fl = w.solid == 0
+    # the fields hold rho - rho_ref in FP32; FP64 gives it back exactly
+    r0 = np.float32(w.rho_ref[0])
+    drho = (rho64 - float(r0)).astype(np.float32)
+    rho = np.where(fl, r0 + drho, np.float32(1))  # solid nodes: no division by 0
+    ux = px.astype(np.float32) / rho
+    uy = py.astype(np.float32) / rho
+    assert np.array_equal(np.where(fl, rho, 0), plain[0])
+    assert np.array_equal(np.where(fl, ux, 0), plain[1])
+    assert np.array_equal(np.where(fl, uy, 0), plain[2])
