@@ -64,9 +64,11 @@ __device__ __forceinline__ void thermo_final(const double *partials, int nblocks
 }
 
 // Block b handles rows b, b + gridDim.x, ...; its threads stride over x.
+// 64 registers keep 4 blocks per SM, so the 4 x 152 blocks of a large
+// lattice are resident at once.
 // Quantities 0..8 come from FP32 planes and are summed per thread as FP32
 // pairs; 9..12 are FP64 arrays (reaction runs only); 13, 14 are counts.
-__global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
+__global__ void __launch_bounds__(TB, 4) k_thermo_partial(const ThermoArgs a) {
   const Geometry &g = a.g;
   float hi[9], lo[9];
 #pragma unroll
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(TB) k_thermo_partial(const ThermoArgs a) {
   const float *f0 = a.fields;
   const float *f1 = a.nc > 1 ? a.fields + (size_t)NFIELD * P : nullptr;
   for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
-#pragma unroll 4
+#pragma unroll 2
     for (int x = threadIdx.x; x < g.nx; x += TB) {
       const size_t self = (size_t)y * g.pitch + x;
       if (solid_at(a.mask, g.mw, x, y)) {
