@@ -897,6 +897,39 @@ def test_full_size_reactive_1024x512():
     assert np.max(np.abs(Cg[fl] - o.solute_C()[fl])) < TOL32
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_full_size_batch256(storage):
+    """The 256-lattice batch as the benchmark runs it (autotuned tiles and
+    schedule, graph-captured launch; FP32 with exact momentum pairs, FP16
+    with stochastic rounding), 6 iterations; six lattices (the smallest, the
+    largest and four others) against the oracle one by one."""
+    ws = synth.batch()
+    kw = {"precise": True} if storage == "fp32" else {"h_max": 5e-3, "rounding": "stochastic"}
+    lats = [lb2d.from_workload(w, storage, **kw) for w in ws]
+    b = lb2d.Batch(lats)
+    b.autotune(None)
+    b.iteration(6, use_graph=True)
+    sizes = [w.nodes for w in ws]
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 37, 101, 173, 250})
+    # FP16: the populations carry h = f - w rho_ref in units of 2^-s, s the
+    # largest integer with h_max 2^s <= 2^14; six stochastic roundings stay
+    # within a few such units (these flows are far below h_max, so the
+    # relative measure of FP32 does not apply)
+    s_fp16 = 0
+    while 5e-3 * 2.0 ** (s_fp16 + 1) <= 2.0 ** 14:
+        s_fp16 += 1
+    for k in pick:
+        o = oracle_from_workload(ws[k])
+        o.step(6)
+        if storage == "fp32":
+            e, _ = pop_err(lats[k], o)
+            assert e < TOL32, (k, e)
+        else:
+            fl = (o.solid() == 0)[None]
+            err = float(np.max(np.where(fl, np.abs(lats[k].populations() - o.f(0)), 0.0)))
+            assert err < 8 * 2.0 ** -s_fp16, (k, err, 2.0 ** -s_fp16)
+
+
 def test_full_size_shan_chen_2048():
     w = synth.shan_chen2(2048)
     lt, o = run_pair(w, 2)
