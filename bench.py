@@ -524,6 +524,7 @@ def run_gb300(args, world, rank, local, dist):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_fluid_local", "kernel_ms": kernel_ms,
+                     "frac_of_nominal_8000_gbs": achieved / 8000.0,
                      "algorithmic_bytes_per_launch": alg_bytes},
         "copy_same_bytes": copy_ctx,
         "e2e": e2e,
