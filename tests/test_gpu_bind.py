@@ -133,3 +133,26 @@ def test_velocity_f32_paths():
     assert np.array_equal(np.where(fl, rho, 0), plain[0])
     assert np.array_equal(np.where(fl, ux, 0), plain[1])
     assert np.array_equal(np.where(fl, uy, 0), plain[2])
+
+
+def test_new_entry_point_errors():
+    """Argument and order errors of lb_set_step, lb_get_flips and the
+    fused kernel choice."""
+    w = synth.porous(64, 48, seed=2)
+    lt = lb2d.from_workload(w, "fp32")
+    with pytest.raises(lb2d.LBError):
+        lt.set_step(-1)
+    assert lt.flips().size == 0            # no surface reaction: nothing grows
+    lt.iteration(2)
+    assert lt.flips().size == 0
+    with pytest.raises(lb2d.LBError):
+        lt.set_kernel("bogus")
+    lt.set_kernel("fused")                 # no solute: the iteration refuses it
+    with pytest.raises(lb2d.LBError) as e:
+        lt.iteration(1)
+    assert "LB_E_UNSUPPORTED" in str(e.value)
+    lt.set_kernel("auto")
+    lt.iteration(1)
+    lt.set_step(1000)                      # the step count is the caller's to set
+    lt.iteration(1)
+    assert lt.get_thermo()["step"] == 1001
