@@ -12,15 +12,16 @@
  *     lb_last_error() gives the message of the last failure on a context.
  *   - Nodes are (x, y), 0 <= x < nx, 0 <= y < ny.  A paper script's
  *     lattice(N_x, N_y) has nx = N_x + 1, ny = N_y + 1 (lattice command:
- *     "sites are numbered from 0 to N_x").  Node arrays passed in or out
+ *     the sites run from 0 to N_x).  Node arrays passed in or out
  *     are dense row-major [ny][nx] (x fastest); population arrays are
  *     [q][ny][nx] with the D2Q9 numbering e0=(0,0) e1=(1,0) e2=(0,1)
  *     e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1) and the
  *     D2Q4 numbering g1..g4 = +x,+y,-x,-y at index 0..3.
  *   - Host pointers are borrowed for the duration of the call; the library
  *     copies what it needs.  Pinned host memory makes the copies faster
- *     but is not required.  All device memory is owned by the library and
- *     released by lb_destroy.
+ *     but is not required.  Device memory is owned by the library and
+ *     released by lb_destroy, except state buffers the caller supplies
+ *     with lb_bind (the caller's to free, after lb_destroy).
  *   - Calls on one context run on the CUDA stream given to lb_create, in
  *     order; calls that return host data synchronise that stream.  A
  *     context is not thread safe.
