@@ -679,6 +679,66 @@ def test_paper_poiseuille_script_commands():
     assert lt.get_thermo()["step"] == 600
 
 
+def test_paper_commands_circles_hybrid_solute():
+    """A lattice set up command by command as a paper script would: the
+    hybrid boundary style with a slip circle and a mixed (R = 0.4)
+    rectangle (obstacle command with styles), the populations and the
+    solute by position0 (rectangle and circle), momentum0 and
+    concentration0, a body force by aveforce's mode form; the oracle gets
+    the same state built here from the commands' definitions (integer
+    circle rule, momentum0 adding to populations, solute at rest
+    equilibrium), 150 iterations compared."""
+    nx, ny = 80, 60
+    lt = lb2d.Lattice()
+    lt.lattice(nx, ny, 0.8)
+    lt.solute(0.7, 4)
+    lt.set_storage("fp32", [24.0])
+    lt.boundary_style("hybrid")
+    lt.obstacle_circle_styled(50, 30, 8, "slip", 0.0)
+    lt.obstacle_rect_styled(10, 17, 40, 47, "mixed", 0.4)
+    lt.position0_rect(0, nx - 1, 0, ny - 1)
+    for m, v in enumerate([4, 4, 4, 4, 4, 1, 1, 1, 1]):
+        lt.momentum0(m, v)
+    lt.concentration0(0.5)
+    lt.position0_circle(25, 20, 6)
+    lt.momentum0(0, 0.2)
+    lt.concentration0(1.0)
+    lt.aveforce(1, 2e-5)
+    lt.thermo(50)
+    lt.iteration(150)
+
+    y, x = np.mgrid[0:ny, 0:nx]
+    circle = (x - 50) ** 2 + (y - 30) ** 2 <= 8 * 8
+    rect = (x >= 10) & (x <= 17) & (y >= 40) & (y <= 47)
+    solid = (circle | rect).astype(np.uint8)
+    assert np.array_equal(lt.mask(), solid)
+    bump = ((x - 25) ** 2 + (y - 20) ** 2 <= 36) & (solid == 0)
+    f = np.zeros((9, ny, nx))
+    f[0:5] = 4.0
+    f[5:9] = 1.0
+    f[0] += np.where(bump, 0.2, 0.0)
+    f = np.where(solid[None] != 0, 0.0, f)
+    C = np.where(solid != 0, 0.0, np.where(bump, 1.5, 0.5))
+    from oracle.orc import Oracle
+    o = Oracle(nx, ny, 1, 4)
+    o.set_solid(solid)
+    o.set_tau(0.8)
+    o.set_taus(0.7)
+    o.set_f(f)
+    o.set_solute_equilibrium(C)
+    o.set_slip(0.0, np.where(circle, 1.0, np.where(rect, 0.4, 0.0)))
+    o.set_aveforce(2e-5, 0.0)
+    o.step(150)
+    assert rel_u(lt, o) < TOL32
+    fl = solid == 0
+    _, Cg, _ = lt.solute_state(g=False, b=False)
+    assert np.max(np.abs(Cg[fl] - o.solute_C()[fl])) / np.max(o.solute_C()[fl]) < TOL32
+    # the script's populations (4, 4, 4, 4, 4, 1, 1, 1, 1) sit far from the
+    # rest weights (|f - w rho_ref| up to 6.7), so FP32 storage rounds at the
+    # 1e-7 level per value and the mass moves by about 5e-8 in 150 steps
+    assert abs(lt.get_thermo()["mass1"] - o.thermo()["mass1"]) / o.thermo()["mass1"] < 1e-6
+
+
 def test_thermo_every_nf():
     w = synth.channel(64, 32, 1.0, 1e-5)
     lt = lb2d.from_workload(w, thermo=7)
