@@ -314,6 +314,28 @@ def variants(args, local, stream, flush, value_fp32):
                    "rounding": "stochastic", "tolerance_met": "2e-3 (FP16) / 1e-2 (BF16) rel. u, parity tests",
                    "kernel_ms": float(np.median(t))}
         del lt
+    # the same recipe at 4096^2 (1.2 GB of FP32 state, far beyond L2, so
+    # back-to-back steps need no flush): where the memory system, not the
+    # launch, sets the time
+    peak = peaks()[0]
+    w4 = synth.porous(4096, 4096, seed=1)
+    big = {"workload": "porous 4096x4096 (same recipe, seed 1)", "l2": "state 1.2 GB > L2, steps back to back"}
+    for st, kw in (("fp32", {}), ("fp16", {"h_max": 2e-3, "rounding": "stochastic"})):
+        lt = lb2d.from_workload(w4, st, device=local, stream=stream.cuda_stream, **kw)
+        lt.thermo(1 << 30)
+        lt.iteration(5)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 50
+        a.record(stream)
+        lt.iteration(n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        big[st] = {"value": w4.nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                   "bytes_all_nodes_frac": BYTES_PER_FLUID_NODE[st] * w4.nodes / (ms * 1e-3) / 1e9 / peak}
+        del lt
+    big["fp16_speedup_vs_fp32"] = big["fp16"]["value"] / big["fp32"]["value"]
+    out["porous_4096"] = big
     # config 5: 256 periodic porous lattices, sides 64..512, one persistent
     # launch per iteration against one launch per lattice, FP32 and FP16
     ws = synth.batch()
