@@ -465,11 +465,12 @@ def test_reactive_growth_small(q):
 
 @pytest.mark.parametrize("q", [4, 9])
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
-def test_fused_fluid_solute_bitwise(q, storage):
+@pytest.mark.parametrize("size", [(128, 64), (100, 70)])
+def test_fused_fluid_solute_bitwise(q, storage, size):
     """The fused fluid-solute kernel (the default with a solute) gives the
     separate streaming and solute kernels' results bit for bit, growth
-    included."""
-    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3,
+    included; 100 x 70 leaves padding lanes past nx in every row."""
+    w = synth.reactive(size[0], size[1], seed=3, ndiscs=4, rmin=4, rmax=7, q=q, kr=0.02, bmax=0.3,
                        growth_seed=7)
     kw = {"h_max": 2e-2, "rounding": "stochastic"} if storage != "fp32" else {}
     out = []
