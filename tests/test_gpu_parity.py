@@ -464,6 +464,25 @@ def test_reactive_growth_small(q):
 
 
 @pytest.mark.parametrize("q", [4, 9])
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reactive_16bit_fluid_storage(q, storage):
+    """Config-4 recipe (128 x 64, reaction on, no growth yet) with the fluid
+    populations in 16-bit storage (stochastic rounding; the solute lattice
+    stays FP32): concentration and velocity within the 16-bit tolerance of
+    the FP64 oracle after 300 iterations (the fused kernel)."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=7, q=q, kr=2e-3, bmax=50.0,
+                       growth_seed=7, inlet="pressure")
+    tol = 2e-3 if storage == "fp16" else 1e-2
+    lt, o = run_pair(w, 300, storage=storage, h_max=4e-3, rounding="stochastic")
+    assert (lt.mask() == w.solid).all() and (o.solid() == w.solid).all()
+    fl = w.solid == 0
+    _, Cg, _ = lt.solute_state(g=False, b=False)
+    Co = o.solute_C()
+    assert np.max(np.abs(Cg[fl] - Co[fl])) / np.max(Co[fl]) < tol
+    assert rel_u(lt, o) < tol
+
+
+@pytest.mark.parametrize("q", [4, 9])
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 @pytest.mark.parametrize("size", [(128, 64), (100, 70)])
 def test_fused_fluid_solute_bitwise(q, storage, size):
