@@ -482,6 +482,23 @@ def test_reactive_16bit_fluid_storage(q, storage):
     assert rel_u(lt, o) < tol
 
 
+@pytest.mark.parametrize("R", [1.0, 0.4])
+def test_reactive_with_slip_walls(R):
+    """The reactive recipe under the slip (R = 1) and mixed (R = 0.4)
+    boundary styles: the fluid slips along the walls and discs, the solute
+    keeps its bounce-back/reaction links; 200 iterations of the fused
+    kernel against the oracle."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=7, q=9, kr=2e-3, bmax=50.0,
+                       growth_seed=7, inlet="pressure")
+    w.slip = (R,)
+    lt, o = run_pair(w, 200)
+    fl = w.solid == 0
+    _, Cg, _ = lt.solute_state(g=False, b=False)
+    Co = o.solute_C()
+    assert np.max(np.abs(Cg[fl] - Co[fl])) / np.max(Co[fl]) < TOL32
+    assert rel_u(lt, o) < TOL32
+
+
 @pytest.mark.parametrize("q", [4, 9])
 @pytest.mark.parametrize("storage", ["fp32", "fp16"])
 @pytest.mark.parametrize("size", [(128, 64), (100, 70)])
