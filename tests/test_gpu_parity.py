@@ -274,6 +274,32 @@ def test_two_components_without_interforce():
     assert rel_u(lt, o) < TOL32
 
 
+@pytest.mark.parametrize("q", [4, 9])
+@pytest.mark.parametrize("G", [0.0, 0.9])
+def test_two_components_carry_a_solute(q, G):
+    """A solute advected by a two-component fluid (separate fluid and
+    solute kernels, mass-exact collision, with or without interforce): the
+    solvent velocity of Eq. (4) is the mixture's sum(j + F/2)/sum(rho)."""
+    nx, ny = 48, 32
+    mask = synth.random_mask(nx, ny, 4, 0.1)
+    y, x = np.mgrid[0:ny, 0:nx]
+    blob = (x - 20) ** 2 + (y - 14) ** 2 < 64
+    w = synth.Workload(name="2cs", nx=nx, ny=ny, solid=mask,
+                       rho=[np.where(mask, 0, np.where(blob, 1.0, 0.05)), np.where(mask, 0, np.where(blob, 0.05, 1.0))],
+                       tau=(0.8, 1.1), alpha=(4 / 9, 4 / 9), aveforce=((2e-5, 0.0), (2e-5, 0.0)),
+                       interforce=(G, 0.0, 0.0) if G else None, rho_ref=(0.5, 0.5),
+                       solute_q=q, taus=0.7, C=np.where(mask, 0, synth.noise_field(nx, ny, 6, 0.5, 1.5)))
+    lt, o = run_pair(w, 120)
+    for c in (1, 2):
+        assert rel_rho(lt, o, w, comp=c) < TOL32
+    fl = mask == 0
+    _, Cg, _ = lt.solute_state(g=False, b=False)
+    Co = o.solute_C()
+    assert np.max(np.abs(Cg[fl] - Co[fl])) / np.max(Co[fl]) < TOL32
+    errs, _, _ = thermo_err(lt, o, ["solute"])
+    assert errs["solute"] < 1e-6
+
+
 @pytest.mark.parametrize("taus,alphas,G,init", [((0.626, 2.5), (4 / 9, 0.8), 0.0, "step"),
                                                  ((1.0, 1.0), (0.0, 0.998), 0.0, "wave"),
                                                  ((1.0, 1.0), (4 / 9, 0.8), 1.0, "step")])
