@@ -329,9 +329,15 @@ int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out);
  * loads the library until the process exits) instead of a buffer of the
  * context; the result is the same, bit for bit, as lb_get_thermo's.
  * Inputs: ctx (its fields, mask and deposits on the device); output: *out
- * (host).  Returns LB_E_ARG if the lattice would need more than 1024
- * blocks of partial sums, LB_E_ORDER before the first lb_iteration, and
- * synchronises ctx's stream.  The first call on a device looks up the
+ * (host).  The thermo kernel takes one block per lattice row, at most four
+ * per SM, so the array serves every lattice on GPUs of up to 256 SMs;
+ * a lattice that would need more than 1024 blocks gets LB_E_ARG.  Returns
+ * LB_E_ORDER unless the last iteration executed ended with a thermo step
+ * and no state was replaced since (lb_set_populations, lb_set_equilibrium,
+ * lb_set_solute_*, lb_set_precipitate, lb_load_state, lb_set_step): the
+ * field planes then describe the live mask and deposits the kernel also
+ * reads.  Returns LB_E_TIMEOUT, like lb_iteration, if a TMA pipeline wait
+ * gave up.  Synchronises ctx's stream.  The first call on a device looks up the
  * array's device address (once per device, with that device current);
  * make that first call before any stream capture.  All calls share the
  * one array: calls whose kernels overlap on a GPU (different streams,

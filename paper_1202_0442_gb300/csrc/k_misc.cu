@@ -64,11 +64,11 @@ __device__ __forceinline__ void thermo_final(const double *partials, int nblocks
 }
 
 // Block b handles rows b, b + gridDim.x, ...; its threads stride over x.
-// 64 registers keep 4 blocks per SM, so the 4 x 152 blocks of a large
-// lattice are resident at once.
+// 64 registers keep THERMO_BLOCKS_PER_SM blocks per SM, so a grid of that
+// many blocks per SM is resident at once.
 // Quantities 0..8 come from FP32 planes and are summed per thread as FP32
 // pairs; 9..12 are FP64 arrays (reaction runs only); 13, 14 are counts.
-__global__ void __launch_bounds__(TB, 4) k_thermo_partial(const ThermoArgs a) {
+__global__ void __launch_bounds__(TB, THERMO_BLOCKS_PER_SM) k_thermo_partial(const ThermoArgs a) {
   const Geometry &g = a.g;
   float hi[9], lo[9];
 #pragma unroll
@@ -299,10 +299,11 @@ inline int ok() { return cudaGetLastError() == cudaSuccess ? 1 : -1; }
 
 }  // namespace
 
-int thermo_blocks(const Geometry &g) {
-  // one block per row, at most 4 per SM of a 152-SM GB300
+int thermo_blocks(const Geometry &g, int sms) {
+  // one block per row, at most THERMO_BLOCKS_PER_SM per SM (all resident)
   int b = g.ny;
-  if (b > 4 * 152) b = 4 * 152;
+  const int cap = THERMO_BLOCKS_PER_SM * (sms > 0 ? sms : 1);
+  if (b > cap) b = cap;
   return b < 1 ? 1 : b;
 }
 

@@ -124,6 +124,7 @@ struct lb_ctx {
   int *errw = nullptr;   // device error word of the TMA kernel
   int sms = 0;
   bool fields_valid = false;
+  int64_t fields_step = -1;  // iteration whose end state the field planes hold
   lb_thermo_t thermo{};
   bool thermo_valid = false;
 
@@ -383,7 +384,7 @@ int commit(lb_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->nflips, 1));
   TRY(dalloc(ctx, &ctx->errw, 1));
   CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
-  ctx->tblocks = thermo_blocks(g);
+  ctx->tblocks = thermo_blocks(g, ctx->sms);
   TRY(dalloc(ctx, &ctx->partials, (size_t)ctx->tblocks * NTHERMO));
   TRY(dalloc(ctx, &ctx->tout, NTHERMO + 2));
   TRY(dalloc(ctx, &ctx->tdone, 1));
@@ -1145,6 +1146,7 @@ int lb_concentration0(lb_ctx *ctx, double value) {
 
 int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho, const double *ux, const double *uy) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   if (!fluid_ok(ctx, fluid) || !rho) return ctx->fail(LB_E_ARG, "bad fluid or null rho");
   const size_t nn = (size_t)ctx->nx * ctx->ny;
@@ -1168,6 +1170,7 @@ int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho, const double *
 
 int lb_set_solute_equilibrium(lb_ctx *ctx, const double *C, const double *ux, const double *uy) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
   if (!C) return ctx->fail(LB_E_ARG, "null C");
   ctx->painted_C = false;
@@ -1185,6 +1188,7 @@ int lb_set_solute_equilibrium(lb_ctx *ctx, const double *C, const double *ux, co
 
 int lb_set_populations(lb_ctx *ctx, int fluid, const double *f) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   if (!fluid_ok(ctx, fluid) || !f) return ctx->fail(LB_E_ARG, "bad fluid or null array");
   if (!ctx->committed) ctx->painted_f[fluid - 1] = false;
@@ -1203,6 +1207,7 @@ int lb_set_populations(lb_ctx *ctx, int fluid, const double *f) {
 
 int lb_set_solute_populations(lb_ctx *ctx, const double *g) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
   if (!g) return ctx->fail(LB_E_ARG, "null array");
   ctx->painted_C = false;
@@ -1219,6 +1224,7 @@ int lb_set_solute_populations(lb_ctx *ctx, const double *g) {
 
 int lb_set_precipitate(lb_ctx *ctx, const double *b) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!b) return ctx->fail(LB_E_ARG, "null array");
   TRY(commit(ctx));
   Stage st;
@@ -1323,6 +1329,7 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
     TRY(one_step(ctx, thermo));
     if (thermo) {
       ctx->fields_valid = true;
+      ctx->fields_step = ctx->t;
       TRY(run_thermo(ctx));
     }
   }
@@ -1596,6 +1603,7 @@ int lb_save_state(lb_ctx *ctx, void *host, size_t bytes) {
 
 int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
   NEED_CTX();
+  ctx->fields_step = -1;  // the live state no longer matches the field planes
   size_t need = 0;
   TRY(lb_state_size(ctx, &need));
   if (!host || bytes != need) return ctx->fail(LB_E_ARG, "snapshot must be %zu bytes", need);
@@ -2055,8 +2063,10 @@ namespace {
 // plus the final record (NTHERMO sums, flip count, error word) and the
 // blocks-finished counter: (1024 + 1) * 16 + 2 doubles and 4 bytes =
 // 131,220 bytes, held by every GPU that loads the library until the
-// process exits
+// process exits.  The thermo grid has at most THERMO_BLOCKS_PER_SM blocks
+// per SM, so 1024 blocks cover GPUs of up to 256 SMs.
 constexpr int STATIC_THERMO_BLOCKS = 1024;
+static_assert(STATIC_THERMO_BLOCKS >= THERMO_BLOCKS_PER_SM * 256, "static thermo scratch below 256 SMs");
 static __device__ __align__(256) double g_thermo_scratch[(STATIC_THERMO_BLOCKS + 1) * NTHERMO + 2];
 static __device__ unsigned int g_thermo_done;
 
@@ -2072,7 +2082,14 @@ std::mutex g_thermo_scratch_mu;
 extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   NEED_CTX();
   if (!out) return ctx->fail(LB_E_ARG, "null output");
-  if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+  if (!ctx->fields_valid || !ctx->thermo_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
+  // the field planes must describe the live state: written by the last
+  // iteration executed, with no state replaced and no step count set since
+  // (mask, deposits and removed mass are read live)
+  if (ctx->fields_step != ctx->t)
+    return ctx->fail(LB_E_ORDER, "the node fields are not those of the current state (step %lld): the "
+                     "record can be recomputed only after an iteration whose last step is a thermo step",
+                     (long long)ctx->t);
   if (ctx->device < 0 || ctx->device >= STATIC_MAX_DEVICES)
     return ctx->fail(LB_E_UNSUPPORTED, "device %d is beyond the %d devices the static scratch serves",
                      ctx->device, STATIC_MAX_DEVICES);
@@ -2110,6 +2127,7 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   ta.out = scratch + (size_t)STATIC_THERMO_BLOCKS * NTHERMO;
   ta.done = done;  // zero at load; the last block of every call resets it
   ta.nflips = ctx->nflips;
+  ta.errw = ctx->errw;
   LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
   double rec[NTHERMO + 2];
   CK(cudaMemcpyAsync(rec, ta.out, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
@@ -2117,9 +2135,11 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   const double *h = rec;
   unsigned long long nfl = 0;
   memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
+  if ((int)rec[NTHERMO + 1])
+    return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
   lb_thermo_t T;
   memset(&T, 0, sizeof T);
-  T.step = ctx->thermo.step;
+  T.step = ctx->t;
   T.nsolid = (int64_t)llround(h[13]);
   T.nfluid = (int64_t)llround(h[14]);
   for (int c = 0; c < ctx->nc; c++) {

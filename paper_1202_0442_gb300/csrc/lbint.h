@@ -179,7 +179,9 @@ int launch_fluid_tma(int storage, const FluidArgs &a, int *err, cudaStream_t s, 
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
 int launch_growth(const GrowthArgs &a, cudaStream_t s);
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);
-int thermo_blocks(const Geometry &g);
+// thermo grid: one block per row, at most THERMO_BLOCKS_PER_SM per SM
+constexpr int THERMO_BLOCKS_PER_SM = 4;
+int thermo_blocks(const Geometry &g, int sms);
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s);
 
 // state conversion between FP64 host-layout arrays [q][ny][nx] and storage

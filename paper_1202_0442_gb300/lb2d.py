@@ -441,18 +441,11 @@ class Lattice:
         self._ck(self._L.lb_launch_count(self._h, C.byref(n)))
         return int(n.value)
 
-    # -- convenience -----------------------------------------------------------
     def velocity(self):
-        """Solvent velocity of Eq. (4) from the FP64 field export."""
-        rs = np.zeros((self.ny, self.nx))
-        pxs, pys = np.zeros_like(rs), np.zeros_like(rs)
-        for s in range(1, self.ncomp + 1):
-            r, px, py, _ = self.fields(s)
-            rs += r
-            pxs += px
-            pys += py
-        safe = np.where(rs > 0, rs, 1.0)
-        return np.where(rs > 0, pxs / safe, 0.0), np.where(rs > 0, pys / safe, 0.0)
+        """Solvent velocity of Eq. (4) as the library computes it
+        (lb_get_velocity_f32), as float64 arrays [ny][nx]."""
+        _, ux, uy = self.velocity_f32()
+        return ux.astype(np.float64), uy.astype(np.float64)
 
 
 def _buffer(buf):

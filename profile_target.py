@@ -1,9 +1,9 @@
 """A small, self-contained run of one kernel for ncu captures.
 
-    python -m paper_1202_0442_gb300.profile_target porous4096 fp32
-    python -m paper_1202_0442_gb300.profile_target shanchen2048 fp32
-    python -m paper_1202_0442_gb300.profile_target reactive fp32
-    python -m paper_1202_0442_gb300.profile_target batch256 fp32
+    python profile_target.py porous4096 fp32
+    python profile_target.py shanchen2048 fp32
+    python profile_target.py reactive fp32
+    python profile_target.py batch256 fp32
 
 Sets up the named workload on cuda:0, runs a fixed number of iterations
 (thermo off, so every launch is the same kernel sequence) and exits 0.
@@ -13,7 +13,12 @@ few GB.
 """
 from __future__ import annotations
 
+import os
 import sys
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def main(argv=None) -> int:
@@ -23,7 +28,7 @@ def main(argv=None) -> int:
     iters = int(argv[2]) if len(argv) > 2 else 8
     import torch
 
-    from . import build, lb2d, synth
+    from paper_1202_0442_gb300 import build, lb2d, synth
     build.build()
     torch.cuda.set_device(0)
     if name == "porous4096":

@@ -9,8 +9,6 @@ pytest suites:
     python tests/long_parity.py oracle <dir> [case ...]   # on CPU cores
     python tests/long_parity.py compare <gpu_dir> <oracle_dir>
     python tests/long_parity.py report <dir>              # config 3 at 2048^2, GPU only
-    python tests/long_parity.py fliplog <dir> [case ...]  # GPU: every step's growth flips
-    python tests/long_parity.py firstflip <gpu_dir> <dir> [case ...]  # oracle side of it
     python tests/long_parity.py owindows <dir> [case ...]  # oracle states + flips for windows
     python tests/long_parity.py gwindows <odir> <dir> [case ...]  # GPU restarted in each window
 
@@ -20,14 +18,6 @@ one process per case, and writes <dir>/<case>.npz; `compare` prints one
 markdown table row per (case, storage): relative errors in rho and u,
 masks, mass drift of both sides, and the case's own physics numbers.
 No value produced here is stored as an expected value anywhere.
-
-`fliplog` and `firstflip` locate where the growth decisions of a reactive
-case part: the GPU writes the list of nodes turned solid at every step,
-the oracle runs on its own (nothing of the GPU run goes into it) recording
-every growth trigger whose b lay within 1e-3 bmax of bmax, and the two lists
-are compared step by step up to the first step where they differ.  The
-report gives that step, the nodes in question, and the distance of their
-triggering neighbours from the threshold in the oracle's FP64 arithmetic.
 
 `owindows` / `gwindows` compare growth decisions along the whole run by
 restarting the GPU from the oracle's state: the oracle saves, at a few
@@ -312,93 +302,6 @@ def compare(gdir, odir):
 REACTIVE = ("reactive_q4", "reactive_q9")
 
 
-def run_fliplog(outdir, names):
-    import torch
-    from paper_1202_0442_gb300 import build, lb2d
-    build.build()
-    torch.cuda.set_device(0)
-    os.makedirs(outdir, exist_ok=True)
-    for name in names:
-        make, steps, _, _ = CASES[name]
-        w = make()
-        lt = lb2d.from_workload(w, "fp32", thermo=0)
-        t0 = time.time()
-        ts, nodes = [], []
-        for t in range(1, steps + 1):
-            lt.iteration(1)
-            f = lt.flips()
-            ts.append(np.full(f.size, t, np.int32))
-            nodes.append(f.astype(np.int32))
-        np.savez_compressed(os.path.join(outdir, f"{name}_fliplog.npz"),
-                            t=np.concatenate(ts), node=np.concatenate(nodes), steps=np.array(steps))
-        print(f"{name}: {sum(x.size for x in nodes)} flips in {steps} steps, {time.time() - t0:.1f} s",
-              flush=True)
-
-
-def _neighbours(n, nx, ny):
-    y, x = divmod(int(n), nx)
-    out = []
-    for dx in (-1, 0, 1):
-        for dy in (-1, 0, 1):
-            if (dx or dy) and 0 <= x + dx < nx and 0 <= y + dy < ny:
-                out.append((y + dy) * nx + x + dx)
-    return out
-
-
-def _firstflip_one(args):
-    name, gdir, outdir = args
-    sys.path.insert(0, ROOT)
-    from oracle.drive import oracle_from_workload
-    make, _, _, _ = CASES[name]
-    w = make()
-    log = np.load(os.path.join(gdir, f"{name}_fliplog.npz"))
-    gt, gn, steps = log["t"], log["node"], int(log["steps"])
-    order = np.argsort(gt, kind="stable")
-    gt, gn = gt[order], gn[order]
-    starts = np.searchsorted(gt, np.arange(1, steps + 2))
-    o = oracle_from_workload(w)
-    eps = 1e-3
-    o.set_margin_eps(eps, 1 << 16)
-    bmax = abs(w.reaction[3])
-    t0 = time.time()
-    near = []          # |b - bmax| / bmax of near-threshold triggers seen so far
-    agreed = 0
-    rep = {"case": name, "steps": steps, "first_diff": None}
-    for t in range(1, steps + 1):
-        o.step(1)
-        fo = o.flips()
-        fg = np.sort(gn[starts[t - 1]:starts[t]]).astype(np.int64)
-        idx, val = o.margin_events()
-        if np.array_equal(fo, fg):
-            agreed += fo.size
-            near.extend((np.abs(val) / bmax).tolist())
-            continue
-        margin = {int(i): float(v) / bmax for i, v in zip(idx, val)}
-        diff = []
-        for n in np.setxor1d(fo, fg):
-            trig = {m: margin[m] for m in _neighbours(n, w.nx, w.ny) if m in margin}
-            diff.append({"node": int(n), "xy": [int(n) % w.nx, int(n) // w.nx],
-                         "in": "oracle" if n in set(fo.tolist()) else "gpu",
-                         "near_triggers": trig})
-        rep.update({"first_diff": t, "diff": diff})
-        break
-    near = np.array(near) if near else np.zeros(1)
-    rep.update({"agreed_flips": int(agreed), "near_events_agreed": int((near > 0).sum()),
-                "min_margin_agreed": float(near[near > 0].min()) if (near > 0).any() else None,
-                "seconds": time.time() - t0})
-    with open(os.path.join(outdir, f"{name}_firstflip.json"), "w") as fh:
-        json.dump(rep, fh, indent=1)
-    return name, rep
-
-
-def run_firstflip(gdir, outdir, names):
-    os.makedirs(outdir, exist_ok=True)
-    names = [n for n in names if n in REACTIVE] or list(REACTIVE)
-    with mp.get_context("spawn").Pool(len(names)) as pool:
-        for name, rep in pool.imap_unordered(_firstflip_one, [(n, gdir, outdir) for n in names]):
-            print(name, json.dumps(rep)[:2000], flush=True)
-
-
 WINDOW_STARTS = (10000, 25000, 40000)
 WINDOW = 1000
 
@@ -557,9 +460,6 @@ def main(argv):
     if mode == "report":
         run_report(argv[1])
         return 0
-    if mode == "firstflip":
-        run_firstflip(argv[1], argv[2], argv[3:])
-        return 0
     if mode == "gwindows":
         run_gwindows(argv[1], argv[2], argv[3:])
         return 0
@@ -567,9 +467,7 @@ def main(argv):
         run_owindows(argv[1], argv[2:])
         return 0
     names = argv[2:] or list(CASES)
-    if mode == "fliplog":
-        run_fliplog(argv[1], [n for n in names if n in REACTIVE] or list(REACTIVE))
-    elif mode == "gpu":
+    if mode == "gpu":
         run_gpu(argv[1], names)
     elif mode == "oracle":
         run_oracle(argv[1], names)

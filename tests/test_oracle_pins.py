@@ -1065,6 +1065,42 @@ def test_growth_single_trigger():
     assert np.isclose(th["solute"] + th["removed_solute"], g_before.sum(), rtol=1e-13)
 
 
+def _splitmix64_py(x: int) -> int:
+    """SplitMix64's output function (Steele, Lea and Flood 2014), written
+    here from the published definition, apart from the oracle's C code."""
+    m = (1 << 64) - 1
+    z = (x + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def test_growth_pick_hand_computed():
+    """Which neighbour a trigger turns solid (surface_reaction command,
+    App. C rules 3 and 5, reading R9): on the 5 x 5 lattice the trigger is
+    node 12 = (2, 2), its fluid 4-neighbours in the order +x, +y, -x, -y are
+    nodes 13, 17, 11, 7, and in the first iteration (t = 1) the key is
+    seed ^ (t nx ny + node) = seed ^ 37.
+      seed 12: SplitMix64(12 ^ 37 = 41) = 0x118e846ea93bc949, mod 4 = 1 -> +y, node 17
+      seed 13: SplitMix64(13 ^ 37 = 40) = 0x369eae0b0ca19112, mod 4 = 2 -> -x, node 11
+    A 0-based t (key seed ^ 12) would pick index 3 (node 7) and 1 (node 17),
+    and the orders (+x, -x, +y, -y) or (-y, -x, +y, +x) other nodes, so
+    each of those mistakes fails here."""
+    assert _splitmix64_py(0) == 0xE220A8397B1DCDAF   # the published first output
+    cases = {12: (0x118E846EA93BC949, 17), 13: (0x369EAE0B0CA19112, 11)}
+    for seed, (hval, node) in cases.items():
+        assert _splitmix64_py(seed ^ 37) == hval
+        assert [13, 17, 11, 7][hval % 4] == node
+        # the case tells the plausible variants apart
+        assert [13, 17, 11, 7][_splitmix64_py(seed ^ 12) % 4] != node
+        assert [13, 11, 17, 7][hval % 4] != node
+        assert [7, 11, 17, 13][hval % 4] != node
+        o, _ = _growth_case(seed)
+        o.step()
+        assert [int(v) for v in o.flips()] == [node]
+        assert o.solid()[node // 5, node % 5] == 1
+
+
 def test_growth_margin_records():
     """The oracle's own record of growth decisions taken near the threshold
     (used to place a GPU/oracle difference in growth): a trigger whose b is

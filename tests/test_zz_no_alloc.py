@@ -51,3 +51,29 @@ def test_static_thermo_equals_allocating_thermo(case):
         _same(first, ref)
         _same(second, ref)
         assert first["nfluid"] + first["nsolid"] == w.nodes
+
+
+def test_static_thermo_refuses_fields_of_another_state():
+    """With thermo every 7 iterations, a run that stops between thermo steps
+    leaves field planes of an earlier step while the mask and deposits move
+    on: the call must refuse rather than mix the two.  So must it after a
+    snapshot round trip, until an iteration ends with a thermo step."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=9, kr=0.02, bmax=0.3)
+    lt = lb2d.from_workload(w, thermo=7)
+    lt.iteration(17)                        # thermo at 7 and 14, not at 17
+    with pytest.raises(lb2d.LBError) as e:
+        lt.thermo_static()
+    assert e.value.code == lb2d.LB_E_ORDER
+    lt.iteration(4)                         # 21: a thermo step
+    _same(lt.thermo_static(), lt.get_thermo())
+    buf = np.zeros(lt.state_size(), np.uint8)
+    lt.save_state(buf)
+    lt.load_state(buf)
+    with pytest.raises(lb2d.LBError) as e:
+        lt.thermo_static()
+    assert e.value.code == lb2d.LB_E_ORDER
+    lt.iteration(7)                         # 28: a thermo step again
+    ref = lt.get_thermo()
+    assert ref["step"] == 28
+    for _ in range(2):
+        _same(lt.thermo_static(), ref)
