@@ -111,10 +111,68 @@ int lb_launch_count(const lb_ctx *ctx, uint64_t *out);
  * component's planes with 32-bit offsets). */
 int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau);
 
-/* processors command: accepted after lb_lattice and ignored (one GPU runs
- * the whole lattice, like the serial module); before lb_lattice it fails
- * with LB_E_ORDER as in the paper. */
+/* processors command (Sec. Commands, processors; Sec. Parallelization): the
+ * px x py grid of processes the lattice is split over.  After lb_lattice
+ * (LB_E_ORDER before it, as in the paper) and before the first iteration.
+ * On its own it changes nothing: the context still holds the whole lattice.
+ * With lb_processor_rank the context holds one piece of it; pieces are y
+ * slabs, so px must be 1. */
 int lb_processors(lb_ctx *ctx, int px, int py);
+
+/* Make the context hold slab `rank` (0 <= rank < py) of a lattice split by
+ * lb_processors(ctx, 1, py) into py y slabs: lattice rows [y0, y0 + n),
+ * y0 = floor(rank ny / py), n = floor((rank + 1) ny / py) - y0, plus `halo`
+ * ghost rows on each side (1; 2 with interforce or a slip, mixed or hybrid
+ * boundary style) that hold the neighbouring slabs' rows (periodic in y:
+ * slab py - 1 and slab 0 are neighbours).  rank -1 returns to the whole
+ * lattice.  After lb_processors, before the first iteration.
+ * Every command of the setup is issued as for the whole lattice (node
+ * coordinates, obstacle masks and initial-state arrays [..][ny][nx] of the
+ * whole lattice); the context keeps the rows it holds.  The read-out calls
+ * (lb_get_fields, lb_get_velocity_f32, lb_get_populations, lb_get_solute,
+ * lb_get_mask) return the slab's own rows, arrays [..][n][nx]; lb_get_thermo
+ * sums over the slab's own nodes (the lattice's record is the sum over the
+ * slabs).  Each slab draws the same random numbers for a node as the whole
+ * lattice does, so after every iteration followed by a halo exchange the
+ * slabs hold, bit for bit, the rows of the whole lattice.  A slab of a
+ * lattice split into py > 1 advances one iteration per lb_iteration call
+ * (LB_E_ORDER for Nt > 1): exchange halos between calls.  Not built for
+ * slabs (LB_E_UNSUPPORTED at the first iteration): surface_reaction,
+ * intersolute, the TMA kernel, batches.  A slab needs at least
+ * max(3, 2 halo) rows (LB_E_ARG). */
+int lb_processor_rank(lb_ctx *ctx, int rank);
+
+/* Bytes of one halo message of a slab (either face; the same for every
+ * slab of a lattice).  With one ghost row a face carries the populations
+ * the pull takes across it: fluid directions 2, 5, 6 (moving to +y) or
+ * 4, 7, 8 (to -y) of each component and the solute's (+y or -y) ones, one
+ * row each; with two ghost rows every population of two rows.  Layout:
+ * planes in order (component, direction; then solute direction), each
+ * `halo` rows of round_up(nx, 32) values of the storage type.  After the
+ * device state exists (LB_E_ORDER before). */
+int lb_halo_size(lb_ctx *ctx, size_t *bytes);
+
+/* Copy the slab's own rows that its neighbour across face `face` (0: the
+ * low-y side, the slab rank - 1; 1: the high-y side, rank + 1) needs into
+ * the device buffer `buf` (lb_halo_size bytes, 16-byte aligned, on the
+ * context's device); queued on the context's stream.  After an iteration,
+ * the buffer of face 1 goes to slab rank + 1 and that of face 0 to rank - 1
+ * (e.g. by NCCL), which unpack them into their face 0 and face 1. */
+int lb_halo_pack(lb_ctx *ctx, int face, void *buf);
+
+/* Fill the slab's ghost rows on face `face` (0: low y, from slab rank - 1's
+ * face-1 message; 1: high y, from rank + 1's face-0 message) from the
+ * device buffer `buf`; queued on the context's stream. */
+int lb_halo_unpack(lb_ctx *ctx, int face, const void *buf);
+
+/* The halo exchange of all n slabs of one lattice held in one process on
+ * one device and stream (ctxs[r] holds slab r of n): each slab's first and
+ * last own rows go to its neighbours' ghost rows, device to device, in one
+ * launch on that stream.  Call after every iteration of the slabs (all at
+ * the same step).  LB_E_ARG if the contexts are not the slabs of one
+ * lattice at one step, LB_E_UNSUPPORTED if they do not share the device
+ * and stream. */
+int lb_exchange(lb_ctx *const *ctxs, int n);
 
 /* fluids command: two components with relaxation times tau1, tau2 and
  * density-ratio parameters alpha1, alpha2 in [0, 1) (LB_E_ARG otherwise).

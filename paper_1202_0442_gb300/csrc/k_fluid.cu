@@ -63,7 +63,8 @@ __device__ __forceinline__ void pull9(const S *base, const Geometry &g, int x, i
 __device__ __forceinline__ int solid_u(const FluidArgs &p, int x, int y) {
   const Geometry &g = p.g;
   if ((x < 0 || x >= g.nx) && p.edge_x) return -1;
-  if ((y < 0 || y >= g.ny) && p.edge_y) return -1;
+  const int gy = grow(g, y);  // the lattice's edges, not a slab's
+  if ((gy < 0 || gy >= g.gny) && p.edge_y) return -1;
   x = x < 0 ? x + g.nx : (x >= g.nx ? x - g.nx : x);
   y = y < 0 ? y + g.ny : (y >= g.ny ? y - g.ny : y);
   return solid_at(p.mask, g.mw, x, y);
@@ -172,8 +173,8 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
 template <class S, int NC, bool ME, bool PM, int SR>
 __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * LOC_BY + threadIdx.y;
-  if (y >= p.g.ny) return;
+  const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.yhi) return;
   // x < pitch: the grid covers whole 32-node words
   fluid_node<S, NC, ME, PM, SR>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
 }
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
 template <class S, int SR, int Q>
 __global__ void __launch_bounds__(32 * LOC_BY, 4) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * LOC_BY + threadIdx.y;
-  if (y >= p.g.ny) return;
+  const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.yhi) return;
   const uint32_t bits = __ldg(p.nbc + (size_t)y * p.g.pitch + x);
   float u[2];
   if (!fluid_node<S, 1, false, false, SR>(p, x, y, bits, u)) return;
@@ -205,9 +206,9 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
   __shared__ float sd[NC][SC_TY + 2][SC_TX + 2];
   const Geometry &g = p.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * SC_TX, y0 = blockIdx.y * SC_TY;
+  const int x0 = blockIdx.x * SC_TX, y0 = g.ylo + blockIdx.y * SC_TY;
   const int xr = x0 + tx, yr = y0 + ty;
-  const bool real = xr < g.nx && yr < g.ny;
+  const bool real = xr < g.nx && yr < g.yhi;
   const int x = wrapi(xr, g.nx), y = wrapi(yr, g.ny);
   // the node's 3 x 3 solid neighbourhood (lanes past the lattice edge take
   // the wrapped node's)
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
     F[c][0] = -p.G * self * sx;
     F[c][1] = -p.G * self * sy;
   }
-  collide_store<S, NC, true>(p, x, y, bits, h, F);
+  collide_store<S, NC, true, true>(p, x, y, bits, h, F);
 }
 
 template <class S>
@@ -307,9 +308,10 @@ __global__ void k_gradient(const GradArgs a) {
     case 0: x = 0; y = c; dx = 1; break;
     case 1: x = g.nx - 1; y = c; dx = -1; break;
     case 2: x = c; y = 0; dy = 1; break;
-    default: x = c; y = g.ny - 1; dy = -1; break;
+    default: x = c; y = g.gny - 1; dy = -1; break;
   }
-  if (solid_at(a.mask, g.mw, x, y)) return;
+  y -= g.yoff;  // rows of the whole lattice -> rows held here
+  if (y < g.ylo || y >= g.yhi || solid_at(a.mask, g.mw, x, y)) return;
   const size_t n0 = (size_t)y * g.pitch + x;
   const size_t n1 = (size_t)wrapi(y + dy, g.ny) * g.pitch + wrapi(x + dx, g.nx);
   const size_t n2 = (size_t)wrapi(y + 2 * dy, g.ny) * g.pitch + wrapi(x + 2 * dx, g.nx);
@@ -350,7 +352,7 @@ __global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g) 
 template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
-    dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.ny + SC_TY - 1) / SC_TY);
+    dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.yhi - a.g.ylo + SC_TY - 1) / SC_TY);
     if (a.slip) {
       if (nc == 1) k_fluid_sc<S, 1, true><<<grd, blk, 0, s>>>(a);
       else k_fluid_sc<S, 2, true><<<grd, blk, 0, s>>>(a);
@@ -359,7 +361,7 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
       else k_fluid_sc<S, 2, false><<<grd, blk, 0, s>>>(a);
     }
   } else {
-    dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
+    dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
     if (nc == 1) {
       if (me) {
         if (a.pm) k_fluid_local<S, 1, true, true, 0><<<grd, blk, 0, s>>>(a);
@@ -372,7 +374,7 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
         else k_fluid_local<S, 1, false, false, 1><<<grd, blk, 0, s>>>(a);
       }
     } else {
-      k_fluid_local<S, 2, true, false, 0><<<grd, blk, 0, s>>>(a);
+      k_fluid_local<S, 2, true, true, 0><<<grd, blk, 0, s>>>(a);
     }
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
@@ -390,7 +392,7 @@ int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs 
 
 template <class S, int SR>
 int launch_fluid_solute_t(int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
-  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.ny + LOC_BY - 1) / LOC_BY);
+  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
   if (q == 4) k_fluid_solute<S, SR, 4><<<grd, blk, 0, s>>>(a, sa);
   else k_fluid_solute<S, SR, 9><<<grd, blk, 0, s>>>(a, sa);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TB, THERMO_BLOCKS_PER_SM) k_thermo_partial(con
   const size_t P = g.plane;
   const float *f0 = a.fields;
   const float *f1 = a.nc > 1 ? a.fields + (size_t)NFIELD * P : nullptr;
-  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+  for (int y = g.ylo + blockIdx.x; y < g.yhi; y += gridDim.x) {
 #pragma unroll 2
     for (int x = threadIdx.x; x < g.nx; x += TB) {
       const size_t self = (size_t)y * g.pitch + x;
@@ -159,10 +159,13 @@ __global__ void __launch_bounds__(TB, THERMO_BLOCKS_PER_SM) k_thermo_partial(con
   }
 }
 
+// node of dense index idx over the rows [ylo, yhi): the host-side arrays
+// of the conversion kernels are [yhi - ylo][nx], index (y - ylo) nx + x
 __device__ __forceinline__ bool node_of(int idx, const Geometry &g, int &x, int &y) {
-  if (idx >= g.nx * g.ny) return false;
-  y = idx / g.nx;
-  x = idx - y * g.nx;
+  if (idx >= g.nx * (g.yhi - g.ylo)) return false;
+  const int r = idx / g.nx;
+  x = idx - r * g.nx;
+  y = g.ylo + r;
   return true;
 }
 
@@ -172,8 +175,8 @@ __global__ void k_import_pops(const double *src, S *dst, const uint32_t *mask, G
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
-  const size_t nn = (size_t)g.nx * g.ny;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t nn = (size_t)g.nx * (g.yhi - g.ylo);
   for (int i = 0; i < q; i++) {
     double v = sol ? 0.0 : src[(size_t)i * nn + dense];
     if (shift && !sol) v -= wshare(i, alpha) * (double)rho_ref;
@@ -187,8 +190,8 @@ __global__ void k_export_pops(const S *src, double *dst, const uint32_t *mask, G
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
-  const size_t nn = (size_t)g.nx * g.ny;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t nn = (size_t)g.nx * (g.yhi - g.ylo);
   for (int i = 0; i < q; i++) {
     double v = 0.0;
     if (!sol) {
@@ -208,7 +211,7 @@ __global__ void k_equilibrium(const double *rho, const double *ux, const double 
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
   const double r = rho[dense], u = ux ? ux[dense] : 0.0, v = uy ? uy[dense] : 0.0;
   const double dr = r - (double)rho_ref, usq = u * u + v * v;
 #pragma unroll
@@ -227,7 +230,7 @@ __global__ void k_solute_equilibrium(const double *C, const double *ux, const do
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
   const double c = C[dense], u = ux ? ux[dense] : 0.0, v = uy ? uy[dense] : 0.0;
   for (int i = 0; i < q; i++) {
     double val;
@@ -246,7 +249,7 @@ __global__ void k_export_fields(const float *fields, const uint32_t *mask, Geome
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
   const double R = (double)rho_ref;
   if (rho) rho[dense] = sol ? 0.0 : R + (double)fields[self];
   if (px) px[dense] = sol ? 0.0 : (double)fields[g.plane + self];
@@ -259,7 +262,7 @@ __global__ void k_export_velocity(const float *fields, int nc, const uint32_t *m
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  const size_t dense = (size_t)y * g.nx + x, self = (size_t)y * g.pitch + x;
+  const size_t dense = (size_t)(y - g.ylo) * g.nx + x, self = (size_t)y * g.pitch + x;
   float rs = 0.f, pxs = 0.f, pys = 0.f;
   for (int c = 0; c < nc; c++) {
     const float *fl = fields + (size_t)c * NFIELD * g.plane;
@@ -276,23 +279,23 @@ __global__ void k_export_plane_f32(const float *src, const uint32_t *mask, Geome
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
   const bool sol = solid_at(mask, g.mw, x, y);
-  dst[(size_t)y * g.nx + x] = sol ? 0.0 : (double)src[(size_t)y * g.pitch + x];
+  dst[(size_t)(y - g.ylo) * g.nx + x] = sol ? 0.0 : (double)src[(size_t)y * g.pitch + x];
 }
 
 __global__ void k_export_plane_f64(const double *src, Geometry g, double *dst) {
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
-  dst[(size_t)y * g.nx + x] = src[(size_t)y * g.pitch + x];
+  dst[(size_t)(y - g.ylo) * g.nx + x] = src[(size_t)y * g.pitch + x];
 }
 
 __global__ void k_import_plane_f64(const double *src, Geometry g, double *dst) {
   int x, y;
   if (!node_of(blockIdx.x * blockDim.x + threadIdx.x, g, x, y)) return;
-  dst[(size_t)y * g.pitch + x] = src[(size_t)y * g.nx + x];
+  dst[(size_t)y * g.pitch + x] = src[(size_t)(y - g.ylo) * g.nx + x];
 }
 
 inline unsigned grid1(const Geometry &g) {
-  return (unsigned)(((long long)g.nx * g.ny + 255) / 256);
+  return (unsigned)(((long long)g.nx * (g.yhi - g.ylo) + 255) / 256);
 }
 
 inline int ok() { return cudaGetLastError() == cudaSuccess ? 1 : -1; }
@@ -300,11 +303,35 @@ inline int ok() { return cudaGetLastError() == cudaSuccess ? 1 : -1; }
 }  // namespace
 
 int thermo_blocks(const Geometry &g, int sms) {
-  // one block per row, at most THERMO_BLOCKS_PER_SM per SM (all resident)
-  int b = g.ny;
+  // one block per updated row, at most THERMO_BLOCKS_PER_SM per SM (all resident)
+  int b = g.yhi - g.ylo;
   const int cap = THERMO_BLOCKS_PER_SM * (sms > 0 ? sms : 1);
   if (b > cap) b = cap;
   return b < 1 ? 1 : b;
+}
+
+namespace {
+
+// contiguous runs copied between device buffers (the halo rows of slabs):
+// run k goes from src[k] to dst[k], bytes[k] of them (16-byte aligned, a
+// multiple of 16); blockIdx.y picks the run
+__global__ void k_copy_runs(const CopyRuns r) {
+  const int k = blockIdx.y;
+  const uint4 *s = (const uint4 *)r.src[k];
+  uint4 *d = (uint4 *)r.dst[k];
+  const unsigned n16 = r.bytes[k] >> 4;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x) d[i] = s[i];
+}
+
+}  // namespace
+
+int launch_copy_runs(const CopyRuns &r, cudaStream_t s) {
+  if (r.n <= 0) return 0;
+  unsigned most = 0;
+  for (int k = 0; k < r.n; k++) most = max(most, r.bytes[k] >> 4);
+  const unsigned bx = (most + 255) / 256;
+  k_copy_runs<<<dim3(bx < 1 ? 1 : (bx > 16 ? 16 : bx), r.n), 256, 0, s>>>(r);
+  return ok();
 }
 
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {

@@ -39,9 +39,9 @@ namespace {
 template <int Q>
 __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
-  if (y >= g.ny) return;
+  const int y = g.ylo + blockIdx.y * blockDim.y + threadIdx.y;
+  if (y >= g.yhi) return;
   const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx) return;
   const size_t self = (size_t)y * g.pitch + x;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
     p.Cpre_out[self] = 0.f;
     return;
   }
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
   float gt[Q], Cw, Cflux = 0.f;
   int nU;
   uint32_t U, cross;
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
 template <int Q>
 __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = p.g;
-  if (y >= g.ny) return;
+  const int y = g.ylo + blockIdx.y * blockDim.y + threadIdx.y;
+  if (y >= g.yhi) return;
   const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx || ((bits >> 4) & 1u)) return;
   const size_t self = (size_t)y * g.pitch + x;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
 }  // namespace
 
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
-  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + 7) / 8);
   int n = 0;
   if (a.inter) {
     if (q == 4) k_solute_pre<4><<<grd, blk, 0, s>>>(a);

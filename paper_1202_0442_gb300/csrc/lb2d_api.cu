@@ -55,6 +55,7 @@ size_t storage_bytes(int st) { return st == ST_FP32 ? 4 : 2; }
 
 }  // namespace
 
+
 struct lb_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -96,6 +97,12 @@ struct lb_ctx {
   double isG = 0, ispsi0 = 0, isC0 = 0;
   uint64_t seed = 0;
   int nf = 0;
+  // processors command: a px x py grid of processes; a context given a
+  // rank (lb_processor_rank) holds one y slab of the lattice: rows
+  // [sy0, sy0 + sny) and `halo` ghost rows on each side
+  int px = 1, py = 1;
+  int rank = -1;  // -1: the whole lattice
+  int halo = 0, sy0 = 0, sny = 0;
 
   // device state
   Geometry g{};
@@ -120,7 +127,8 @@ struct lb_ctx {
   unsigned int *tdone = nullptr;  // thermo blocks finished (reset by the last)
   int tblocks = 0;
   int64_t t = 0;
-  int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline
+  int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
+                         // 3 fused fluid-solute
   int *errw = nullptr;   // device error word of the TMA kernel
   int sms = 0;
   bool fields_valid = false;
@@ -161,6 +169,8 @@ struct lb_ctx {
   } while (0)
 
 namespace {
+
+int exchange_slabs(lb_ctx *const *ctxs, int n);  // slabs: halo rows (below)
 
 int set_device(lb_ctx *ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -244,8 +254,55 @@ int buffer_index(const char *what) {
   return -1;
 }
 
+// ghost rows on each side of a slab: the pull reaches one row; interforce
+// (the neighbours' densities after this step's streaming) and the slip
+// styles (mirror sources two rows away) reach two
+int slab_halo(const lb_ctx *ctx) { return (ctx->sc || ctx->bstyle != 0) ? 2 : 1; }
+
+// rows [y0, y0 + n) of slab `rank` out of py (sizes differ by one at most)
+void slab_rows(const lb_ctx *ctx, int rank, int &y0, int &n) {
+  y0 = (int)((long long)rank * ctx->ny / ctx->py);
+  n = (int)((long long)(rank + 1) * ctx->ny / ctx->py) - y0;
+}
+
+// rows the context holds on the device: the lattice's, or a slab's own
+// rows and its ghost rows
+int held_rows(const lb_ctx *ctx) {
+  if (ctx->rank < 0) return ctx->ny;
+  int y0, n;
+  slab_rows(ctx, ctx->rank, y0, n);
+  return n + 2 * slab_halo(ctx);
+}
+
+// rows of the lattice updated here (its own rows for a slab)
+int own_rows(const lb_ctx *ctx) { return ctx->committed ? ctx->g.yhi - ctx->g.ylo : ctx->ny; }
+
+// geometry for the conversion kernels that fill every held row (ghost rows
+// included)
+Geometry all_rows(const Geometry &g) {
+  Geometry a = g;
+  a.ylo = 0;
+  a.yhi = g.ny;
+  return a;
+}
+
+// the held rows of a host array [planes][ny][nx] of the whole lattice, as
+// [planes][held rows][nx] (held row y is lattice row y + yoff, wrapped)
+const double *held_part(const lb_ctx *ctx, const double *src, int planes, std::vector<double> &buf) {
+  if (!src || ctx->rank < 0) return src;
+  const Geometry &g = ctx->g;
+  const size_t nx = (size_t)ctx->nx, nn = nx * ctx->ny, nl = nx * g.ny;
+  buf.resize((size_t)planes * nl);
+  for (int q = 0; q < planes; q++)
+    for (int y = 0; y < g.ny; y++) {
+      const int gy = ((y + g.yoff) % ctx->ny + ctx->ny) % ctx->ny;
+      memcpy(&buf[q * nl + y * nx], src + q * nn + (size_t)gy * nx, nx * sizeof(double));
+    }
+  return buf.data();
+}
+
 size_t buffer_bytes(const lb_ctx *ctx, int k) {
-  const size_t plane = (size_t)ctx->ny * (size_t)((ctx->nx + 31) / 32 * 32);
+  const size_t plane = (size_t)held_rows(ctx) * (size_t)((ctx->nx + 31) / 32 * 32);
   switch (k) {
     case 0:
     case 1: return (size_t)ctx->nc * 9 * plane * storage_bytes(ctx->storage);
@@ -356,13 +413,27 @@ int commit(lb_ctx *ctx) {
   if (ctx->committed) return LB_OK;
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   TRY(validate(ctx));
+  if (ctx->rank >= 0) {
+    // a slab: which parts of the method it holds
+    if (ctx->react) return ctx->fail(LB_E_UNSUPPORTED, "surface_reaction on a slab is not built: run the reactive lattice whole");
+    if (ctx->inter) return ctx->fail(LB_E_UNSUPPORTED, "intersolute on a slab is not built: run the lattice whole");
+    ctx->halo = slab_halo(ctx);
+    slab_rows(ctx, ctx->rank, ctx->sy0, ctx->sny);
+    if (ctx->sny < std::max(3, 2 * ctx->halo))
+      return ctx->fail(LB_E_ARG, "slab %d has %d rows; it needs at least %d", ctx->rank, ctx->sny,
+                       std::max(3, 2 * ctx->halo));
+  }
   TRY(set_device(ctx));
   Geometry &g = ctx->g;
   g.nx = ctx->nx;
-  g.ny = ctx->ny;
+  g.ny = held_rows(ctx);
   g.pitch = (ctx->nx + 31) / 32 * 32;
   g.mw = g.pitch / 32;
   g.plane = (size_t)g.ny * g.pitch;
+  g.gny = ctx->ny;
+  g.ylo = ctx->rank >= 0 ? ctx->halo : 0;
+  g.yhi = g.ylo + (ctx->rank >= 0 ? ctx->sny : ctx->ny);
+  g.yoff = ctx->rank >= 0 ? ctx->sy0 - ctx->halo : 0;
   const size_t sb = storage_bytes(ctx->storage);
   const size_t fbytes = (size_t)ctx->nc * 9 * g.plane * sb;
   for (int k = 0; k < 2; k++) TRY(dalloc_state(ctx, (uint8_t **)&ctx->fbuf[k], fbytes, k));
@@ -389,11 +460,12 @@ int commit(lb_ctx *ctx) {
   TRY(dalloc(ctx, &ctx->tout, NTHERMO + 2));
   TRY(dalloc(ctx, &ctx->tdone, 1));
 
-  // bit-packed mask
+  // bit-packed mask of the held rows (held row y is lattice row y + yoff)
+  auto lattice_row = [&](int y) { return ((y + g.yoff) % ctx->ny + ctx->ny) % ctx->ny; };
   std::vector<uint32_t> m((size_t)g.ny * g.mw, 0u);
   for (int y = 0; y < g.ny; y++)
     for (int x = 0; x < g.nx; x++)
-      if (ctx->solid[(size_t)y * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
+      if (ctx->solid[(size_t)lattice_row(y) * g.nx + x]) m[(size_t)y * g.mw + (x >> 5)] |= 1u << (x & 31);
   CK(cudaMemcpyAsync(ctx->mask, m.data(), m.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
   LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream));
   ctx->mask_host = m;
@@ -407,7 +479,7 @@ int commit(lb_ctx *ctx) {
     for (int c = 0; c < ctx->nc; c++)
       for (int y = 0; y < g.ny; y++)
         for (int x = 0; x < g.nx; x++) {
-          const size_t n = (size_t)y * g.nx + x;
+          const size_t n = (size_t)lattice_row(y) * g.nx + x;
           if (ctx->solid[n]) rh[(size_t)c * g.plane + (size_t)y * g.pitch + x] = ctx->Rh[c][n];
         }
     CK(cudaMemcpyAsync(ctx->Rmap, rh.data(), rh.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
@@ -419,7 +491,7 @@ int commit(lb_ctx *ctx) {
     std::vector<double> bh(g.plane, 0.0);
     for (int y = 0; y < g.ny; y++)
       for (int x = 0; x < g.nx; x++)
-        if (ctx->solid[(size_t)y * g.nx + x]) bh[(size_t)y * g.pitch + x] = ctx->b0;
+        if (ctx->solid[(size_t)lattice_row(y) * g.nx + x]) bh[(size_t)y * g.pitch + x] = ctx->b0;
     CK(cudaMemcpyAsync(ctx->b, bh.data(), bh.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
   }
   ctx->committed = true;
@@ -578,7 +650,8 @@ int one_step(lb_ctx *ctx, bool fields) {
   // two components and Shan-Chen runs keep |f - w rho_ref| large: their
   // collision is the mass-exact one
   const bool mass_exact = ctx->nc == 2 || ctx->sc;
-  const bool tma_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0 && !ctx->pm && tma_supported(ctx->storage, ctx->g);
+  const bool tma_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0 && !ctx->pm && ctx->rank < 0 &&
+                      tma_supported(ctx->storage, ctx->g);
   if (ctx->kernel == 2 && !tma_ok)
     return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component noslip lattices without "
                      "interforce whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
@@ -780,7 +853,22 @@ int lb_processors(lb_ctx *ctx, int px, int py) {
   if (ctx->momentum_cmd)
     return ctx->fail(LB_E_ORDER, "processors must precede inlet_momentum/outlet_momentum and momentum0");
   if (px < 1 || py < 1) return ctx->fail(LB_E_ARG, "processor grid must be positive");
-  return LB_OK;  // one GPU runs the whole lattice
+  if (ctx->committed) return ctx->fail(LB_E_ORDER, "processors must precede the first iteration");
+  if (ctx->rank >= 0 && (px != 1 || ctx->rank >= py))
+    return ctx->fail(LB_E_ARG, "rank %d does not fit the processor grid %d x %d", ctx->rank, px, py);
+  ctx->px = px;
+  ctx->py = py;
+  return LB_OK;
+}
+
+int lb_processor_rank(lb_ctx *ctx, int rank) {
+  NEED_CTX();
+  if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "the rank must follow lattice and processors");
+  if (ctx->committed) return ctx->fail(LB_E_ORDER, "the rank must precede the first iteration");
+  if (ctx->px != 1) return ctx->fail(LB_E_UNSUPPORTED, "slabs split the lattice along y only: processors(1, py)");
+  if (rank < -1 || rank >= ctx->py) return ctx->fail(LB_E_ARG, "rank %d is outside 0..%d", rank, ctx->py - 1);
+  ctx->rank = rank;
+  return LB_OK;
 }
 
 int lb_fluids(lb_ctx *ctx, double tau1, double tau2, double alpha1, double alpha2) {
@@ -1155,13 +1243,16 @@ int lb_set_equilibrium(lb_ctx *ctx, int fluid, const double *rho, const double *
       return ctx->fail(LB_E_ARG, "density must be positive on fluid node (%zu,%zu)", n % ctx->nx, n / ctx->nx);
   ctx->painted_f[fluid - 1] = false;
   TRY(commit(ctx));
+  // a slab takes its rows and ghost rows of the lattice's arrays
+  std::vector<double> br, bu, bv;
+  const size_t nl = (size_t)ctx->nx * ctx->g.ny;
   Stage r, u, v;
-  TRY(stage_in(ctx, r, rho, nn));
-  if (ux) TRY(stage_in(ctx, u, ux, nn));
-  if (uy) TRY(stage_in(ctx, v, uy, nn));
+  TRY(stage_in(ctx, r, held_part(ctx, rho, 1, br), nl));
+  if (ux) TRY(stage_in(ctx, u, held_part(ctx, ux, 1, bu), nl));
+  if (uy) TRY(stage_in(ctx, v, held_part(ctx, uy, 1, bv), nl));
   const size_t sb = storage_bytes(ctx->storage);
   void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
-  LAUNCH(launch_equilibrium(ctx->storage, r.p, u.p, v.p, dst, ctx->mask, ctx->g,
+  LAUNCH(launch_equilibrium(ctx->storage, r.p, u.p, v.p, dst, ctx->mask, all_rows(ctx->g),
                             (float)ctx->rho_ref[fluid - 1], ctx->scale, ctx->alpha[fluid - 1], ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->state_set[fluid - 1] = true;
@@ -1175,12 +1266,14 @@ int lb_set_solute_equilibrium(lb_ctx *ctx, const double *C, const double *ux, co
   if (!C) return ctx->fail(LB_E_ARG, "null C");
   ctx->painted_C = false;
   TRY(commit(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  std::vector<double> bc, bu, bv;
+  const size_t nl = (size_t)ctx->nx * ctx->g.ny;
   Stage c, u, v;
-  TRY(stage_in(ctx, c, C, nn));
-  if (ux) TRY(stage_in(ctx, u, ux, nn));
-  if (uy) TRY(stage_in(ctx, v, uy, nn));
-  LAUNCH(launch_solute_equilibrium(ctx->qs, c.p, u.p, v.p, ctx->gbuf[ctx->cur], ctx->mask, ctx->g, ctx->stream));
+  TRY(stage_in(ctx, c, held_part(ctx, C, 1, bc), nl));
+  if (ux) TRY(stage_in(ctx, u, held_part(ctx, ux, 1, bu), nl));
+  if (uy) TRY(stage_in(ctx, v, held_part(ctx, uy, 1, bv), nl));
+  LAUNCH(launch_solute_equilibrium(ctx->qs, c.p, u.p, v.p, ctx->gbuf[ctx->cur], ctx->mask, all_rows(ctx->g),
+                                   ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->solute_set = true;
   return LB_OK;
@@ -1193,12 +1286,13 @@ int lb_set_populations(lb_ctx *ctx, int fluid, const double *f) {
   if (!fluid_ok(ctx, fluid) || !f) return ctx->fail(LB_E_ARG, "bad fluid or null array");
   if (!ctx->committed) ctx->painted_f[fluid - 1] = false;
   TRY(commit(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  std::vector<double> bf;
+  const size_t nl = (size_t)ctx->nx * ctx->g.ny;
   Stage st;
-  TRY(stage_in(ctx, st, f, 9 * nn));
+  TRY(stage_in(ctx, st, held_part(ctx, f, 9, bf), 9 * nl));
   const size_t sb = storage_bytes(ctx->storage);
   void *dst = (uint8_t *)ctx->fbuf[ctx->cur] + (size_t)(fluid - 1) * 9 * ctx->g.plane * sb;
-  LAUNCH(launch_import_pops(ctx->storage, st.p, dst, ctx->mask, ctx->g, 9, (float)ctx->rho_ref[fluid - 1],
+  LAUNCH(launch_import_pops(ctx->storage, st.p, dst, ctx->mask, all_rows(ctx->g), 9, (float)ctx->rho_ref[fluid - 1],
                             ctx->scale, true, ctx->alpha[fluid - 1], ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->state_set[fluid - 1] = true;
@@ -1212,10 +1306,11 @@ int lb_set_solute_populations(lb_ctx *ctx, const double *g) {
   if (!g) return ctx->fail(LB_E_ARG, "null array");
   ctx->painted_C = false;
   TRY(commit(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  std::vector<double> bg;
+  const size_t nl = (size_t)ctx->nx * ctx->g.ny;
   Stage st;
-  TRY(stage_in(ctx, st, g, (size_t)ctx->qs * nn));
-  LAUNCH(launch_import_pops(ST_FP32, st.p, ctx->gbuf[ctx->cur], ctx->mask, ctx->g, ctx->qs, 0.f, 1.f, false,
+  TRY(stage_in(ctx, st, held_part(ctx, g, ctx->qs, bg), (size_t)ctx->qs * nl));
+  LAUNCH(launch_import_pops(ST_FP32, st.p, ctx->gbuf[ctx->cur], ctx->mask, all_rows(ctx->g), ctx->qs, 0.f, 1.f, false,
                             4.0 / 9.0, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->solute_set = true;
@@ -1227,9 +1322,10 @@ int lb_set_precipitate(lb_ctx *ctx, const double *b) {
   ctx->fields_step = -1;  // the live state no longer matches the field planes
   if (!b) return ctx->fail(LB_E_ARG, "null array");
   TRY(commit(ctx));
+  std::vector<double> bb;
   Stage st;
-  TRY(stage_in(ctx, st, b, (size_t)ctx->nx * ctx->ny));
-  LAUNCH(launch_import_plane_f64(st.p, ctx->g, ctx->b, ctx->stream));
+  TRY(stage_in(ctx, st, held_part(ctx, b, 1, bb), (size_t)ctx->nx * ctx->g.ny));
+  LAUNCH(launch_import_plane_f64(st.p, all_rows(ctx->g), ctx->b, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return LB_OK;
 }
@@ -1324,9 +1420,16 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
     return ctx->fail(LB_E_ORDER, "solute has no initial state (concentration0 or lb_set_solute_equilibrium)");
   TRY(commit(ctx));
   TRY(set_device(ctx));
+  // a slab reads its ghost rows every iteration: with other slabs they are
+  // filled between calls (lb_exchange or lb_halo_pack/unpack); a single slab
+  // (processors 1 x 1) is its own neighbour and refills them itself
+  if (ctx->rank >= 0 && ctx->py > 1 && Nt > 1)
+    return ctx->fail(LB_E_ORDER, "a slab of a lattice split into %d advances one iteration per call, its halo "
+                     "rows exchanged between calls", ctx->py);
   for (int k = 1; k <= Nt; k++) {
     const bool thermo = ctx->nf > 0 ? ((ctx->t + 1) % ctx->nf == 0) : (k == Nt);
     TRY(one_step(ctx, thermo));
+    if (ctx->rank >= 0 && ctx->py == 1) TRY(exchange_slabs(&ctx, 1));
     if (thermo) {
       ctx->fields_valid = true;
       ctx->fields_step = ctx->t;
@@ -1349,7 +1452,7 @@ int lb_get_fields(lb_ctx *ctx, int fluid, double *rho, double *px, double *py, d
   if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
   if (!fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad fluid");
   TRY(set_device(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  const size_t nn = (size_t)ctx->nx * own_rows(ctx);  // a slab: its own rows
   Stage st;
   TRY(stage_alloc(ctx, st, 4 * nn));
   LAUNCH(launch_export_fields(ctx->fields, fluid - 1, ctx->mask, ctx->g, (float)ctx->rho_ref[fluid - 1], st.p,
@@ -1377,7 +1480,7 @@ int lb_get_velocity_f32(lb_ctx *ctx, float *rho, float *ux, float *uy) {
   if (!ctx->fields_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
   if (!rho || !ux || !uy) return ctx->fail(LB_E_ARG, "null output");
   TRY(set_device(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  const size_t nn = (size_t)ctx->nx * own_rows(ctx);  // a slab: its own rows
   float rr[2] = {(float)ctx->rho_ref[0], (float)ctx->rho_ref[1]};
   if (device_view(rho) && device_view(ux) && device_view(uy)) {
     // page-locked outputs: the export kernel writes them over the host link
@@ -1410,7 +1513,7 @@ int lb_get_populations(lb_ctx *ctx, int fluid, double *f) {
   if (!ctx->committed) return ctx->fail(LB_E_ORDER, "no device state yet");
   if (!fluid_ok(ctx, fluid) || !f) return ctx->fail(LB_E_ARG, "bad fluid or null array");
   TRY(set_device(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  const size_t nn = (size_t)ctx->nx * own_rows(ctx);  // a slab: its own rows
   Stage st;
   TRY(stage_alloc(ctx, st, 9 * nn));
   const size_t sb = storage_bytes(ctx->storage);
@@ -1426,7 +1529,7 @@ int lb_get_solute(lb_ctx *ctx, double *g, double *C, double *b) {
   NEED_CTX();
   if (!ctx->committed) return ctx->fail(LB_E_ORDER, "no device state yet");
   TRY(set_device(ctx));
-  const size_t nn = (size_t)ctx->nx * ctx->ny;
+  const size_t nn = (size_t)ctx->nx * own_rows(ctx);  // a slab: its own rows
   if (g) {
     if (!ctx->qs) return ctx->fail(LB_E_ORDER, "no solute");
     Stage st;
@@ -1459,16 +1562,19 @@ int lb_get_mask(lb_ctx *ctx, uint8_t *mask) {
   NEED_CTX();
   if (!mask) return ctx->fail(LB_E_ARG, "null output");
   if (!ctx->committed) {
-    memcpy(mask, ctx->solid.data(), ctx->solid.size());
+    int y0 = 0, n = ctx->ny;
+    if (ctx->rank >= 0) slab_rows(ctx, ctx->rank, y0, n);
+    memcpy(mask, ctx->solid.data() + (size_t)y0 * ctx->nx, (size_t)n * ctx->nx);
     return LB_OK;
   }
   TRY(set_device(ctx));
   std::vector<uint32_t> m((size_t)ctx->g.ny * ctx->g.mw);
   CK(cudaMemcpyAsync(m.data(), ctx->mask, m.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  for (int y = 0; y < ctx->ny; y++)
+  // the updated rows (a slab's own rows)
+  for (int y = ctx->g.ylo; y < ctx->g.yhi; y++)
     for (int x = 0; x < ctx->nx; x++)
-      mask[(size_t)y * ctx->nx + x] = (m[(size_t)y * ctx->g.mw + (x >> 5)] >> (x & 31)) & 1u;
+      mask[(size_t)(y - ctx->g.ylo) * ctx->nx + x] = (m[(size_t)y * ctx->g.mw + (x >> 5)] >> (x & 31)) & 1u;
   return LB_OK;
 }
 
@@ -1547,6 +1653,156 @@ int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count) {
   *count = (int)n;
   return LB_OK;
 }
+
+
+}  // extern "C"
+
+// ======================================================================
+// slabs (processors command): the halo rows between neighbouring slabs
+// ======================================================================
+
+namespace {
+
+struct Run {
+  uint8_t *p;
+  size_t bytes;
+};
+
+// The rows of the current state buffers across face `face` of a slab (0:
+// its low-y side, 1: its high-y side): the rows it sends (ghost = false:
+// its first or last `halo` own rows) or the ghost rows it receives into
+// (ghost = true), one run per population plane.  With one ghost row only
+// the populations the pull takes across the face travel (e_y = +1 for data
+// moving towards +y, e_y = -1 for data moving towards -y); with two ghost
+// rows every population does.
+void face_runs(lb_ctx *ctx, int face, bool ghost, std::vector<Run> &runs) {
+  runs.clear();
+  const Geometry &g = ctx->g;
+  const int H = ctx->halo;
+  const size_t r0 = (size_t)(face == 0 ? (ghost ? 0 : g.ylo) : (ghost ? g.yhi : g.yhi - H));
+  const int dir = ((face == 1) != ghost) ? 1 : -1;  // e_y of the data crossing
+  const size_t row = (size_t)g.pitch, sb = storage_bytes(ctx->storage);
+  for (int c = 0; c < ctx->nc; c++)
+    for (int q = 0; q < 9; q++)
+      if (H > 1 || EYD[q] == dir)
+        runs.push_back({(uint8_t *)ctx->fbuf[ctx->cur] + (((size_t)c * 9 + q) * g.plane + r0 * row) * sb, H * row * sb});
+  for (int q = 0; q < ctx->qs; q++) {
+    const int ey = ctx->qs == 4 ? EY4D[q] : EYD[q];
+    if (H > 1 || ey == dir)
+      runs.push_back({(uint8_t *)ctx->gbuf[ctx->cur] + ((size_t)q * g.plane + r0 * row) * 4, H * row * 4});
+  }
+}
+
+// device-to-device copies src[k] -> dst[k] of bytes[k], MAX_RUNS per launch
+int copy_runs(lb_ctx *ctx, const std::vector<const void *> &src, const std::vector<void *> &dst,
+              const std::vector<size_t> &bytes) {
+  for (size_t k0 = 0; k0 < src.size(); k0 += MAX_RUNS) {
+    CopyRuns r{};
+    r.n = (int)std::min(src.size() - k0, (size_t)MAX_RUNS);
+    for (int k = 0; k < r.n; k++) {
+      r.src[k] = src[k0 + k];
+      r.dst[k] = dst[k0 + k];
+      r.bytes[k] = (unsigned)bytes[k0 + k];
+    }
+    LAUNCH(launch_copy_runs(r, ctx->stream));
+  }
+  return LB_OK;
+}
+
+int slab_check(lb_ctx *ctx) {
+  if (ctx->rank < 0) return ctx->fail(LB_E_ORDER, "not a slab: call lb_processors(1, py) and lb_processor_rank first");
+  if (!ctx->committed) return ctx->fail(LB_E_ORDER, "the slab has no device state yet: set its initial state first");
+  return LB_OK;
+}
+
+// every slab's first and last own rows into its neighbours' ghost rows
+// (periodic in y: slab py - 1 and slab 0 are neighbours)
+int exchange_slabs(lb_ctx *const *ctxs, int n) {
+  std::vector<const void *> src;
+  std::vector<void *> dst;
+  std::vector<size_t> bytes;
+  std::vector<Run> a, b;
+  for (int r = 0; r < n; r++) {
+    for (int face = 0; face < 2; face++) {
+      lb_ctx *to = ctxs[face == 1 ? (r + 1) % n : (r + n - 1) % n];
+      face_runs(ctxs[r], face, false, a);
+      face_runs(to, 1 - face, true, b);
+      for (size_t k = 0; k < a.size(); k++) {
+        src.push_back(a[k].p);
+        dst.push_back(b[k].p);
+        bytes.push_back(a[k].bytes);
+      }
+    }
+  }
+  return copy_runs(ctxs[0], src, dst, bytes);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_halo_size(lb_ctx *ctx, size_t *bytes) {
+  NEED_CTX();
+  if (!bytes) return ctx->fail(LB_E_ARG, "null output");
+  TRY(slab_check(ctx));
+  std::vector<Run> runs;
+  face_runs(ctx, 1, false, runs);
+  size_t n = 0;
+  for (const Run &r : runs) n += r.bytes;
+  *bytes = n;
+  return LB_OK;
+}
+
+static int halo_move(lb_ctx *ctx, int face, void *buf, bool pack) {
+  NEED_CTX();
+  TRY(slab_check(ctx));
+  if (face != 0 && face != 1) return ctx->fail(LB_E_ARG, "face must be 0 (low y) or 1 (high y)");
+  if (!buf || (uintptr_t)buf % 16) return ctx->fail(LB_E_ARG, "halo buffer must be a 16-byte aligned device pointer");
+  TRY(set_device(ctx));
+  std::vector<Run> runs;
+  face_runs(ctx, face, !pack, runs);
+  std::vector<const void *> src;
+  std::vector<void *> dst;
+  std::vector<size_t> bytes;
+  size_t off = 0;
+  for (const Run &r : runs) {
+    uint8_t *b = (uint8_t *)buf + off;
+    src.push_back(pack ? (const void *)r.p : (const void *)b);
+    dst.push_back(pack ? (void *)b : (void *)r.p);
+    bytes.push_back(r.bytes);
+    off += r.bytes;
+  }
+  return copy_runs(ctx, src, dst, bytes);
+}
+
+int lb_halo_pack(lb_ctx *ctx, int face, void *buf) { return halo_move(ctx, face, buf, true); }
+
+int lb_halo_unpack(lb_ctx *ctx, int face, const void *buf) { return halo_move(ctx, face, (void *)buf, false); }
+
+int lb_exchange(lb_ctx *const *ctxs, int n) {
+  if (!ctxs || n < 1) return LB_E_ARG;
+  for (int r = 0; r < n; r++)
+    if (!ctxs[r]) return LB_E_ARG;
+  lb_ctx *c0 = ctxs[0];
+  for (int r = 0; r < n; r++) {
+    lb_ctx *c = ctxs[r];
+    TRY(slab_check(c));
+    if (c->rank != r || c->py != n)
+      return c->fail(LB_E_ARG, "lb_exchange takes the %d slabs of one lattice in rank order", c->py);
+    if (c->nx != c0->nx || c->ny != c0->ny || c->nc != c0->nc || c->qs != c0->qs || c->storage != c0->storage ||
+        c->halo != c0->halo || c->cur != c0->cur || c->t != c0->t)
+      return c->fail(LB_E_ARG, "slab %d does not belong to the same lattice and step as slab 0", r);
+    if (c->device != c0->device || c->stream != c0->stream)
+      return c->fail(LB_E_UNSUPPORTED, "lb_exchange moves rows within one device and stream; "
+                     "across devices use lb_halo_pack/lb_halo_unpack");
+  }
+  TRY(set_device(c0));
+  return exchange_slabs(ctxs, n);
+}
+
+}  // extern "C"
+
+extern "C" {
 
 // snapshot layout: header, populations (current buffer), mask, solute
 // populations, and with surface_reaction the precipitate, removed tallies
@@ -1845,7 +2101,7 @@ int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out) {
     lb_ctx *c = ctxs[k];
     int rc = LB_OK;
     if (!c) rc = LB_E_ARG;
-    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0] || c->bstyle != 0)
+    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0] || c->bstyle != 0 || c->rank >= 0)
       rc = c->fail(LB_E_UNSUPPORTED, "batched lattices are periodic single-component noslip lattices with body forces");
     else {
       for (int s = 0; s < c->nc && rc == LB_OK; s++)

@@ -43,8 +43,9 @@ __device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, f
 
 // moments, forces, equilibrium velocity, BGK and the stores of one node.
 // Fsc: interforce already evaluated (zero when off).  ME: mass-exact
-// collision (see below).  PM: the momentum as an exact hi + lo sum (single
-// component; the storage flag LB_PRECISE_MOMENTUM).  FOLD (scaled 16-bit
+// collision (see below).  PM: the momentum as an exact hi + lo sum (the
+// storage flag LB_PRECISE_MOMENTUM for one component; always with two
+// components and interforce).  FOLD (scaled 16-bit
 // storage, not ME): h arrives and leaves in the stored units 2^s h, so the
 // loads and stores skip their scale factors; the moments are unscaled once
 // and the equilibrium is formed directly in stored units.  SR: 0 read
@@ -55,6 +56,9 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
                                               float *uo = nullptr) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
+  // the node's slot in the whole lattice: the random words are the same
+  // whether the lattice is held whole or in slabs
+  const int hself = self + g.yoff * g.pitch;
   const int P = (int)g.plane;
   float drho[NC], rho[NC], jx[NC], jy[NC], jxl[NC], jyl[NC], Fx[NC], Fy[NC];
   // stored units -> physical units (a power of two: exact)
@@ -64,7 +68,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     const float(&f)[9] = h[c];
     drho[c] = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]) * un;
     rho[c] = p.rho_ref[c] + drho[c];
-    if (PM && NC == 1) {
+    if (PM) {
       momentum_exact(f, jx[c], jxl[c], jy[c], jyl[c]);
     } else {
       jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
@@ -95,12 +99,14 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     uex[0] = mxt[0] * ir;
     uey[0] = myt[0] * ir;
   } else {
-    // common velocity sum(j/tau) / sum(rho/tau), shifted per component
+    // common velocity sum(j/tau) / sum(rho/tau), shifted per component;
+    // with PM each j enters as hi + lo (the pair's sum is j to FP32
+    // precision relative to j itself, not to the populations it came from)
     float nxs = 0.f, nys = 0.f, den = 0.f;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      nxs += jx[c] * p.omega[c];
-      nys += jy[c] * p.omega[c];
+      nxs += (PM ? jx[c] + jxl[c] : jx[c]) * p.omega[c];
+      nys += (PM ? jy[c] + jyl[c] : jy[c]) * p.omega[c];
       den += rho[c] * p.omega[c];
     }
     const float upx = nxs / den, upy = nys / den;
@@ -129,7 +135,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     if (!ME && SR != 0) {
       // SR 2: one hash per node and component, then a linear congruential
       // sequence whose high bits dither each store
-      uint32_t r = SR == 2 ? rnd(p.sr_seed, self, c, 0) : 0u;
+      uint32_t r = SR == 2 ? rnd(p.sr_seed, hself, c, 0) : 0u;
 #pragma unroll
       for (int i = 0; i < 9; i++) {
         const float v = h[c][i] + om * (heq[i] - h[c][i]);
@@ -142,7 +148,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         }
       }
     } else if (!ME) {
-      uint32_t r = p.sr_seed ? rnd(p.sr_seed, self, c, 0) : 0u;
+      uint32_t r = p.sr_seed ? rnd(p.sr_seed, hself, c, 0) : 0u;
 #pragma unroll
       for (int i = 0; i < 9; i++) {
         // dither of the 16-bit stores: one hash per node and component,
@@ -174,7 +180,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         // 16-bit dither: an independent hash per store (a linear
         // congruential sequence per node, as in the plain collision, was
         // measurably worse for the two-component runs)
-        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, self, c, i) | 1u) : 0u;
+        const uint32_t r = p.sr_seed ? (rnd(p.sr_seed, hself, c, i) | 1u) : 0u;
         const float v = Store<S>::st_ret(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]),
                                          p.scale, p.inv_scale, r);
         float s, e;
@@ -194,10 +200,10 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         // fast division's last bit: a probability, compared with a uniform
         // variate
         const float pr = __fdividef(fabsf(rem), fabsf(nxt - h0));
-        const float u01 = (float)(rnd(p.step_seed, self, c, 9) >> 8) * (1.0f / 16777216.0f);
+        const float u01 = (float)(rnd(p.step_seed, hself, c, 9) >> 8) * (1.0f / 16777216.0f);
         if (u01 < pr) h0 = nxt;
       }
-      const uint32_t r0 = p.sr_seed ? (rnd(p.sr_seed, self, c, 0) | 1u) : 0u;
+      const uint32_t r0 = p.sr_seed ? (rnd(p.sr_seed, hself, c, 0) | 1u) : 0u;
       Store<S>::st(out, self, h0, p.scale, r0);
     }
     if (p.fields) {
@@ -235,12 +241,13 @@ template <int NC>
 __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
                                                float (&h)[NC][9], float sc = 1.0f) {
   const Geometry &g = p.g;
-  if (!(x == 0 || y == 0 || x == g.nx - 1 || y == g.ny - 1)) return;
+  const int gy = grow(g, y);  // openings are placed on the whole lattice
+  if (!(x == 0 || gy == 0 || x == g.nx - 1 || gy == g.gny - 1)) return;
 #pragma unroll 1
   for (int k = 0; k < p.nopen; k++) {
-    if (!opening_has(p.op[k], x, y, g.nx, g.ny)) continue;
+    if (!opening_has(p.op[k], x, gy, g.nx, g.gny)) continue;
 #pragma unroll
-    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, y, p.rho_ref[c], sc);
+    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, gy, p.rho_ref[c], sc);
     break;
   }
 }

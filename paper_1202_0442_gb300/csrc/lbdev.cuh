@@ -155,6 +155,9 @@ __device__ __forceinline__ int solid_at(const uint32_t *m, int mw, int x, int y)
   return (int)((__ldg(m + (size_t)y * mw + (x >> 5)) >> (x & 31)) & 1u);
 }
 
+// row of the whole lattice of an updated local row y
+__device__ __forceinline__ int grow(const Geometry &g, int y) { return y + g.yoff; }
+
 // a mod n in [0, n)
 __device__ __forceinline__ int wrapi(int a, int n) {
   a %= n;

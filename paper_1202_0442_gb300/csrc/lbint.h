@@ -32,8 +32,13 @@ struct OpenDesc {
 };
 
 struct Geometry {
-  int nx, ny, pitch, mw;  // mw = pitch / 32 mask words per row
+  int nx, ny, pitch, mw;  // ny: rows held (a slab: its own rows and its
+                          // ghost rows); mw = pitch / 32 mask words per row
   size_t plane;           // ny * pitch
+  // rows updated [ylo, yhi) (every row of a whole lattice); local row y is
+  // row y + yoff of the whole lattice of gny rows (yoff = 0, gny = ny for
+  // a whole lattice)
+  int ylo, yhi, yoff, gny;
 };
 
 // one iteration of the fluid lattice(s)
@@ -163,6 +168,15 @@ struct ThermoArgs {
   const int *errw;        // or nullptr
 };
 
+// device-to-device copies of up to MAX_RUNS contiguous runs in one launch
+constexpr int MAX_RUNS = 128;
+struct CopyRuns {
+  int n;
+  const void *src[MAX_RUNS];
+  void *dst[MAX_RUNS];
+  unsigned bytes[MAX_RUNS];
+};
+
 // launchers (return the kernel count launched, or -1 on a launch error)
 int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s);
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
@@ -183,6 +197,7 @@ int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);
 constexpr int THERMO_BLOCKS_PER_SM = 4;
 int thermo_blocks(const Geometry &g, int sms);
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s);
+int launch_copy_runs(const CopyRuns &r, cudaStream_t s);
 
 // state conversion between FP64 host-layout arrays [q][ny][nx] and storage
 int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,

@@ -80,7 +80,7 @@ template <int Q>
 __device__ float solute_streamed_C(const SoluteArgs &p, int x, int y) {
   const Geometry &g = p.g;
   if (solid_at(p.mask, g.mw, x, y)) return 0.f;
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
   float gt[Q], Cw;
   int nU;
   uint32_t U, cross;
@@ -166,7 +166,7 @@ __device__ __forceinline__ void solute_node(const SoluteArgs &p, int x, int y, u
                                             float uy) {
   const Geometry &g = p.g;
   const size_t self = (size_t)y * g.pitch + x;
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, y, g.nx, g.ny) : -1;
+  const int k = p.nopen ? opening_of(p.op, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
   float gt[Q], Cw, Cflux = 0.f;
   int nU;
   uint32_t U, cross;

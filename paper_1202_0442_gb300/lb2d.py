@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -65,6 +65,11 @@ SIGNATURES = {
     "lb_launch_count": (I, [P, C.POINTER(C.c_uint64)]),
     "lb_lattice": (I, [P, S, I, I, D]),
     "lb_processors": (I, [P, I, I]),
+    "lb_processor_rank": (I, [P, I]),
+    "lb_halo_size": (I, [P, C.POINTER(SZ)]),
+    "lb_halo_pack": (I, [P, I, P]),
+    "lb_halo_unpack": (I, [P, I, P]),
+    "lb_exchange": (I, [C.POINTER(P), I]),
     "lb_fluids": (I, [P, D, D, D, D]),
     "lb_solute": (I, [P, D, I]),
     "lb_set_storage": (I, [P, I, DP, D]),
@@ -175,6 +180,7 @@ class Lattice:
         self.nx = self.ny = 0
         self.ncomp = 1
         self.q = 0
+        self._py, self._rank = 1, -1
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -201,6 +207,35 @@ class Lattice:
 
     def processors(self, px: int, py: int):
         self._ck(self._L.lb_processors(self._h, px, py))
+        self._py = py
+
+    def processor_rank(self, rank: int):
+        """Hold slab ``rank`` of the lattice split by processors(1, py)."""
+        self._ck(self._L.lb_processor_rank(self._h, rank))
+        self._rank = rank
+
+    @property
+    def rows(self):
+        """(first row, row count) of the rows this context updates and
+        returns: the whole lattice, or its slab."""
+        if self._rank < 0:
+            return 0, self.ny
+        y0 = self._rank * self.ny // self._py
+        return y0, (self._rank + 1) * self.ny // self._py - y0
+
+    def halo_size(self) -> int:
+        n = SZ()
+        self._ck(self._L.lb_halo_size(self._h, C.byref(n)))
+        return n.value
+
+    def halo_pack(self, face: int, buf) -> None:
+        """Rows for the neighbour across ``face`` (0 low y, 1 high y) into
+        the CUDA tensor ``buf`` (halo_size() bytes)."""
+        self._ck(self._L.lb_halo_pack(self._h, face, C.c_void_p(buf.data_ptr())))
+
+    def halo_unpack(self, face: int, buf) -> None:
+        """Ghost rows on ``face`` from the CUDA tensor ``buf``."""
+        self._ck(self._L.lb_halo_unpack(self._h, face, C.c_void_p(buf.data_ptr())))
 
     def fluids(self, tau1: float, tau2: float, alpha1: float = 4 / 9, alpha2: float = 4 / 9):
         self._ck(self._L.lb_fluids(self._h, tau1, tau2, alpha1, alpha2))
@@ -350,7 +385,7 @@ class Lattice:
         return t.as_dict()
 
     def fields(self, fluid: int = 1):
-        sh = (self.ny, self.nx)
+        sh = (self.rows[1], self.nx)
         r, px, py, req = (np.zeros(sh) for _ in range(4))
         self._ck(self._L.lb_get_fields(self._h, fluid, _dp(r), _dp(px), _dp(py), _dp(req)))
         return r, px, py, req
@@ -358,7 +393,7 @@ class Lattice:
     def velocity_f32(self, out=None):
         """Total density and solvent velocity (FP32) of the last iteration;
         ``out`` may be three preallocated (pinned) float32 arrays."""
-        sh = (self.ny, self.nx)
+        sh = (self.rows[1], self.nx)
         if out is None:
             out = tuple(np.zeros(sh, np.float32) for _ in range(3))
         r, u, v = out
@@ -367,20 +402,20 @@ class Lattice:
         return out
 
     def populations(self, fluid: int = 1) -> np.ndarray:
-        a = np.zeros((9, self.ny, self.nx))
+        a = np.zeros((9, self.rows[1], self.nx))
         self._ck(self._L.lb_get_populations(self._h, fluid, _dp(a)))
         return a
 
     def solute_state(self, g=True, Cf=True, b=True):
-        sh = (self.ny, self.nx)
-        ga = np.zeros((self.q, self.ny, self.nx)) if g else None
+        sh = (self.rows[1], self.nx)
+        ga = np.zeros((self.q, self.rows[1], self.nx)) if g else None
         ca = np.zeros(sh) if Cf else None
         ba = np.zeros(sh) if b else None
         self._ck(self._L.lb_get_solute(self._h, _dp(ga), _dp(ca), _dp(ba)))
         return ga, ca, ba
 
     def mask(self) -> np.ndarray:
-        m = np.zeros((self.ny, self.nx), np.uint8)
+        m = np.zeros((self.rows[1], self.nx), np.uint8)
         self._ck(self._L.lb_get_mask(self._h, m.ctypes.data_as(U8P)))
         return m
 
@@ -448,6 +483,16 @@ class Lattice:
         return ux.astype(np.float64), uy.astype(np.float64)
 
 
+def exchange(lattices: Sequence["Lattice"]) -> None:
+    """Halo exchange of the slabs of one lattice held in this process on one
+    device and stream (lattices[r] holds slab r), lb_exchange."""
+    arr = (P * len(lattices))(*[lt.handle for lt in lattices])
+    rc = lattices[0]._L.lb_exchange(arr, len(lattices))
+    if rc != LB_OK:
+        msgs = [lt._L.lb_last_error(lt.handle).decode() for lt in lattices]
+        raise LBError(rc, "lb_exchange: " + " | ".join(m for m in msgs if m))
+
+
 def _buffer(buf):
     if hasattr(buf, "data_ptr"):
         return buf.data_ptr(), buf.numel() * buf.element_size()
@@ -499,12 +544,17 @@ class Batch:
 def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0,
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
                   rounding: str = "nearest", kernel: str = "auto", precise: bool = False,
-                  bind: Optional[dict] = None, step: int = 0) -> Lattice:
+                  bind: Optional[dict] = None, step: int = 0,
+                  slab: Optional[Tuple[int, int]] = None) -> Lattice:
     """Issue the command sequence that sets up workload ``w``.  ``bind``:
     state buffer name -> caller-owned CUDA tensor (Lattice.bind); ``step``:
-    iterations already done (a state that continues another run)."""
+    iterations already done (a state that continues another run); ``slab``:
+    (py, rank) to hold one y slab of the lattice (processors command)."""
     lt = Lattice(device, stream)
     lt.lattice(w.nx, w.ny, w.tau[0])
+    if slab is not None:
+        lt.processors(1, slab[0])
+        lt.processor_rank(slab[1])
     if step:
         lt.set_step(step)
     if w.ncomp == 2:

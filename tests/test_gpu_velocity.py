@@ -44,19 +44,36 @@ def _porous_forced():
     return w
 
 
-def _two_components(forces: bool):
-    w = copy.deepcopy(synth.shan_chen2(1024))
-    if not forces:
-        w.interforce = None
-        w.adhesive = (None, None)
+def _two_components_forced():
+    """The two-component Shan-Chen recipe at 1024^2: interforce G = 0.9 and
+    an adhesive ring (+-0.3) drive the flow."""
+    return synth.shan_chen2(1024)
+
+
+def _two_components_unforced():
+    """Two miscible components (0.6 / 0.4 with +-1 % seeded noise) in the
+    benchmark's disc medium, periodic, no force of any kind: the flow is the
+    decay of the initial density noise."""
+    w = copy.deepcopy(synth.porous())
+    fl = w.solid == 0
+    n1 = synth.noise_field(w.nx, w.ny, 11, -0.01, 0.01)
+    n2 = synth.noise_field(w.nx, w.ny, 12, -0.01, 0.01)
+    w.openings = []
+    w.rho = [np.where(fl, 0.6 * (1 + n1), 0.0), np.where(fl, 0.4 * (1 + n2), 0.0)]
+    w.tau = (0.8, 1.1)
+    w.alpha = (4 / 9, 4 / 9)
+    w.aveforce = ((0.0, 0.0), (0.0, 0.0))
+    w.aveacceleration = ((0.0, 0.0), (0.0, 0.0))
+    w.adhesive = (None, None)
+    w.rho_ref = (0.6, 0.4)
     return w
 
 
 CASES = {
     "porous_pressure": (synth.porous, 30),
     "porous_force": (_porous_forced, 30),
-    "two_components_interforce_adhesion": (lambda: _two_components(True), 10),
-    "two_components_no_force": (lambda: _two_components(False), 10),
+    "two_components_interforce_adhesion": (_two_components_forced, 10),
+    "two_components_no_force": (_two_components_unforced, 10),
 }
 
 
