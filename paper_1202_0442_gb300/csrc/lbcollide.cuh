@@ -49,11 +49,14 @@ __device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, f
 // storage, not ME): h arrives and leaves in the stored units 2^s h, so the
 // loads and stores skip their scale factors; the moments are unscaled once
 // and the equilibrium is formed directly in stored units.  SR: 0 read
-// p.sr_seed, 1 round to nearest, 2 stochastic rounding.
-template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0>
+// p.sr_seed, 1 round to nearest, 2 stochastic rounding.  KEEP (not ME): the
+// nine stored values of each component go to kept[c][0..8] instead of
+// memory, rounded exactly as the stores would round them (the caller
+// stores them, e.g. two nodes' values as pairs).
+template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0, bool KEEP = false>
 __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
                                               float (&h)[NC][9], const float (&Fsc)[NC][2],
-                                              float *uo = nullptr) {
+                                              float *uo = nullptr, S (*kept)[9] = nullptr) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
   // the node's slot in the whole lattice: the random words are the same
@@ -141,10 +144,12 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         const float v = h[c][i] + om * (heq[i] - h[c][i]);
         if (SR == 2) {
           r = r * 1664525u + 1013904223u;
-          if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
+          if (KEEP) kept[c][i] = Store<S>::q_dither(FOLD ? v : v * p.scale, r);
+          else if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
           else Store<S>::st_dither(out, i * P + self, v * p.scale, r);
         } else {
-          Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
+          if (KEEP) kept[c][i] = Store<S>::q(v, FOLD ? 1.0f : p.scale);
+          else Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
         }
       }
     } else if (!ME) {
@@ -154,8 +159,11 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         // dither of the 16-bit stores: one hash per node and component,
         // then a linear congruential sequence (its high bits) per direction
         r = r * 1664525u + 1013904223u;
-        Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale,
-                     p.sr_seed ? (r >> 13) | 1u : 0u);
+        if (KEEP)
+          kept[c][i] = Store<S>::q(h[c][i] + om * (heq[i] - h[c][i]), p.scale, p.sr_seed ? (r >> 13) | 1u : 0u);
+        else
+          Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale,
+                       p.sr_seed ? (r >> 13) | 1u : 0u);
       }
     } else {
       // Mass-exact collision: when |h| is large (two components, or one far

@@ -62,3 +62,21 @@ def test_reference_arm_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2
     assert d["unit"] == "MLUPS" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_lpt_partition_balance():
+    """bench.py's longest-processing-time bin packing of the batch's node
+    counts: every lattice in exactly one bin, the largest load within 4/3 of
+    the lower bound max(total / bins, largest item)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1202_0442_gb300 import synth
+    sizes = [w.nodes for w in synth.batch()]
+    for m in (1, 2, 3, 4, 8):
+        bins = bench.lpt_partition(sizes, m)
+        assert sorted(k for b in bins for k in b) == list(range(len(sizes)))
+        loads = [sum(sizes[k] for k in b) for b in bins]
+        lower = max(sum(sizes) / m, max(sizes))
+        assert max(loads) <= 4 / 3 * lower
+    # 5 -> bin 0, 4 -> bin 1, 3 -> bin 1 (load 4), 3 -> bin 0 (5), 3 -> bin 1 (7)
+    assert bench.lpt_partition([5, 4, 3, 3, 3], 2) == [[0, 3], [1, 2, 4]]

@@ -5,6 +5,7 @@ an invariant, a special case or a value printed in the paper, chosen so
 that a dropped term, a wrong sign or a swapped index in the oracle fails
 one of them.
 """
+import copy
 import os
 
 import numpy as np
@@ -1146,3 +1147,37 @@ def test_growth_choice_is_equiprobable():
             assert abs(c - S * p) < 4 * sd, counts
         for (yy, xx) in block:
             assert yy * 5 + xx not in counts
+
+
+def test_window_of_a_periodic_lattice_is_exact_inside():
+    """The windowed comparison of the 2048^2 Shan-Chen lattice rests on the
+    domain of dependence of the update: pull (one node) plus the interforce
+    and adhesion sums over the neighbours' densities after streaming (one
+    more), so after T iterations a node depends only on nodes within 2T.  A
+    window cut out of the periodic lattice and run as a lattice of its own
+    reproduces the whole lattice's FP64 result bit for bit on nodes more than
+    2T + 2 from its edge (here 192^2, T = 12, a window across the adhesive
+    ring), and not on nodes close to the edge."""
+    from paper_1202_0442_gb300 import synth
+    n, T, core = 192, 12, 10
+    margin = 2 * T + 2
+    size = core + 2 * margin
+    w = synth.shan_chen2(n)
+    whole = oracle_from_workload(w)
+    whole.step(T)
+    x0, y0 = n // 2 + int(round(600 * n / 2048)) - core // 2, n // 2 - core // 2
+    wx, wy = x0 - margin, y0 - margin
+    ys, xs = np.arange(wy, wy + size) % n, np.arange(wx, wx + size) % n
+    cut = copy.deepcopy(w)
+    cut.solid = w.solid[np.ix_(ys, xs)]
+    cut.rho = [r[np.ix_(ys, xs)] for r in w.rho]
+    cut.nx = cut.ny = size
+    win = oracle_from_workload(cut)
+    win.step(T)
+    for c in (0, 1):
+        a = whole.fields(c)[0][np.ix_(ys, xs)]
+        b = win.fields(c)[0]
+        inner = (slice(margin, margin + core),) * 2
+        assert np.array_equal(a[inner], b[inner])
+        assert not np.array_equal(a[:4, :4], b[:4, :4])
+    assert whole.solid()[np.ix_(ys, xs)][margin:margin + core, margin:margin + core].any()
