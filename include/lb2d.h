@@ -368,6 +368,17 @@ int lb_thermo(lb_ctx *ctx, int Nf);
  * does not apply to the setup fails the iteration with LB_E_UNSUPPORTED. */
 int lb_set_kernel(lb_ctx *ctx, const char *name);
 
+/* Clock cycles an mbarrier wait of the TMA kernel may take before the kernel
+ * gives up (failure detection; the paper has no counterpart).  A wait that
+ * runs out sets the context's error word; the CTA then lets the copies it
+ * has already issued land (waiting up to the default limit, about two
+ * seconds at 2 GHz) and returns, so no asynchronous copy is in flight when
+ * it exits.  The next thermo evaluation returns LB_E_TIMEOUT and clears the
+ * word; the state of that iteration is not valid (restore a snapshot).
+ * cycles < 0 restores the default; 0 makes every wait that is not already
+ * complete give up (a test of the path).  Any time. */
+int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles);
+
 /* iteration command: advance Nt iterations.  The first call validates the
  * setup (LB_E_ARG with a message if it is inconsistent) and moves the
  * state to the GPU.  Returns LB_E_NAN if a thermo sum is not finite. */

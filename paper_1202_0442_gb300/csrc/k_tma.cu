@@ -19,9 +19,11 @@
 // per-node arithmetic then lacks the warps to hide its latency.  It is kept
 // as a selectable kernel (lb_set_kernel "tma"); "auto" picks streaming.
 //
-// Every mbarrier wait is bounded: after about two seconds of clock cycles
-// it records the failure in the error word, waits (bounded again) for the
-// copies already issued, and the CTA returns.
+// Every mbarrier wait is bounded by a clock-cycle limit the host sets
+// (lb_set_wait_limit; by default about two seconds): a wait that runs out
+// records the failure in the error word, then waits for the copies already
+// issued with the long default limit, so no copy into shared memory is in
+// flight when the CTA returns.
 #include "lbcollide.cuh"
 
 namespace lbk {
@@ -151,8 +153,11 @@ __device__ __forceinline__ uint32_t mask_word(const uint32_t *m, const Geometry 
   return (w >= 0 && w < g.mw) ? __ldg(m + (size_t)gy * g.mw + w) : 0u;
 }
 
+// the limit of the waits that let issued copies land before a CTA gives up
+constexpr long long DRAIN_LIMIT = 4000000000LL;  // clock cycles (~2 s at 2 GHz)
+
 template <class S, int SR>
-__global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, int *err) {
+__global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, int *err, long long limit) {
   using L = TmaLayout<S>;
   // the same arithmetic as the streaming kernel (scaled 16-bit storage
   // folded, rounding mode SR), so the two agree bit for bit
@@ -168,7 +173,6 @@ __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, 
   const int tiles_x = (g.nx + TT_W - 1) / TT_W, tiles_y = (g.ny + TT_H - 1) / TT_H;
   const int ntiles = tiles_x * tiles_y;
   const int tid = threadIdx.x;
-  const long long limit = 4000000000LL;  // clock cycles (~2 s at 2 GHz)
   const S *fin = (const S *)p.fin;
 
   if (tid == 0) {
@@ -202,8 +206,8 @@ __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, 
     if (__syncthreads_or(!ok)) {
       // record the failure, let the copies already issued land, leave
       if (tid == 0) atomicOr(err, 1);
-      if (pending & 1u) mbar_wait_bounded(&bar[0], phase & 1u, limit);
-      if (pending & 2u) mbar_wait_bounded(&bar[1], (phase >> 1) & 1u, limit);
+      if (pending & 1u) mbar_wait_bounded(&bar[0], phase & 1u, DRAIN_LIMIT);
+      if (pending & 2u) mbar_wait_bounded(&bar[1], (phase >> 1) & 1u, DRAIN_LIMIT);
       return;
     }
     phase ^= 1u << s;
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, 
 }
 
 template <class S>
-int launch_tma_t(const FluidArgs &a, int *err, cudaStream_t s, int sms) {
+int launch_tma_t(const FluidArgs &a, int *err, long long limit, cudaStream_t s, int sms) {
   using L = TmaLayout<S>;
   static bool configured[64] = {};
   int dev = 0;
@@ -268,8 +272,8 @@ int launch_tma_t(const FluidArgs &a, int *err, cudaStream_t s, int sms) {
   const int ntiles = ((a.g.nx + TT_W - 1) / TT_W) * ((a.g.ny + TT_H - 1) / TT_H);
   int grid = sms * per;
   if (grid > ntiles) grid = ntiles;
-  if (a.sr_seed) k_fluid_tma<S, 2><<<grid, TT_THREADS, L::SMEM, s>>>(a, err);
-  else k_fluid_tma<S, 1><<<grid, TT_THREADS, L::SMEM, s>>>(a, err);
+  if (a.sr_seed) k_fluid_tma<S, 2><<<grid, TT_THREADS, L::SMEM, s>>>(a, err, limit);
+  else k_fluid_tma<S, 1><<<grid, TT_THREADS, L::SMEM, s>>>(a, err, limit);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -281,11 +285,12 @@ bool tma_supported(int storage, const Geometry &g) {
   return g.nx % hx == 0 && g.nx >= 2 * hx && (long long)g.plane * 9 < (1LL << 31);
 }
 
-int launch_fluid_tma(int storage, const FluidArgs &a, int *err, cudaStream_t s, int sms) {
+int launch_fluid_tma(int storage, const FluidArgs &a, int *err, long long limit, cudaStream_t s, int sms) {
+  if (limit < 0) limit = DRAIN_LIMIT;
   switch (storage) {
-    case ST_FP16: return launch_tma_t<__half>(a, err, s, sms);
-    case ST_BF16: return launch_tma_t<__nv_bfloat16>(a, err, s, sms);
-    default: return launch_tma_t<float>(a, err, s, sms);
+    case ST_FP16: return launch_tma_t<__half>(a, err, limit, s, sms);
+    case ST_BF16: return launch_tma_t<__nv_bfloat16>(a, err, limit, s, sms);
+    default: return launch_tma_t<float>(a, err, limit, s, sms);
   }
 }
 

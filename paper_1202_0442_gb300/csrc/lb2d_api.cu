@@ -130,6 +130,7 @@ struct lb_ctx {
   int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
                          // 3 fused fluid-solute, 4 two nodes per thread (k_fluid_pair)
   int *errw = nullptr;   // device error word of the TMA kernel
+  long long wait_limit = -1;  // TMA kernel's wait limit in clock cycles (-1: its default)
   int sms = 0;
   bool fields_valid = false;
   int64_t fields_step = -1;  // iteration whose end state the field planes hold
@@ -615,7 +616,12 @@ int run_thermo(lb_ctx *ctx) {
   unsigned long long nfl = 0;
   memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
   const int errw = (int)rec[NTHERMO + 1];
-  if (errw) return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
+  if (errw) {
+    // reported once: the word is cleared for the iterations that follow
+    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
+  }
   lb_thermo_t &T = ctx->thermo;
   memset(&T, 0, sizeof T);
   T.step = ctx->t;
@@ -700,7 +706,7 @@ int one_step(lb_ctx *ctx, bool fields) {
     fa.uout = ctx->bound[5] ? ctx->u : nullptr;
     LAUNCH(launch_fluid_solute(ctx->storage, ctx->qs, fa, sa, s));
   } else if (tma_ok && ctx->kernel == 2) {
-    LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, s, ctx->sms));
+    LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, ctx->wait_limit, s, ctx->sms));
   } else if (pair_ok && ctx->kernel == 4) {
     LAUNCH(launch_fluid_pair(ctx->storage, fa, s));
   } else {
@@ -1406,6 +1412,12 @@ int lb_set_kernel(lb_ctx *ctx, const char *name) {
   else if (!strcmp(name, "fused")) ctx->kernel = 3;
   else if (!strcmp(name, "pair")) ctx->kernel = 4;
   else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming, tma, fused or pair");
+  return LB_OK;
+}
+
+int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles) {
+  NEED_CTX();
+  ctx->wait_limit = cycles < 0 ? -1 : (long long)cycles;
   return LB_OK;
 }
 
@@ -2398,8 +2410,11 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   const double *h = rec;
   unsigned long long nfl = 0;
   memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
-  if ((int)rec[NTHERMO + 1])
+  if ((int)rec[NTHERMO + 1]) {
+    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
+  }
   lb_thermo_t T;
   memset(&T, 0, sizeof T);
   T.step = ctx->t;

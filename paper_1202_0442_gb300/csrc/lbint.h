@@ -189,9 +189,10 @@ int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaSt
 // x-adjacent nodes per thread (k_fluid_pair; same bits as k_fluid_local)
 int launch_fluid_pair(int storage, const FluidArgs &a, cudaStream_t s);
 // persistent TMA-pipelined single-component kernel (k_tma.cu); err is a
-// device word the kernel sets when an mbarrier wait times out
+// device word the kernel sets when an mbarrier wait runs past `limit`
+// clock cycles (negative: the default, about two seconds)
 bool tma_supported(int storage, const Geometry &g);
-int launch_fluid_tma(int storage, const FluidArgs &a, int *err, cudaStream_t s, int sms);
+int launch_fluid_tma(int storage, const FluidArgs &a, int *err, long long limit, cudaStream_t s, int sms);
 // one solute iteration (two kernels with intersolute: concentrations, then the update)
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
 int launch_growth(const GrowthArgs &a, cudaStream_t s);

@@ -104,6 +104,7 @@ SIGNATURES = {
     "lb_intersolute": (I, [P, D, D, D]),
     "lb_adhesiveforce": (I, [P, D, D, D, I]),
     "lb_set_kernel": (I, [P, S]),
+    "lb_set_wait_limit": (I, [P, C.c_int64]),
     "lb_thermo": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
     "lb_get_thermo": (I, [P, C.POINTER(Thermo)]),
@@ -365,6 +366,10 @@ class Lattice:
     # -- output and action -----------------------------------------------------
     def set_kernel(self, name: str = "auto"):
         self._ck(self._L.lb_set_kernel(self._h, _b(name)))
+
+    def set_wait_limit(self, cycles: int = -1):
+        """Clock-cycle limit of the TMA kernel's waits (-1: default)."""
+        self._ck(self._L.lb_set_wait_limit(self._h, int(cycles)))
 
     def thermo(self, Nf: int):
         self._ck(self._L.lb_thermo(self._h, Nf))

@@ -109,3 +109,27 @@ def test_tma_rejects_unsupported_width():
     with pytest.raises(lb2d.LBError) as ei:
         lt.iteration(1)
     assert ei.value.code == lb2d.LB_E_UNSUPPORTED
+
+
+def test_bounded_wait_runs_out_and_recovers():
+    """Failure detection without a GPU fault: with the wait limit at 0 every
+    wait of the TMA kernel that is not already complete gives up; the
+    kernel records it, lets its issued copies land and returns, and the
+    next thermo evaluation reports LB_E_TIMEOUT.  With the default limit
+    restored and the state restored from a snapshot the lattice runs on
+    normally, bit for bit like an undisturbed run."""
+    w = synth.porous(256, 96, seed=4, rmin=4, rmax=10)
+    lt = lb2d.from_workload(w, kernel="tma")
+    ref = lb2d.from_workload(w, kernel="tma")
+    snap = np.zeros(lt.state_size(), np.uint8)
+    lt.save_state(snap)
+    lt.set_wait_limit(0)
+    with pytest.raises(lb2d.LBError) as e:
+        lt.iteration(3)
+    assert e.value.code == lb2d.LB_E_TIMEOUT
+    lt.set_wait_limit(-1)
+    lt.load_state(snap)
+    lt.iteration(7)
+    ref.iteration(7)
+    assert np.array_equal(lt.populations(), ref.populations())
+    assert lt.get_thermo() == ref.get_thermo()
