@@ -179,128 +179,6 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) 
   fluid_node<S, NC, ME, PM, SR>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
 }
 
-// ---------------------------------------------------------------------
-// Two x-adjacent nodes per thread (k_fluid_pair): a warp updates 64
-// consecutive nodes of a row.  Every population plane is read and written
-// as aligned pairs (x0, x0 + 1), x0 even: the planes without an x shift
-// (directions 0, 2, 4) need nothing else; for a shift of +1 (1, 5, 8) the
-// node x0 takes the high value of the pair to its left, which the lane to
-// its left already holds (a warp shuffle), for -1 (3, 6, 7) the node x0 + 1
-// takes the low value of the pair to its right; only the warp's edge lanes
-// and the lattice's x edges (periodic wrap) load that value themselves.
-// Bounce-back reads the node's own pair of the opposite plane.  Per node
-// the arithmetic is k_fluid_local's (collide_store, the same random words),
-// so both kernels give the same bits; the pair kernel issues half the
-// memory instructions and address arithmetic per node.
-// ---------------------------------------------------------------------
-constexpr int PAIR_BY = 8;
-
-__device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
-__device__ __forceinline__ float2 ld2(const __half *p) {
-  return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
-}
-__device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
-  return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
-}
-__device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }
-__device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-__device__ __forceinline__ void st2(float *p, float a, float b) {
-  *reinterpret_cast<float2 *>(p) = make_float2(a, b);
-}
-__device__ __forceinline__ void st2(__half *p, __half a, __half b) {
-  *reinterpret_cast<__half2 *>(p) = __halves2half2(a, b);
-}
-__device__ __forceinline__ void st2(__nv_bfloat16 *p, __nv_bfloat16 a, __nv_bfloat16 b) {
-  *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(a, b);
-}
-
-template <class S, bool PM, int SR>
-__global__ void __launch_bounds__(32 * PAIR_BY, 4) k_fluid_pair(const FluidArgs p) {
-  // scaled 16-bit storage runs folded (stored units throughout), as in
-  // k_fluid_local without the mass-exact collision
-  constexpr bool FOLD = Store<S>::kScaled;
-  const Geometry &g = p.g;
-  const int lane = threadIdx.x;
-  const int x0 = blockIdx.x * 64 + 2 * lane;
-  const int y = g.ylo + blockIdx.y * PAIR_BY + threadIdx.y;
-  if (y >= g.yhi) return;  // warp-uniform
-  const int self = y * g.pitch + x0;
-  // the two nodes' neighbour codes; lanes past the row (pitch not a
-  // multiple of 64) and padding slots read as solid
-  uint32_t bA = 1u << NBPOS(0, 0), bB = bA;
-  if (x0 < g.pitch) {
-    const uint32_t two = __ldg(reinterpret_cast<const uint32_t *>(p.nbc + self));
-    bA = two & 0xffffu;
-    bB = two >> 16;
-  }
-  const bool fA = !((bA >> NBPOS(0, 0)) & 1u), fB = !((bB >> NBPOS(0, 0)) & 1u);
-  const bool act = fA || fB;
-  const unsigned busy = __ballot_sync(0xffffffffu, act);
-  if (!busy) return;
-  const int P = (int)g.plane;
-  S *out = (S *)p.fout;
-  if (!act) {
-    // solid pair: zeros where its 32-byte sector holds a fluid node, so
-    // the warp writes whole sectors (solid slots stay zero)
-    constexpr int LPS = 16 / (int)sizeof(S);  // lanes per 32-byte sector
-    if (x0 < g.pitch && ((busy >> (lane & ~(LPS - 1))) & ((1u << LPS) - 1u))) {
-      const S z = Store<S>::q(0.0f, 1.0f);
-#pragma unroll
-      for (int i = 0; i < 9; i++) st2(out + i * P + self, z, z);
-    }
-  }
-  const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  const S *fin = (const S *)p.fin;
-  float h[2][1][9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
-    const int ex = EX(i), ey = EY(i);
-    const S *row = fin + (size_t)i * P + (size_t)(ey > 0 ? ym : (ey < 0 ? yp : y)) * g.pitch;
-    const float2 v = act ? ld2(row + x0) : make_float2(0.f, 0.f);
-    float a, b;
-    if (ex == 0) {
-      a = v.x;
-      b = v.y;
-    } else if (ex > 0) {
-      // sources x0 - 1 (the left lane's high value) and x0
-      a = __shfl_up_sync(0xffffffffu, v.y, 1);
-      if (act && (lane == 0 || x0 == 0)) a = ld1(row + (x0 == 0 ? g.nx - 1 : x0 - 1));
-      b = v.x;
-    } else {
-      // sources x0 + 1 and x0 + 2 (the right lane's low value), wrapped
-      b = __shfl_down_sync(0xffffffffu, v.x, 1);
-      if (act && (lane == 31 || x0 + 2 >= g.nx)) b = ld1(row + (x0 + 2 >= g.nx ? x0 + 2 - g.nx : x0 + 2));
-      a = (act && x0 + 1 >= g.nx) ? ld1(row) : v.y;
-    }
-    if (i) {
-      // half-way bounce-back: a solid source gives the node's own value of
-      // the opposite direction
-      const bool sA = fA && ((bA >> NBPOS(-ex, -ey)) & 1u), sB = fB && ((bB >> NBPOS(-ex, -ey)) & 1u);
-      if (sA || sB) {
-        const float2 o = ld2(fin + (size_t)OPP(i) * P + self);
-        if (sA) a = o.x;
-        if (sB) b = o.y;
-      }
-    }
-    h[0][0][i] = a;
-    h[1][0][i] = b;
-  }
-  if (!act) return;
-  S kept[2][1][9];
-  const float F[1][2] = {{0.f, 0.f}};
-#pragma unroll
-  for (int n = 0; n < 2; n++) {
-    const bool fl = n ? fB : fA;
-    if (!fl) continue;
-    if (p.nopen) apply_openings<1>(p, x0 + n, y, h[n], FOLD ? p.scale : 1.0f);
-    collide_store<S, 1, false, PM, FOLD, SR, true>(p, x0 + n, y, n ? bB : bA, h[n], F, nullptr, kept[n]);
-  }
-  const S z = Store<S>::q(0.0f, 1.0f);
-#pragma unroll
-  for (int i = 0; i < 9; i++) st2(out + i * P + self, fA ? kept[0][0][i] : z, fB ? kept[1][0][i] : z);
-}
-
 // One fluid and one solute iteration of a single-component lattice in one
 // pass (no intersolute): the solute update of a node needs only its own
 // solvent velocity of this iteration, which stays in registers, and the
@@ -413,7 +291,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
     F[c][0] = -p.G * self * sx;
     F[c][1] = -p.G * self * sy;
   }
-  collide_store<S, NC, true, true>(p, x, y, bits, h, F);
+  collide_store<S, NC, true>(p, x, y, bits, h, F);
 }
 
 template <class S>
@@ -496,34 +374,13 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
         else k_fluid_local<S, 1, false, false, 1><<<grd, blk, 0, s>>>(a);
       }
     } else {
-      k_fluid_local<S, 2, true, true, 0><<<grd, blk, 0, s>>>(a);
+      k_fluid_local<S, 2, true, false, 0><<<grd, blk, 0, s>>>(a);
     }
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
-template <class S>
-int launch_fluid_pair_t(const FluidArgs &a, cudaStream_t s) {
-  dim3 blk(32, PAIR_BY), grd((a.g.pitch + 63) / 64, (a.g.yhi - a.g.ylo + PAIR_BY - 1) / PAIR_BY);
-  if (a.sr_seed) {
-    if (a.pm) k_fluid_pair<S, true, 2><<<grd, blk, 0, s>>>(a);
-    else k_fluid_pair<S, false, 2><<<grd, blk, 0, s>>>(a);
-  } else {
-    if (a.pm) k_fluid_pair<S, true, 1><<<grd, blk, 0, s>>>(a);
-    else k_fluid_pair<S, false, 1><<<grd, blk, 0, s>>>(a);
-  }
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
-}
-
 }  // namespace
-
-int launch_fluid_pair(int storage, const FluidArgs &a, cudaStream_t s) {
-  switch (storage) {
-    case ST_FP16: return launch_fluid_pair_t<__half>(a, s);
-    case ST_BF16: return launch_fluid_pair_t<__nv_bfloat16>(a, s);
-    default: return launch_fluid_pair_t<float>(a, s);
-  }
-}
 
 int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs &a, cudaStream_t s) {
   switch (storage) {

@@ -128,7 +128,7 @@ struct lb_ctx {
   int tblocks = 0;
   int64_t t = 0;
   int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
-                         // 3 fused fluid-solute, 4 two nodes per thread (k_fluid_pair)
+                         // 3 fused fluid-solute
   int *errw = nullptr;   // device error word of the TMA kernel
   long long wait_limit = -1;  // TMA kernel's wait limit in clock cycles (-1: its default)
   int sms = 0;
@@ -661,10 +661,6 @@ int one_step(lb_ctx *ctx, bool fields) {
   if (ctx->kernel == 2 && !tma_ok)
     return ctx->fail(LB_E_UNSUPPORTED, "the TMA kernel runs single-component noslip lattices without "
                      "interforce whose width is a multiple of 4 (FP32) or 8 (16-bit) nodes");
-  const bool pair_ok = ctx->nc == 1 && !ctx->sc && ctx->bstyle == 0;
-  if (ctx->kernel == 4 && !pair_ok)
-    return ctx->fail(LB_E_UNSUPPORTED, "the pair kernel runs single-component lattices without interforce "
-                     "and with noslip walls");
   SoluteArgs sa{};
   if (ctx->qs) {
     sa.g = ctx->g;
@@ -707,8 +703,6 @@ int one_step(lb_ctx *ctx, bool fields) {
     LAUNCH(launch_fluid_solute(ctx->storage, ctx->qs, fa, sa, s));
   } else if (tma_ok && ctx->kernel == 2) {
     LAUNCH(launch_fluid_tma(ctx->storage, fa, ctx->errw, ctx->wait_limit, s, ctx->sms));
-  } else if (pair_ok && ctx->kernel == 4) {
-    LAUNCH(launch_fluid_pair(ctx->storage, fa, s));
   } else {
     LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
   }
@@ -1410,8 +1404,7 @@ int lb_set_kernel(lb_ctx *ctx, const char *name) {
   else if (!strcmp(name, "streaming")) ctx->kernel = 1;
   else if (!strcmp(name, "tma")) ctx->kernel = 2;
   else if (!strcmp(name, "fused")) ctx->kernel = 3;
-  else if (!strcmp(name, "pair")) ctx->kernel = 4;
-  else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming, tma, fused or pair");
+  else return ctx->fail(LB_E_ARG, "kernel must be auto, streaming, tma or fused");
   return LB_OK;
 }
 

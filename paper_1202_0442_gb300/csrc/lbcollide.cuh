@@ -43,20 +43,16 @@ __device__ __forceinline__ void momentum_exact(const float (&f)[9], float &jx, f
 
 // moments, forces, equilibrium velocity, BGK and the stores of one node.
 // Fsc: interforce already evaluated (zero when off).  ME: mass-exact
-// collision (see below).  PM: the momentum as an exact hi + lo sum (the
-// storage flag LB_PRECISE_MOMENTUM for one component; always with two
-// components and interforce).  FOLD (scaled 16-bit
+// collision (see below).  PM: the momentum as an exact hi + lo sum (single
+// component; the storage flag LB_PRECISE_MOMENTUM).  FOLD (scaled 16-bit
 // storage, not ME): h arrives and leaves in the stored units 2^s h, so the
 // loads and stores skip their scale factors; the moments are unscaled once
 // and the equilibrium is formed directly in stored units.  SR: 0 read
-// p.sr_seed, 1 round to nearest, 2 stochastic rounding.  KEEP (not ME): the
-// nine stored values of each component go to kept[c][0..8] instead of
-// memory, rounded exactly as the stores would round them (the caller
-// stores them, e.g. two nodes' values as pairs).
-template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0, bool KEEP = false>
+// p.sr_seed, 1 round to nearest, 2 stochastic rounding.
+template <class S, int NC, bool ME, bool PM = false, bool FOLD = false, int SR = 0>
 __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, uint32_t bits,
                                               float (&h)[NC][9], const float (&Fsc)[NC][2],
-                                              float *uo = nullptr, S (*kept)[9] = nullptr) {
+                                              float *uo = nullptr) {
   const Geometry &g = p.g;
   const int self = y * g.pitch + x;
   // the node's slot in the whole lattice: the random words are the same
@@ -71,7 +67,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     const float(&f)[9] = h[c];
     drho[c] = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8]) * un;
     rho[c] = p.rho_ref[c] + drho[c];
-    if (PM) {
+    if (PM && NC == 1) {
       momentum_exact(f, jx[c], jxl[c], jy[c], jyl[c]);
     } else {
       jx[c] = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
@@ -102,14 +98,12 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     uex[0] = mxt[0] * ir;
     uey[0] = myt[0] * ir;
   } else {
-    // common velocity sum(j/tau) / sum(rho/tau), shifted per component;
-    // with PM each j enters as hi + lo (the pair's sum is j to FP32
-    // precision relative to j itself, not to the populations it came from)
+    // common velocity sum(j/tau) / sum(rho/tau), shifted per component
     float nxs = 0.f, nys = 0.f, den = 0.f;
 #pragma unroll
     for (int c = 0; c < NC; c++) {
-      nxs += (PM ? jx[c] + jxl[c] : jx[c]) * p.omega[c];
-      nys += (PM ? jy[c] + jyl[c] : jy[c]) * p.omega[c];
+      nxs += jx[c] * p.omega[c];
+      nys += jy[c] * p.omega[c];
       den += rho[c] * p.omega[c];
     }
     const float upx = nxs / den, upy = nys / den;
@@ -144,12 +138,10 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         const float v = h[c][i] + om * (heq[i] - h[c][i]);
         if (SR == 2) {
           r = r * 1664525u + 1013904223u;
-          if (KEEP) kept[c][i] = Store<S>::q_dither(FOLD ? v : v * p.scale, r);
-          else if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
+          if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
           else Store<S>::st_dither(out, i * P + self, v * p.scale, r);
         } else {
-          if (KEEP) kept[c][i] = Store<S>::q(v, FOLD ? 1.0f : p.scale);
-          else Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
+          Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
         }
       }
     } else if (!ME) {
@@ -159,11 +151,8 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         // dither of the 16-bit stores: one hash per node and component,
         // then a linear congruential sequence (its high bits) per direction
         r = r * 1664525u + 1013904223u;
-        if (KEEP)
-          kept[c][i] = Store<S>::q(h[c][i] + om * (heq[i] - h[c][i]), p.scale, p.sr_seed ? (r >> 13) | 1u : 0u);
-        else
-          Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale,
-                       p.sr_seed ? (r >> 13) | 1u : 0u);
+        Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), p.scale,
+                     p.sr_seed ? (r >> 13) | 1u : 0u);
       }
     } else {
       // Mass-exact collision: when |h| is large (two components, or one far

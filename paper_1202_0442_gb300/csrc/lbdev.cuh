@@ -47,10 +47,6 @@ __host__ __device__ constexpr int OPP4(int i) { return (i + 2) & 3; }
 template <class S> struct Store;
 template <> struct Store<float> {
   static constexpr bool kScaled = false;  // stored values carry no 2^s factor
-  // the stored value of v, as st / st_dither would write it
-  static __device__ __forceinline__ float q(float v, float) { return v; }
-  static __device__ __forceinline__ float q(float v, float, uint32_t) { return v; }
-  static __device__ __forceinline__ float q_dither(float v, uint32_t) { return v; }
   static __device__ __forceinline__ void st_dither(float *p, size_t k, float v, uint32_t) { p[k] = v; }
   static __device__ __forceinline__ float ld(const float *p, size_t k, float) {
     return __ldg(p + k);
@@ -76,13 +72,6 @@ template <> struct Store<float> {
 // same way every step, which would otherwise act as a steady bias.
 template <> struct Store<__half> {
   static constexpr bool kScaled = true;
-  static __device__ __forceinline__ __half q(float v, float sc) { return __float2half_rn(v * sc); }
-  static __device__ __forceinline__ __half q(float v, float sc, uint32_t r) {
-    return r ? __float2half_rz(__uint_as_float(__float_as_uint(v * sc) + (r & 0x1fffu))) : __float2half_rn(v * sc);
-  }
-  static __device__ __forceinline__ __half q_dither(float v, uint32_t d) {
-    return __float2half_rz(__uint_as_float(__float_as_uint(v) + (d >> 19)));
-  }
   // v already scaled; d: a random word, its top 13 bits dither the 13
   // fraction bits binary16 drops (stochastic rounding)
   static __device__ __forceinline__ void st_dither(__half *p, size_t k, float v, uint32_t d) {
@@ -116,13 +105,6 @@ template <> struct Store<__half> {
 };
 template <> struct Store<__nv_bfloat16> {
   static constexpr bool kScaled = false;
-  static __device__ __forceinline__ __nv_bfloat16 q(float v, float) { return __float2bfloat16_rn(v); }
-  static __device__ __forceinline__ __nv_bfloat16 q(float v, float, uint32_t r) {
-    return r ? __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (r & 0xffffu))) : __float2bfloat16_rn(v);
-  }
-  static __device__ __forceinline__ __nv_bfloat16 q_dither(float v, uint32_t d) {
-    return __float2bfloat16_rz(__uint_as_float(__float_as_uint(v) + (d >> 16)));
-  }
   // d: a random word, its top 16 bits dither the 16 fraction bits bfloat16
   // drops (stochastic rounding)
   static __device__ __forceinline__ void st_dither(__nv_bfloat16 *p, size_t k, float v, uint32_t d) {

@@ -185,9 +185,6 @@ int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
 int launch_fluid_solute(int storage, int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s);
 // neighbour codes of every node slot from the mask (after any mask upload)
 int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s);
-// single-component kernel without interforce or slip that updates two
-// x-adjacent nodes per thread (k_fluid_pair; same bits as k_fluid_local)
-int launch_fluid_pair(int storage, const FluidArgs &a, cudaStream_t s);
 // persistent TMA-pipelined single-component kernel (k_tma.cu); err is a
 // device word the kernel sets when an mbarrier wait runs past `limit`
 // clock cycles (negative: the default, about two seconds)

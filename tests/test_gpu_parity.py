@@ -230,7 +230,7 @@ def test_shan_chen_single_component():
                        tau=(1.0,), interforce=(-120.0, 4.0, 200.0), rho_ref=(200.0,))
     lt, o = run_pair(w, 40)
     assert rel_rho(lt, o, w) < TOL32
-    assert rel_u(lt, o) < 1e-4
+    assert rel_u(lt, o) < TOL32
 
 
 def test_shan_chen_single_with_walls_and_adhesion():
@@ -244,7 +244,7 @@ def test_shan_chen_single_with_walls_and_adhesion():
                        rho_ref=(200.0,))
     lt, o = run_pair(w, 40)
     assert rel_rho(lt, o, w) < TOL32
-    assert rel_u(lt, o) < 1e-4
+    assert rel_u(lt, o) < TOL32
 
 
 def test_shan_chen_two_components_ring():
@@ -254,7 +254,7 @@ def test_shan_chen_two_components_ring():
     lt, o = run_pair(w, 300)
     for c in (1, 2):
         assert rel_rho(lt, o, w, comp=c) < TOL32
-    assert rel_u(lt, o) < 1e-4
+    assert rel_u(lt, o) < TOL32
     errs, tg, to = thermo_err(lt, o, ["mass1", "mass2"])
     assert errs["mass1"] < 1e-9 and errs["mass2"] < 1e-9, errs
 
@@ -439,7 +439,7 @@ def test_slip_two_components(sc):
     lt, o = run_pair(w, 150)
     for c in (1, 2):
         assert rel_rho(lt, o, w, comp=c) < TOL32
-    assert rel_u(lt, o) < (1e-4 if sc else TOL32)
+    assert rel_u(lt, o) < TOL32
     errs, tg, to = thermo_err(lt, o, ["mass1", "mass2"])
     assert errs["mass1"] < 1e-9 and errs["mass2"] < 1e-9, errs
 
