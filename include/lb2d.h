@@ -375,8 +375,8 @@ int lb_set_kernel(lb_ctx *ctx, const char *name);
  * seconds at 2 GHz) and returns, so no asynchronous copy is in flight when
  * it exits.  The next thermo evaluation returns LB_E_TIMEOUT and clears the
  * word; the state of that iteration is not valid (restore a snapshot).
- * cycles < 0 restores the default; 0 makes every wait that is not already
- * complete give up (a test of the path).  Any time. */
+ * cycles < 0 restores the default; 0 makes every CTA give up at its first
+ * wait (a test of the give-up path).  Any time. */
 int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles);
 
 /* iteration command: advance Nt iterations.  The first call validates the

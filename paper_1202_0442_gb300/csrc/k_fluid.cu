@@ -125,8 +125,9 @@ constexpr int LOC_BY = 8;
 // The update of node (x, y) given its neighbour code (called by every lane
 // of a warp: the warp votes on its solid lanes).  Returns false on solid
 // nodes and row padding.  uo, if given, receives the node's solvent
-// velocity of Eq. (4).
-template <class S, int NC, bool ME, bool PM, int SR>
+// velocity of Eq. (4).  SLIP: the slip/mixed/hybrid boundary styles (a
+// compile-time switch: the noslip kernels carry none of its registers).
+template <class S, int NC, bool ME, bool PM, int SR, bool SLIP>
 __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uint32_t bits,
                                            float *uo = nullptr) {
   constexpr bool FOLD = Store<S>::kScaled && !ME;
@@ -157,7 +158,7 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
 #pragma unroll
   for (int c = 0; c < NC; c++)
     pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, linv, h[c]);
-  if (p.slip && (bits & DIAG_BITS)) {
+  if (SLIP && (bits & DIAG_BITS)) {
 #pragma unroll
     for (int c = 0; c < NC; c++)
       slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, linv, h[c]);
@@ -170,27 +171,27 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
   return true;
 }
 
-template <class S, int NC, bool ME, bool PM, int SR>
-__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? 8 : 4) k_fluid_local(const FluidArgs p) {
+template <class S, int NC, bool ME, bool PM, int SR, bool SLIP>
+__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? (SLIP ? 6 : 8) : 4) k_fluid_local(const FluidArgs p) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.yhi) return;
   // x < pitch: the grid covers whole 32-node words
-  fluid_node<S, NC, ME, PM, SR>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
+  fluid_node<S, NC, ME, PM, SR, SLIP>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
 }
 
 // One fluid and one solute iteration of a single-component lattice in one
 // pass (no intersolute): the solute update of a node needs only its own
 // solvent velocity of this iteration, which stays in registers, and the
 // previous iteration's solute populations around it.
-template <class S, int SR, int Q>
+template <class S, int SR, int Q, bool SLIP>
 __global__ void __launch_bounds__(32 * LOC_BY, 4) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.yhi) return;
   const uint32_t bits = __ldg(p.nbc + (size_t)y * p.g.pitch + x);
   float u[2];
-  if (!fluid_node<S, 1, false, false, SR>(p, x, y, bits, u)) return;
+  if (!fluid_node<S, 1, false, false, SR, SLIP>(p, x, y, bits, u)) return;
   solute_node<Q>(sp, x, y, bits, u[0], u[1]);
 }
 
@@ -349,6 +350,13 @@ __global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g) 
   nbc[(size_t)y * g.pitch + x] = (uint16_t)b;
 }
 
+template <class S, int NC, bool ME, bool PM, int SR>
+void launch_local(const FluidArgs &a, cudaStream_t s) {
+  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
+  if (a.slip) k_fluid_local<S, NC, ME, PM, SR, true><<<grd, blk, 0, s>>>(a);
+  else k_fluid_local<S, NC, ME, PM, SR, false><<<grd, blk, 0, s>>>(a);
+}
+
 template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
@@ -361,20 +369,19 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
       else k_fluid_sc<S, 2, false><<<grd, blk, 0, s>>>(a);
     }
   } else {
-    dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
     if (nc == 1) {
       if (me) {
-        if (a.pm) k_fluid_local<S, 1, true, true, 0><<<grd, blk, 0, s>>>(a);
-        else k_fluid_local<S, 1, true, false, 0><<<grd, blk, 0, s>>>(a);
+        if (a.pm) launch_local<S, 1, true, true, 0>(a, s);
+        else launch_local<S, 1, true, false, 0>(a, s);
       } else if (a.sr_seed) {
-        if (a.pm) k_fluid_local<S, 1, false, true, 2><<<grd, blk, 0, s>>>(a);
-        else k_fluid_local<S, 1, false, false, 2><<<grd, blk, 0, s>>>(a);
+        if (a.pm) launch_local<S, 1, false, true, 2>(a, s);
+        else launch_local<S, 1, false, false, 2>(a, s);
       } else {
-        if (a.pm) k_fluid_local<S, 1, false, true, 1><<<grd, blk, 0, s>>>(a);
-        else k_fluid_local<S, 1, false, false, 1><<<grd, blk, 0, s>>>(a);
+        if (a.pm) launch_local<S, 1, false, true, 1>(a, s);
+        else launch_local<S, 1, false, false, 1>(a, s);
       }
     } else {
-      k_fluid_local<S, 2, true, false, 0><<<grd, blk, 0, s>>>(a);
+      launch_local<S, 2, true, false, 0>(a, s);
     }
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
@@ -393,8 +400,13 @@ int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs 
 template <class S, int SR>
 int launch_fluid_solute_t(int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
   dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
-  if (q == 4) k_fluid_solute<S, SR, 4><<<grd, blk, 0, s>>>(a, sa);
-  else k_fluid_solute<S, SR, 9><<<grd, blk, 0, s>>>(a, sa);
+  if (a.slip) {
+    if (q == 4) k_fluid_solute<S, SR, 4, true><<<grd, blk, 0, s>>>(a, sa);
+    else k_fluid_solute<S, SR, 9, true><<<grd, blk, 0, s>>>(a, sa);
+  } else {
+    if (q == 4) k_fluid_solute<S, SR, 4, false><<<grd, blk, 0, s>>>(a, sa);
+    else k_fluid_solute<S, SR, 9, false><<<grd, blk, 0, s>>>(a, sa);
+  }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(TT_THREADS, 3) k_fluid_tma(const FluidArgs p, 
       if (tid < L::ROWS * L::MW)
         mnext = mask_word(p.mask, g, (kn % tiles_x) * TT_W, (kn / tiles_x) * TT_H, tid, L::ROWS, L::MW);
     }
-    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, limit);
+    // limit 0: give up at the first wait (the give-up path on demand; a
+    // blocking try_wait can otherwise see the copies land within its own
+    // suspend time)
+    const bool ok = limit > 0 && mbar_wait_bounded(&bar[s], (phase >> s) & 1u, limit);
     if (__syncthreads_or(!ok)) {
       // record the failure, let the copies already issued land, leave
       if (tid == 0) atomicOr(err, 1);

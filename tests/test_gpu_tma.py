@@ -113,8 +113,8 @@ def test_tma_rejects_unsupported_width():
 
 def test_bounded_wait_runs_out_and_recovers():
     """Failure detection without a GPU fault: with the wait limit at 0 every
-    wait of the TMA kernel that is not already complete gives up; the
-    kernel records it, lets its issued copies land and returns, and the
+    CTA of the TMA kernel gives up at its first wait; it records that, lets
+    its issued copies land and returns, and the
     next thermo evaluation reports LB_E_TIMEOUT.  With the default limit
     restored and the state restored from a snapshot the lattice runs on
     normally, bit for bit like an undisturbed run."""
