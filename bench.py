@@ -43,6 +43,10 @@ sys.path.insert(0, ROOT)
 METRIC = "D2Q9 MLUPS and % of HBM roofline; 16-bit-storage & batched vs plain FP32 at ≤1e-5"
 WORKLOAD = "porous 1024x1024 (random discs r 8-24 seed 1, porosity 0.7, Zou-He rho 1.001/1.0, tau 0.8)"
 BYTES_PER_FLUID_NODE = {"fp32": 72, "fp16": 36, "bf16": 36}
+# measured against the FP64 oracle on this workload after its stated 10 000
+# iterations (tests/long_parity.py); the target for 16-bit storage is 2e-3
+ACCURACY_16 = {"fp16": "rel. u 7.0e-4 after 10 000 iterations: meets 2e-3",
+               "bf16": "rel. u 6.1e-3 after 10 000 iterations: misses 2e-3 (8-bit significand)"}
 
 
 def peaks():
@@ -432,7 +436,7 @@ def variants(args, local, stream, flush, value_fp32):
         t = time_steps(lt, min(args.steps, 60), flush, stream)
         v = w.nodes / (t.mean() * 1e-3) / 1e6
         out[st] = {"value": v, "unit": "MLUPS", "speedup_vs_fp32": v / value_fp32,
-                   "rounding": "stochastic", "tolerance_met": "2e-3 (FP16) / 1e-2 (BF16) rel. u, parity tests",
+                   "rounding": "stochastic", "accuracy": ACCURACY_16[st],
                    "kernel_ms": float(np.median(t))}
         del lt
     # the same recipe at 4096^2 (1.2 GB of FP32 state, far beyond L2, so
@@ -502,7 +506,11 @@ def variants(args, local, stream, flush, value_fp32):
             "speedup": ms_s / ms_b, "ms_per_iteration_batched": ms_b,
             "ms_per_iteration_per_lattice": ms_s, "graph": True,
             "roofline_frac": bpn * fluid / (ms_b * 1e-3) / 1e9 / peak,
-            "state_bytes": int(2 * bpn * nodes)}
+            "state_bytes": int(2 * bpn * nodes),
+            "accuracy": ("rel. u <= 3.8e-6 on 8 sampled lattices after 5000 iterations (exact momentum pairs): meets 1e-5"
+                         if st == "fp32" else
+                         "rel. u 5.8e-4 to 2.6e-2 on 8 sampled lattices after 5000 iterations: "
+                         "misses 2e-3 on the slow ones")}
         del b, lats
     out["batched_fp16"]["speedup_vs_fp32_batched"] = (out["batched"]["ms_per_iteration_batched"]
                                                      / out["batched_fp16"]["ms_per_iteration_batched"])
