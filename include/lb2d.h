@@ -123,8 +123,11 @@ int lb_processors(lb_ctx *ctx, int px, int py);
  * lb_processors(ctx, 1, py) into py y slabs: lattice rows [y0, y0 + n),
  * y0 = floor(rank ny / py), n = floor((rank + 1) ny / py) - y0, plus `halo`
  * ghost rows on each side (1; 2 with interforce or a slip, mixed or hybrid
- * boundary style) that hold the neighbouring slabs' rows (periodic in y:
- * slab py - 1 and slab 0 are neighbours).  rank -1 returns to the whole
+ * boundary style; 3 with surface_reaction, whose slab also updates the two
+ * ghost rows next to its own rows, redundantly, so that precipitation and
+ * growth at its edges need nothing from its neighbours within an
+ * iteration) that hold the neighbouring slabs' rows (periodic in y: slab
+ * py - 1 and slab 0 are neighbours).  rank -1 returns to the whole
  * lattice.  After lb_processors, before the first iteration.
  * Every command of the setup is issued as for the whole lattice (node
  * coordinates, obstacle masks and initial-state arrays [..][ny][nx] of the
@@ -132,13 +135,14 @@ int lb_processors(lb_ctx *ctx, int px, int py);
  * (lb_get_fields, lb_get_velocity_f32, lb_get_populations, lb_get_solute,
  * lb_get_mask) return the slab's own rows, arrays [..][n][nx]; lb_get_thermo
  * sums over the slab's own nodes (the lattice's record is the sum over the
- * slabs).  Each slab draws the same random numbers for a node as the whole
- * lattice does, so after every iteration followed by a halo exchange the
- * slabs hold, bit for bit, the rows of the whole lattice.  A slab of a
+ * slabs; lb_get_flips gives indices into the slab's own rows).  Each slab
+ * draws the same random numbers for a node as the whole lattice does (the
+ * growth pick included), so after every iteration followed by a halo
+ * exchange the slabs hold, bit for bit, the rows of the whole lattice.  A slab of a
  * lattice split into py > 1 advances one iteration per lb_iteration call
  * (LB_E_ORDER for Nt > 1): exchange halos between calls.  Not built for
- * slabs (LB_E_UNSUPPORTED at the first iteration): surface_reaction,
- * intersolute, the TMA kernel, batches.  A slab needs at least
+ * slabs (LB_E_UNSUPPORTED at the first iteration): intersolute, the TMA
+ * kernel, batches.  A slab needs at least
  * max(3, 2 halo) rows (LB_E_ARG). */
 int lb_processor_rank(lb_ctx *ctx, int rank);
 
@@ -146,10 +150,13 @@ int lb_processor_rank(lb_ctx *ctx, int rank);
  * slab of a lattice).  With one ghost row a face carries the populations
  * the pull takes across it: fluid directions 2, 5, 6 (moving to +y) or
  * 4, 7, 8 (to -y) of each component and the solute's (+y or -y) ones, one
- * row each; with two ghost rows every population of two rows.  Layout:
- * planes in order (component, direction; then solute direction), each
- * `halo` rows of round_up(nx, 32) values of the storage type.  After the
- * device state exists (LB_E_ORDER before). */
+ * row each; with two or three ghost rows every population of that many
+ * rows, and with surface_reaction also those rows of the solid mask and
+ * of the FP64 deposits.  Layout: planes in order (component, direction;
+ * then solute direction; then mask words, deposits), each `halo` rows of
+ * round_up(nx, 32) values of the storage type, every part starting at a
+ * multiple of 16 bytes.  After the device state exists (LB_E_ORDER
+ * before). */
 int lb_halo_size(lb_ctx *ctx, size_t *bytes);
 
 /* Copy the slab's own rows that its neighbour across face `face` (0: the

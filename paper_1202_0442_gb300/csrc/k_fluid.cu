@@ -174,8 +174,8 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
 template <class S, int NC, bool ME, bool PM, int SR, bool SLIP>
 __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? (SLIP ? 6 : 8) : 4) k_fluid_local(const FluidArgs p) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
-  if (y >= p.g.yhi) return;
+  const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.chi) return;
   // x < pitch: the grid covers whole 32-node words
   fluid_node<S, NC, ME, PM, SR, SLIP>(p, x, y, __ldg(p.nbc + (size_t)y * p.g.pitch + x));
 }
@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? (SLIP ?
 template <class S, int SR, int Q, bool SLIP>
 __global__ void __launch_bounds__(32 * LOC_BY, 4) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
   const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = p.g.ylo + blockIdx.y * LOC_BY + threadIdx.y;
-  if (y >= p.g.yhi) return;
+  const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
+  if (y >= p.g.chi) return;
   const uint32_t bits = __ldg(p.nbc + (size_t)y * p.g.pitch + x);
   float u[2];
   if (!fluid_node<S, 1, false, false, SR, SLIP>(p, x, y, bits, u)) return;
@@ -207,9 +207,9 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
   __shared__ float sd[NC][SC_TY + 2][SC_TX + 2];
   const Geometry &g = p.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * SC_TX, y0 = g.ylo + blockIdx.y * SC_TY;
+  const int x0 = blockIdx.x * SC_TX, y0 = g.clo + blockIdx.y * SC_TY;
   const int xr = x0 + tx, yr = y0 + ty;
-  const bool real = xr < g.nx && yr < g.yhi;
+  const bool real = xr < g.nx && yr < g.chi;
   const int x = wrapi(xr, g.nx), y = wrapi(yr, g.ny);
   // the node's 3 x 3 solid neighbourhood (lanes past the lattice edge take
   // the wrapped node's)
@@ -312,7 +312,7 @@ __global__ void k_gradient(const GradArgs a) {
     default: x = c; y = g.gny - 1; dy = -1; break;
   }
   y -= g.yoff;  // rows of the whole lattice -> rows held here
-  if (y < g.ylo || y >= g.yhi || solid_at(a.mask, g.mw, x, y)) return;
+  if (y < g.clo || y >= g.chi || solid_at(a.mask, g.mw, x, y)) return;
   const size_t n0 = (size_t)y * g.pitch + x;
   const size_t n1 = (size_t)wrapi(y + dy, g.ny) * g.pitch + wrapi(x + dx, g.nx);
   const size_t n2 = (size_t)wrapi(y + 2 * dy, g.ny) * g.pitch + wrapi(x + 2 * dx, g.nx);
@@ -338,9 +338,9 @@ __global__ void k_gradient(const GradArgs a) {
 
 // neighbour code of every node slot (periodic wrap, as the pull uses);
 // slots past nx are coded solid
-__global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g) {
-  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-  if (y >= g.ny || x >= g.pitch) return;
+__global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g, int r0, int r1) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = r0 + blockIdx.y * 8 + threadIdx.y;
+  if (y >= r1 || x >= g.pitch) return;
   uint32_t b = 1u << NBPOS(0, 0);
   if (x < g.nx) {
     const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
@@ -352,7 +352,7 @@ __global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g) 
 
 template <class S, int NC, bool ME, bool PM, int SR>
 void launch_local(const FluidArgs &a, cudaStream_t s) {
-  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
+  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + LOC_BY - 1) / LOC_BY);
   if (a.slip) k_fluid_local<S, NC, ME, PM, SR, true><<<grd, blk, 0, s>>>(a);
   else k_fluid_local<S, NC, ME, PM, SR, false><<<grd, blk, 0, s>>>(a);
 }
@@ -360,7 +360,7 @@ void launch_local(const FluidArgs &a, cudaStream_t s) {
 template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
-    dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.yhi - a.g.ylo + SC_TY - 1) / SC_TY);
+    dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.chi - a.g.clo + SC_TY - 1) / SC_TY);
     if (a.slip) {
       if (nc == 1) k_fluid_sc<S, 1, true><<<grd, blk, 0, s>>>(a);
       else k_fluid_sc<S, 2, true><<<grd, blk, 0, s>>>(a);
@@ -399,7 +399,7 @@ int launch_fluid(int storage, int nc, bool sc, bool mass_exact, const FluidArgs 
 
 template <class S, int SR>
 int launch_fluid_solute_t(int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
-  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + LOC_BY - 1) / LOC_BY);
+  dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + LOC_BY - 1) / LOC_BY);
   if (a.slip) {
     if (q == 4) k_fluid_solute<S, SR, 4, true><<<grd, blk, 0, s>>>(a, sa);
     else k_fluid_solute<S, SR, 9, true><<<grd, blk, 0, s>>>(a, sa);
@@ -421,9 +421,11 @@ int launch_fluid_solute(int storage, int q, const FluidArgs &a, const SoluteArgs
   }
 }
 
-int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s) {
-  dim3 blk(32, 8), grd(g.pitch / 32, (g.ny + 7) / 8);
-  k_nbcode<<<grd, blk, 0, s>>>(mask, nbc, g);
+int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s, int r0, int r1) {
+  if (r1 < 0) r1 = g.ny;
+  if (r1 <= r0) return 0;
+  dim3 blk(32, 8), grd(g.pitch / 32, (r1 - r0 + 7) / 8);
+  k_nbcode<<<grd, blk, 0, s>>>(mask, nbc, g, r0, r1);
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -313,14 +313,21 @@ int thermo_blocks(const Geometry &g, int sms) {
 namespace {
 
 // contiguous runs copied between device buffers (the halo rows of slabs):
-// run k goes from src[k] to dst[k], bytes[k] of them (16-byte aligned, a
-// multiple of 16); blockIdx.y picks the run
+// run k goes from src[k] to dst[k], bytes[k] of them (a multiple of 4; in
+// 16-byte words where both ends and the size allow); blockIdx.y picks the
+// run
 __global__ void k_copy_runs(const CopyRuns r) {
   const int k = blockIdx.y;
-  const uint4 *s = (const uint4 *)r.src[k];
-  uint4 *d = (uint4 *)r.dst[k];
-  const unsigned n16 = r.bytes[k] >> 4;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x) d[i] = s[i];
+  const unsigned step = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if ((((uintptr_t)r.src[k] | (uintptr_t)r.dst[k] | r.bytes[k]) & 15u) == 0) {
+    const uint4 *s = (const uint4 *)r.src[k];
+    uint4 *d = (uint4 *)r.dst[k];
+    for (unsigned i = i0; i < (r.bytes[k] >> 4); i += step) d[i] = s[i];
+  } else {
+    const uint32_t *s = (const uint32_t *)r.src[k];
+    uint32_t *d = (uint32_t *)r.dst[k];
+    for (unsigned i = i0; i < (r.bytes[k] >> 2); i += step) d[i] = s[i];
+  }
 }
 
 }  // namespace

@@ -40,8 +40,8 @@ template <int Q>
 __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const Geometry &g = p.g;
-  const int y = g.ylo + blockIdx.y * blockDim.y + threadIdx.y;
-  if (y >= g.yhi) return;
+  const int y = g.clo + blockIdx.y * blockDim.y + threadIdx.y;
+  if (y >= g.chi) return;
   const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx) return;
   const size_t self = (size_t)y * g.pitch + x;
@@ -66,8 +66,8 @@ template <int Q>
 __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const Geometry &g = p.g;
-  const int y = g.ylo + blockIdx.y * blockDim.y + threadIdx.y;
-  if (y >= g.yhi) return;
+  const int y = g.clo + blockIdx.y * blockDim.y + threadIdx.y;
+  if (y >= g.chi) return;
   const uint32_t bits = solute_bits(p, x, y);
   if (x >= g.nx || ((bits >> 4) & 1u)) return;
   const size_t self = (size_t)y * g.pitch + x;
@@ -87,9 +87,9 @@ __device__ __forceinline__ uint32_t growth_bits(const GrowthArgs &a, int x, int 
 // without a fluid neighbour are untouched (their b cannot change).
 __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int y = a.rlo + blockIdx.y * blockDim.y + threadIdx.y;
   const Geometry &g = a.g;
-  if (y >= g.ny) return;
+  if (y >= a.rhi) return;
   const uint32_t bits = growth_bits(a, x, y);
   if (x >= g.nx || !((bits >> 4) & 1u) || (bits | (1u << 4)) == 0x1ffu) return;
   const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
     const int ex = q == 4 ? EX4(i) : EX(i), ey = q == 4 ? EY4(i) : EY(i);
     if ((bits >> NBPOS(ex, ey)) & 1u) continue;
     const int xf = ex > 0 ? xp : (ex < 0 ? xm : x), yf = ey > 0 ? yp : (ey < 0 ? ym : y);
-    const int k = a.nopen ? opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) : -1;
+    const int k = a.nopen ? opening_of(a.op, a.nopen, xf, grow(g, yf), g.nx, g.gny) : -1;
     if (k >= 0 && crosses_wall(a.op[k].wall, ex, ey)) continue;
     acc += (double)__ldg(a.db + (size_t)yf * g.pitch + xf);
   }
@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
       const int ex = EX4(d), ey = EY4(d);
       if ((bits >> NBPOS(ex, ey)) & 1u) continue;
       const int xf = ex > 0 ? xp : (ex < 0 ? xm : x), yf = ey > 0 ? yp : (ey < 0 ? ym : y);
-      if (a.nopen && opening_of(a.op, a.nopen, xf, yf, g.nx, g.ny) >= 0) continue;
-      const unsigned int off = (unsigned int)(yf * g.pitch + xf);
+      if (a.nopen && opening_of(a.op, a.nopen, xf, grow(g, yf), g.nx, g.gny) >= 0) continue;
+      // a candidate outside the own rows counts (the slab that owns it
+      // takes the same decision) but is marked unowned
+      const unsigned int off = (yf >= g.ylo && yf < g.yhi) ? (unsigned int)(yf * g.pitch + xf) : 0xffffffffu;
       if (n == 0) c0 = off;
       else if (n == 1) c1 = off;
       else if (n == 2) c2 = off;
@@ -123,11 +125,12 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
       n++;
     }
     if (n) {
-      const uint64_t node = (uint64_t)y * (uint64_t)g.nx + (uint64_t)x;
-      const uint64_t key = a.seed ^ ((uint64_t)a.t * (uint64_t)g.nx * (uint64_t)g.ny + node);
+      // node and lattice size of the whole lattice (a slab decides as it does)
+      const uint64_t node = (uint64_t)grow(g, y) * (uint64_t)g.nx + (uint64_t)x;
+      const uint64_t key = a.seed ^ ((uint64_t)a.t * (uint64_t)g.nx * (uint64_t)g.gny + node);
       const int pick = (int)(splitmix64(key) % (uint64_t)n);
       const unsigned int off = pick == 0 ? c0 : pick == 1 ? c1 : pick == 2 ? c2 : c3;
-      if (atomicExch(a.flip + off, 1u) == 0u) a.flist[atomicAdd(a.fcount, 1u)] = off;
+      if (off != 0xffffffffu && atomicExch(a.flip + off, 1u) == 0u) a.flist[atomicAdd(a.fcount, 1u)] = off;
       b = 0.0;
     }
   }
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
 }  // namespace
 
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
-  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.yhi - a.g.ylo + 7) / 8);
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + 7) / 8);
   int n = 0;
   if (a.inter) {
     if (q == 4) k_solute_pre<4><<<grd, blk, 0, s>>>(a);
@@ -213,7 +216,7 @@ int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
 }
 
 int launch_growth(const GrowthArgs &a, cudaStream_t s) {
-  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.rhi - a.rlo + 7) / 8);
   k_gather_grow<<<grd, blk, 0, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return 1;

@@ -257,8 +257,15 @@ int buffer_index(const char *what) {
 
 // ghost rows on each side of a slab: the pull reaches one row; interforce
 // (the neighbours' densities after this step's streaming) and the slip
-// styles (mirror sources two rows away) reach two
-int slab_halo(const lb_ctx *ctx) { return (ctx->sc || ctx->bstyle != 0) ? 2 : 1; }
+// styles (mirror sources two rows away) reach two; with surface reaction
+// the two ghost rows next to the own rows are updated too (redundantly:
+// the precipitation gathered by the boundary rows' solid nodes and the
+// growth decisions of the solid nodes one row out come from them), which
+// reach a third
+int slab_halo(const lb_ctx *ctx) { return ctx->react ? 3 : (ctx->sc || ctx->bstyle != 0) ? 2 : 1; }
+
+// ghost rows on each side that a slab updates redundantly
+int slab_extra(const lb_ctx *ctx) { return ctx->rank >= 0 && ctx->react ? 2 : 0; }
 
 // rows [y0, y0 + n) of slab `rank` out of py (sizes differ by one at most)
 void slab_rows(const lb_ctx *ctx, int rank, int &y0, int &n) {
@@ -416,7 +423,6 @@ int commit(lb_ctx *ctx) {
   TRY(validate(ctx));
   if (ctx->rank >= 0) {
     // a slab: which parts of the method it holds
-    if (ctx->react) return ctx->fail(LB_E_UNSUPPORTED, "surface_reaction on a slab is not built: run the reactive lattice whole");
     if (ctx->inter) return ctx->fail(LB_E_UNSUPPORTED, "intersolute on a slab is not built: run the lattice whole");
     ctx->halo = slab_halo(ctx);
     slab_rows(ctx, ctx->rank, ctx->sy0, ctx->sny);
@@ -435,6 +441,8 @@ int commit(lb_ctx *ctx) {
   g.ylo = ctx->rank >= 0 ? ctx->halo : 0;
   g.yhi = g.ylo + (ctx->rank >= 0 ? ctx->sny : ctx->ny);
   g.yoff = ctx->rank >= 0 ? ctx->sy0 - ctx->halo : 0;
+  g.clo = g.ylo - slab_extra(ctx);
+  g.chi = g.yhi + slab_extra(ctx);
   const size_t sb = storage_bytes(ctx->storage);
   const size_t fbytes = (size_t)ctx->nc * 9 * g.plane * sb;
   for (int k = 0; k < 2; k++) TRY(dalloc_state(ctx, (uint8_t **)&ctx->fbuf[k], fbytes, k));
@@ -741,6 +749,10 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.b0 = ctx->b0;
       ga2.seed = ctx->seed;
       ga2.t = ctx->t;
+      // solid nodes that gather and decide: the own rows, and for a slab one
+      // ghost row each side (their decisions can turn own-row nodes solid)
+      ga2.rlo = ctx->rank >= 0 ? ctx->g.ylo - 1 : 0;
+      ga2.rhi = ctx->rank >= 0 ? ctx->g.yhi + 1 : ctx->g.ny;
       ga2.q = ctx->qs;
       ga2.nopen = sa.nopen;
       for (int k = 0; k < sa.nopen; k++) ga2.op[k] = sa.op[k];
@@ -1658,7 +1670,7 @@ int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count) {
   std::vector<int64_t> node(n);
   for (unsigned int k = 0; k < n; k++) {
     const int64_t y = off[k] / ctx->g.pitch, x = off[k] - y * ctx->g.pitch;
-    node[k] = y * ctx->nx + x;
+    node[k] = (y - ctx->g.ylo) * ctx->nx + x;  // in the own rows (a slab's)
   }
   std::sort(node.begin(), node.end());
   for (int k = 0; k < (int)n && k < cap; k++) idx[k] = node[k];
@@ -1703,6 +1715,22 @@ void face_runs(lb_ctx *ctx, int face, bool ghost, std::vector<Run> &runs) {
     if (H > 1 || ey == dir)
       runs.push_back({(uint8_t *)ctx->gbuf[ctx->cur] + ((size_t)q * g.plane + r0 * row) * 4, H * row * 4});
   }
+  if (ctx->react) {
+    // growth changes the mask and the deposits: their rows travel too
+    runs.push_back({(uint8_t *)(ctx->mask + r0 * g.mw), H * (size_t)g.mw * 4});
+    runs.push_back({(uint8_t *)(ctx->b + r0 * row), H * row * 8});
+  }
+}
+
+// after ghost rows of a slab with surface reaction changed (face 0, 1 or
+// -1 both), the neighbour codes of the rows whose 3 x 3 neighbourhood
+// reaches them
+int refresh_codes(lb_ctx *ctx, int face) {
+  if (!ctx->react) return LB_OK;
+  const Geometry &g = ctx->g;
+  if (face != 1) LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream, 0, g.ylo + 1));
+  if (face != 0) LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream, g.yhi - 1, g.ny));
+  return LB_OK;
 }
 
 // device-to-device copies src[k] -> dst[k] of bytes[k], MAX_RUNS per launch
@@ -1746,8 +1774,13 @@ int exchange_slabs(lb_ctx *const *ctxs, int n) {
       }
     }
   }
-  return copy_runs(ctxs[0], src, dst, bytes);
+  TRY(copy_runs(ctxs[0], src, dst, bytes));
+  for (int r = 0; r < n; r++) TRY(refresh_codes(ctxs[r], -1));
+  return LB_OK;
 }
+
+// offset of each run in a packed halo message (16-byte aligned)
+size_t pad16(size_t n) { return (n + 15) / 16 * 16; }
 
 }  // namespace
 
@@ -1760,7 +1793,7 @@ int lb_halo_size(lb_ctx *ctx, size_t *bytes) {
   std::vector<Run> runs;
   face_runs(ctx, 1, false, runs);
   size_t n = 0;
-  for (const Run &r : runs) n += r.bytes;
+  for (const Run &r : runs) n += pad16(r.bytes);
   *bytes = n;
   return LB_OK;
 }
@@ -1782,9 +1815,10 @@ static int halo_move(lb_ctx *ctx, int face, void *buf, bool pack) {
     src.push_back(pack ? (const void *)r.p : (const void *)b);
     dst.push_back(pack ? (void *)b : (void *)r.p);
     bytes.push_back(r.bytes);
-    off += r.bytes;
+    off += pad16(r.bytes);
   }
-  return copy_runs(ctx, src, dst, bytes);
+  TRY(copy_runs(ctx, src, dst, bytes));
+  return pack ? LB_OK : refresh_codes(ctx, face);
 }
 
 int lb_halo_pack(lb_ctx *ctx, int face, void *buf) { return halo_move(ctx, face, buf, true); }

@@ -35,10 +35,14 @@ struct Geometry {
   int nx, ny, pitch, mw;  // ny: rows held (a slab: its own rows and its
                           // ghost rows); mw = pitch / 32 mask words per row
   size_t plane;           // ny * pitch
-  // rows updated [ylo, yhi) (every row of a whole lattice); local row y is
-  // row y + yoff of the whole lattice of gny rows (yoff = 0, gny = ny for
-  // a whole lattice)
-  int ylo, yhi, yoff, gny;
+  // own rows [ylo, yhi) (every row of a whole lattice): the rows a
+  // context updates for good, sums (thermo) and reads out; computed rows
+  // [clo, chi) (the own rows, and for a slab with surface reaction also
+  // the two ghost rows on each side next to them, updated redundantly so
+  // that the precipitation and growth of the boundary rows need no
+  // exchange within the iteration); local row y is row y + yoff of the
+  // whole lattice of gny rows (yoff = 0, gny = ny for a whole lattice)
+  int ylo, yhi, clo, chi, yoff, gny;
 };
 
 // one iteration of the fluid lattice(s)
@@ -136,6 +140,9 @@ struct GrowthArgs {
   double bmax, b0;
   uint64_t seed;
   int64_t t;              // 1-based iteration number
+  int rlo, rhi;           // rows whose solid nodes gather and decide (a
+                          // slab: its own rows and one ghost row each side;
+                          // only own-row nodes are turned solid)
   int q;
   int nopen;
   OpenDesc op[MAX_OPEN];
@@ -184,7 +191,9 @@ int launch_gradient(int storage, const GradArgs &a, cudaStream_t s);
 // no intersolute, no exact momentum pairs, streaming kernel)
 int launch_fluid_solute(int storage, int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s);
 // neighbour codes of every node slot from the mask (after any mask upload)
-int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s);
+// (rows [r0, r1) only, r1 < 0: to the last row)
+int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaStream_t s, int r0 = 0,
+                  int r1 = -1);
 // persistent TMA-pipelined single-component kernel (k_tma.cu); err is a
 // device word the kernel sets when an mbarrier wait runs past `limit`
 // clock cycles (negative: the default, about two seconds)

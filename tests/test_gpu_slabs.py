@@ -13,8 +13,8 @@ openings) in 2 and 4 slabs, FP16 storage with stochastic rounding in 3
 uneven slabs, two components with interforce and adhesion (two ghost
 rows), a partial-slip wall (two ghost rows), y-wall openings (velocity,
 pressure and gradient outlets on the first and last slab), a solute
-carried by the flow (fused fluid-solute kernel), a single slab that is its
-own neighbour."""
+carried by the flow (fused fluid-solute kernel), solute with surface
+reaction and growth, a single slab that is its own neighbour."""
 import copy
 
 import numpy as np
@@ -26,7 +26,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-THERMO_KEYS = ("mass1", "mass2", "momx", "momy", "mass_eq1", "solute", "nsolid", "nfluid")
+THERMO_KEYS = ("mass1", "mass2", "momx", "momy", "mass_eq1", "solute", "bsum", "removed1", "removed_solute",
+               "nsolid", "nfluid")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -146,6 +147,29 @@ def test_solute_slabs(q):
     _run(w, 4, 30, check_every=15)
 
 
+@pytest.mark.parametrize("q,py", [(9, 2), (9, 4), (4, 3)])
+def test_reactive_growth_slabs(q, py):
+    """Solute, surface reaction, precipitation and growth (App. C) in slabs:
+    each slab also updates the two ghost rows next to its own rows, so the
+    deposits its boundary solids gather and the growth decisions one row
+    out are its own; the mask and deposit rows travel with the halo.  The
+    slabs' populations, solute, deposits, masks and every step's grown
+    nodes equal the whole lattice's bit for bit."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3, growth_seed=7)
+    whole, slabs = _run(w, py, 120, check_every=40)
+    for _ in range(20):
+        whole.iteration(1)
+        for s in slabs:
+            s.iteration(1)
+        lb2d.exchange(slabs)
+        fw = whole.flips()
+        fs = np.sort(np.concatenate([s.flips() + s.rows[0] * w.nx for s in slabs]))
+        assert np.array_equal(fw, fs)
+    _compare(w, whole, slabs)
+    tw = whole.get_thermo()
+    assert tw["flips"] > 0 and tw["flips"] == sum(s.get_thermo()["flips"] for s in slabs)
+
+
 def test_halo_messages_through_buffers():
     """The exchange through packed device buffers (the messages a
     multi-GPU run sends over NCCL) gives the same bits."""
@@ -199,8 +223,10 @@ def test_slab_errors():
     with pytest.raises(lb2d.LBError) as e:
         lb2d.from_workload(w, slab=(24, 3))
     assert e.value.code == lb2d.LB_E_ARG
-    # surface reaction is not built for slabs
-    r = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8)
+    # intersolute is not built for slabs
+    r = copy.deepcopy(synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8))
+    r.reaction = None
+    r.intersolute = (-0.5, 1.0, 1.0)
     with pytest.raises(lb2d.LBError) as e:
         lb2d.from_workload(r, slab=(2, 0))
     assert e.value.code == lb2d.LB_E_UNSUPPORTED
