@@ -85,20 +85,32 @@ __device__ __forceinline__ uint32_t growth_bits(const GrowthArgs &a, int x, int 
 // seed ^ (t nx ny + node) mod the number of candidates, candidates in the
 // order +x, +y, -x, -y); the pick is flagged once and listed.  Solid nodes
 // without a fluid neighbour are untouched (their b cannot change).
+template <int Q>
 __device__ __forceinline__ void gather_grow_node(const GrowthArgs &a, int x, int y, uint32_t bits) {
   const Geometry &g = a.g;
   const int xm = x ? x - 1 : g.nx - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
   const int ym = y ? y - 1 : g.ny - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
   const size_t self = (size_t)y * g.pitch + x;
-  double acc = 0.0;
-  const int q = a.q;
-  for (int i = (q == 4 ? 0 : 1); i < q; i++) {
-    const int ex = q == 4 ? EX4(i) : EX(i), ey = q == 4 ? EY4(i) : EY(i);
+  // the neighbours' shares, all loads issued before the first addition,
+  // then added in index order (FP64)
+  constexpr int I0 = Q == 4 ? 0 : 1;
+  float share[Q];
+#pragma unroll
+  for (int i = I0; i < Q; i++) {
+    const int ex = Q == 4 ? EX4(i) : EX(i), ey = Q == 4 ? EY4(i) : EY(i);
+    share[i] = 0.f;
     if ((bits >> NBPOS(ex, ey)) & 1u) continue;
     const int xf = ex > 0 ? xp : (ex < 0 ? xm : x), yf = ey > 0 ? yp : (ey < 0 ? ym : y);
     const int k = a.nopen ? opening_of(a.op, a.nopen, xf, grow(g, yf), g.nx, g.gny) : -1;
     if (k >= 0 && crosses_wall(a.op[k].wall, ex, ey)) continue;
-    acc += (double)__ldg(a.db + (size_t)yf * g.pitch + xf);
+    share[i] = __ldg(a.db + (size_t)yf * g.pitch + xf);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int i = I0; i < Q; i++) {
+    const int ex = Q == 4 ? EX4(i) : EX(i), ey = Q == 4 ? EY4(i) : EY(i);
+    if ((bits >> NBPOS(ex, ey)) & 1u) continue;
+    acc += (double)share[i];
   }
   double b = a.b[self] + acc;
   if (b > a.bmax) {
@@ -145,7 +157,8 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
       // a listed node whose fluid neighbours have all turned solid has
       // nothing left to gather
       if ((bits | (1u << 4)) == 0x1ffu) continue;
-      gather_grow_node(a, x, y, bits);
+      if (a.q == 4) gather_grow_node<4>(a, x, y, bits);
+      else gather_grow_node<9>(a, x, y, bits);
     }
     return;
   }
@@ -154,7 +167,8 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
   if (y >= a.rhi) return;
   const uint32_t bits = growth_bits(a, x, y);
   if (x >= g.nx || !((bits >> 4) & 1u) || (bits | (1u << 4)) == 0x1ffu) return;
-  gather_grow_node(a, x, y, bits);
+  if (a.q == 4) gather_grow_node<4>(a, x, y, bits);
+  else gather_grow_node<9>(a, x, y, bits);
 }
 
 // One CTA turns the listed nodes solid: mask bit, b = b0, their fluid and
