@@ -144,24 +144,9 @@ __device__ __forceinline__ void gather_grow_node(const GrowthArgs &a, int x, int
   a.b[self] = b;
 }
 
-// a whole lattice: the listed solid nodes (grid-stride); a slab: every
-// node of the rows [rlo, rhi)
+// every solid node with a fluid neighbour in the rows [rlo, rhi)
 __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
   const Geometry &g = a.g;
-  if (a.blist) {
-    const unsigned n = *a.bcount;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-      const unsigned off = a.blist[k];
-      const int y = (int)(off / (unsigned)g.pitch), x = (int)(off - (unsigned)y * (unsigned)g.pitch);
-      const uint32_t bits = growth_bits(a, x, y);
-      // a listed node whose fluid neighbours have all turned solid has
-      // nothing left to gather
-      if ((bits | (1u << 4)) == 0x1ffu) continue;
-      if (a.q == 4) gather_grow_node<4>(a, x, y, bits);
-      else gather_grow_node<9>(a, x, y, bits);
-    }
-    return;
-  }
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = a.rlo + blockIdx.y * 8 + threadIdx.y;
   if (y >= a.rhi) return;
@@ -185,8 +170,6 @@ __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
     const int y = (int)(self / (size_t)g.pitch), x = (int)(self - (size_t)y * g.pitch);
     a.flip[self] = 0u;
     atomicOr(a.mask + (size_t)y * g.mw + (x >> 5), 1u << (x & 31));
-    // the new solid node has fluid neighbours: it gathers from now on
-    if (a.blist) a.blist[atomicAdd(a.bcount, 1u)] = (unsigned int)self;
     a.b[self] = a.b0;
     for (int c = 0; c < a.nc; c++) {
       S *f = (S *)a.f + (size_t)c * 9 * g.plane;
@@ -251,13 +234,9 @@ int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? n + 1 : -1;
 }
 
-int launch_growth(const GrowthArgs &a, cudaStream_t s, int list_blocks) {
-  if (a.blist) {
-    k_gather_grow<<<list_blocks, 256, 0, s>>>(a);
-  } else {
-    dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.rhi - a.rlo + 7) / 8);
-    k_gather_grow<<<grd, blk, 0, s>>>(a);
-  }
+int launch_growth(const GrowthArgs &a, cudaStream_t s) {
+  dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.rhi - a.rlo + 7) / 8);
+  k_gather_grow<<<grd, blk, 0, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return 1;
 }

@@ -114,9 +114,6 @@ struct lb_ctx {
   float *vstage = nullptr;  // lb_get_velocity_f32 staging (3 planes, kept)
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
-  // solid nodes that gather precipitation (whole reactive lattices): plane
-  // offsets of the solid nodes with a fluid neighbour, and their count
-  unsigned int *blist = nullptr, *bcount = nullptr;
   uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
   // host copy of the device mask words while the two are known to agree
   // (lost once growth may have changed the device mask)
@@ -175,7 +172,6 @@ struct lb_ctx {
 namespace {
 
 int exchange_slabs(lb_ctx *const *ctxs, int n);  // slabs: halo rows (below)
-int upload_boundary_list(lb_ctx *ctx, const std::vector<uint32_t> &m);
 
 int set_device(lb_ctx *ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -483,11 +479,6 @@ int commit(lb_ctx *ctx) {
   LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream));
   ctx->mask_host = m;
   ctx->mask_host_valid = true;
-  if (ctx->react && ctx->rank < 0) {
-    TRY(dalloc(ctx, &ctx->blist, g.plane));
-    TRY(dalloc(ctx, &ctx->bcount, 1));
-    TRY(upload_boundary_list(ctx, m));
-  }
 
   // hybrid boundary style: per-node reflection coefficients (0 on fluid
   // nodes, so nodes that grow solid later are noslip)
@@ -561,31 +552,6 @@ int commit(lb_ctx *ctx) {
     int rc = lb_set_solute_equilibrium(ctx, ctx->paint_C.data(), nullptr, nullptr);
     if (rc != LB_OK) return rc;
   }
-  return LB_OK;
-}
-
-// the solid nodes of a whole reactive lattice that have a fluid node in
-// their 3 x 3 neighbourhood (periodic), from the mask words, to the device
-int upload_boundary_list(lb_ctx *ctx, const std::vector<uint32_t> &m) {
-  const Geometry &g = ctx->g;
-  auto solid = [&](int x, int y) {
-    x = (x + g.nx) % g.nx;
-    y = (y + g.ny) % g.ny;
-    return (m[(size_t)y * g.mw + (x >> 5)] >> (x & 31)) & 1u;
-  };
-  std::vector<unsigned int> list;
-  for (int y = 0; y < g.ny; y++)
-    for (int x = 0; x < g.nx; x++) {
-      if (!solid(x, y)) continue;
-      bool edge = false;
-      for (int dy = -1; dy <= 1 && !edge; dy++)
-        for (int dx = -1; dx <= 1 && !edge; dx++) edge = !solid(x + dx, y + dy);
-      if (edge) list.push_back((unsigned int)((size_t)y * g.pitch + x));
-    }
-  const unsigned int n = (unsigned int)list.size();
-  if (n) CK(cudaMemcpyAsync(ctx->blist, list.data(), n * sizeof(unsigned int), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemcpyAsync(ctx->bcount, &n, sizeof n, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
   return LB_OK;
 }
 
@@ -787,8 +753,6 @@ int one_step(lb_ctx *ctx, bool fields) {
       // ghost row each side (their decisions can turn own-row nodes solid)
       ga2.rlo = ctx->rank >= 0 ? ctx->g.ylo - 1 : 0;
       ga2.rhi = ctx->rank >= 0 ? ctx->g.yhi + 1 : ctx->g.ny;
-      ga2.blist = ctx->blist;
-      ga2.bcount = ctx->bcount;
       ga2.q = ctx->qs;
       ga2.nopen = sa.nopen;
       for (int k = 0; k < sa.nopen; k++) ga2.op[k] = sa.op[k];
@@ -801,7 +765,7 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.gpop = ctx->gbuf[nxt];
       ga2.removed = ctx->removed;
       ga2.nflips = ctx->nflips;
-      LAUNCH(launch_growth(ga2, s, std::max(1, std::min(4 * ctx->sms, (int)((ctx->g.plane + 255) / 256)))));
+      LAUNCH(launch_growth(ga2, s));
       LAUNCH(launch_apply_flips(ctx->storage, ga2, s));
     }
   }
@@ -855,7 +819,7 @@ int lb_destroy(lb_ctx *ctx) {
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout, ctx->tdone,
                   ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
-                  ctx->vstage,  ctx->nbc,   ctx->blist,   ctx->bcount};
+                  ctx->vstage,  ctx->nbc};
   for (void *p : ptrs) {
     bool own = p != nullptr;
     for (int k = 0; k < 6; k++) own = own && p != ctx->bound[k];
@@ -1970,7 +1934,6 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
     LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
     memcpy(ctx->mask_host.data(), mask_src, mbytes);
     ctx->mask_host_valid = true;
-    if (ctx->blist) TRY(upload_boundary_list(ctx, ctx->mask_host));
   }
   ctx->t = (int64_t)h.t;
   if (ctx->fcount) CK(cudaMemsetAsync(ctx->fcount, 0, 2 * sizeof(unsigned int), ctx->stream));

@@ -143,12 +143,6 @@ struct GrowthArgs {
   int rlo, rhi;           // rows whose solid nodes gather and decide (a
                           // slab: its own rows and one ghost row each side;
                           // only own-row nodes are turned solid)
-  // the solid nodes that can gather (a whole lattice): plane offsets of
-  // every solid node with a fluid node in its 3 x 3 neighbourhood, *bcount
-  // of them; the flips append the nodes they turn solid.  nullptr: scan
-  // the rows [rlo, rhi) instead (slabs)
-  unsigned int *blist;
-  unsigned int *bcount;
   int q;
   int nopen;
   OpenDesc op[MAX_OPEN];
@@ -207,7 +201,7 @@ bool tma_supported(int storage, const Geometry &g);
 int launch_fluid_tma(int storage, const FluidArgs &a, int *err, long long limit, cudaStream_t s, int sms);
 // one solute iteration (two kernels with intersolute: concentrations, then the update)
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
-int launch_growth(const GrowthArgs &a, cudaStream_t s, int list_blocks);
+int launch_growth(const GrowthArgs &a, cudaStream_t s);
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);
 // thermo grid: one block per row, at most THERMO_BLOCKS_PER_SM per SM
 constexpr int THERMO_BLOCKS_PER_SM = 4;
