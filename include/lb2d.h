@@ -138,15 +138,19 @@ int lb_processors(lb_ctx *ctx, int px, int py);
  * slabs; lb_get_flips gives indices into the slab's own rows).  Each slab
  * draws the same random numbers for a node as the whole lattice does (the
  * growth pick included), so after every iteration followed by a halo
- * exchange the slabs hold, bit for bit, the rows of the whole lattice.  A slab of a
- * lattice split into py > 1 advances one iteration per lb_iteration call
- * (LB_E_ORDER for Nt > 1): exchange halos between calls.  Not built for
- * slabs (LB_E_UNSUPPORTED at the first iteration): intersolute, the TMA
- * kernel, batches.  A slab needs at least
+ * exchange the slabs hold, bit for bit, the rows of the whole lattice.
+ * A slab of a lattice split into py > 1 advances one iteration per
+ * lb_iteration call (LB_E_ORDER for Nt > 1): exchange halos between calls.
+ * Not built for slabs (LB_E_UNSUPPORTED at the first iteration):
+ * intersolute, the TMA kernel, batches.  A slab needs at least
  * max(3, 2 halo) rows (LB_E_ARG). */
 int lb_processor_rank(lb_ctx *ctx, int rank);
 
-/* Bytes of one halo message of a slab (either face; the same for every
+/* The data the processes of a split lattice exchange after every iteration
+ * (processors command, Sec. Parallelization; the paper does not fix its
+ * form): lb_halo_size, lb_halo_pack, lb_halo_unpack, lb_exchange.
+ *
+ * Bytes of one halo message of a slab (either face; the same for every
  * slab of a lattice).  With one ghost row a face carries the populations
  * the pull takes across it: fluid directions 2, 5, 6 (moving to +y) or
  * 4, 7, 8 (to -y) of each component and the solute's (+y or -y) ones, one
