@@ -11,7 +11,8 @@ flushed (a write of a buffer twice its size, then a read of another) before
 every timed step and each step is timed by CUDA events on the library's
 stream.  e2e: the same metric through the public API with host buffers:
 every step uploads the state snapshot from pinned memory, iterates once
-and downloads density and velocity to pinned memory.
+(producing the node fields, output command) and downloads density and
+velocity to pinned memory.
 --impl reference times the FP64 CPU oracle on the same workload.
 
 Multi-GPU (torchrun), --mode:
@@ -619,7 +620,9 @@ def run_gb300(args, world, rank, local, dist):
     snap = torch.empty(size, dtype=torch.uint8, pin_memory=True)
     lt.save_state(snap)
     outs = tuple(torch.empty((w.ny, w.nx), dtype=torch.float32, pin_memory=True) for _ in range(3))
-    lt.thermo(0)  # every call ends with thermo and fresh node fields
+    # every call ends with fresh node fields (output command), no thermo sums
+    lt.thermo(1 << 30)
+    lt.output(1)
     for _ in range(2):
         lt.load_state(snap)
         lt.iteration(1)

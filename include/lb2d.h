@@ -365,6 +365,13 @@ int lb_intersolute(lb_ctx *ctx, double G, double psi0, double C0);
  * synchronises the stream. */
 int lb_thermo(lb_ctx *ctx, int Nf);
 
+/* output command: produce the node fields (each component's density and
+ * momentum j + F/2, read by lb_get_fields and lb_get_velocity_f32) every Nf
+ * iterations (Nf > 0) without the thermo sums; Nf = 0 (the default) leaves
+ * them to the thermo steps.  The paper's command prints them to a file;
+ * here the caller reads them from the library.  No synchronisation. */
+int lb_output(lb_ctx *ctx, int Nf);
+
 /* Fluid kernel for single-component lattices without interforce:
  * "streaming" (one thread per node, loads straight from HBM; the fastest
  * on GB300), "tma" (a persistent kernel that streams 128 x 4 tiles into

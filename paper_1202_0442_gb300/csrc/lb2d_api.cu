@@ -97,6 +97,7 @@ struct lb_ctx {
   double isG = 0, ispsi0 = 0, isC0 = 0;
   uint64_t seed = 0;
   int nf = 0;
+  int nout = 0;  // output command: node fields every nout iterations (0: off)
   // processors command: a px x py grid of processes; a context given a
   // rank (lb_processor_rank) holds one y slab of the lattice: rows
   // [sy0, sy0 + sny) and `halo` ghost rows on each side
@@ -1426,6 +1427,13 @@ int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles) {
   return LB_OK;
 }
 
+int lb_output(lb_ctx *ctx, int Nf) {
+  NEED_CTX();
+  if (Nf < 0) return ctx->fail(LB_E_ARG, "Nf must be >= 0");
+  ctx->nout = Nf;
+  return LB_OK;
+}
+
 int lb_thermo(lb_ctx *ctx, int Nf) {
   NEED_CTX();
   if (Nf < 0) return ctx->fail(LB_E_ARG, "Nf must be >= 0");
@@ -1452,8 +1460,13 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
                      "rows exchanged between calls", ctx->py);
   for (int k = 1; k <= Nt; k++) {
     const bool thermo = ctx->nf > 0 ? ((ctx->t + 1) % ctx->nf == 0) : (k == Nt);
-    TRY(one_step(ctx, thermo));
+    const bool out = ctx->nout > 0 && (ctx->t + 1) % ctx->nout == 0;
+    TRY(one_step(ctx, thermo || out));
     if (ctx->rank >= 0 && ctx->py == 1) TRY(exchange_slabs(&ctx, 1));
+    if (out && !thermo) {
+      ctx->fields_valid = true;
+      ctx->fields_step = ctx->t;
+    }
     if (thermo) {
       ctx->fields_valid = true;
       ctx->fields_step = ctx->t;
@@ -2388,7 +2401,7 @@ extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   // the field planes must describe the live state: written by the last
   // iteration executed, with no state replaced and no step count set since
   // (mask, deposits and removed mass are read live)
-  if (ctx->fields_step != ctx->t)
+  if (ctx->fields_step != ctx->t || ctx->thermo.step != ctx->t)
     return ctx->fail(LB_E_ORDER, "the node fields are not those of the current state (step %lld): the "
                      "record can be recomputed only after an iteration whose last step is a thermo step",
                      (long long)ctx->t);

@@ -106,6 +106,7 @@ SIGNATURES = {
     "lb_set_kernel": (I, [P, S]),
     "lb_set_wait_limit": (I, [P, C.c_int64]),
     "lb_thermo": (I, [P, I]),
+    "lb_output": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
     "lb_get_thermo": (I, [P, C.POINTER(Thermo)]),
     "lb_thermo_static": (I, [P, C.POINTER(Thermo)]),
@@ -370,6 +371,10 @@ class Lattice:
     def set_wait_limit(self, cycles: int = -1):
         """Clock-cycle limit of the TMA kernel's waits (-1: default)."""
         self._ck(self._L.lb_set_wait_limit(self._h, int(cycles)))
+
+    def output(self, Nf: int):
+        """output command: node fields every Nf iterations (0: off)."""
+        self._ck(self._L.lb_output(self._h, Nf))
 
     def thermo(self, Nf: int):
         self._ck(self._L.lb_thermo(self._h, Nf))

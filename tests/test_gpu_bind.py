@@ -156,3 +156,29 @@ def test_new_entry_point_errors():
     lt.set_step(1000)                      # the step count is the caller's to set
     lt.iteration(1)
     assert lt.get_thermo()["step"] == 1001
+
+
+def test_output_command_fields_without_thermo():
+    """output command: node fields every Nf iterations without the thermo
+    sums; the fields equal those a thermo step writes, bit for bit, and no
+    thermo record exists until a thermo step runs."""
+    w = synth.porous(100, 70, seed=5)
+    a = lb2d.from_workload(w, "fp32")
+    b = lb2d.from_workload(w, "fp32")
+    a.thermo(1 << 30)
+    a.output(1)
+    b.thermo(1)
+    a.iteration(9)
+    b.iteration(9)
+    for x, y in zip(a.velocity_f32(), b.velocity_f32()):
+        assert np.array_equal(x, y)
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+    with pytest.raises(lb2d.LBError) as e:
+        a.get_thermo()
+    assert e.value.code == lb2d.LB_E_ORDER
+    with pytest.raises(lb2d.LBError) as e:
+        a.thermo_static()
+    assert e.value.code == lb2d.LB_E_ORDER
+    with pytest.raises(lb2d.LBError):
+        a.output(-1)
