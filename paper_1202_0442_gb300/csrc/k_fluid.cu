@@ -172,7 +172,8 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
 }
 
 template <class S, int NC, bool ME, bool PM, int SR, bool SLIP>
-__global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? (SLIP ? 6 : 8) : 4) k_fluid_local(const FluidArgs p) {
+__global__ void __launch_bounds__(32 * LOC_BY, ((NC == 1 && !ME && !PM) ? (SLIP ? 6 : 8) : 4) * 8 / LOC_BY)
+    k_fluid_local(const FluidArgs p) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.chi) return;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, (NC == 1 && !ME && !PM) ? (SLIP ?
 // solvent velocity of this iteration, which stays in registers, and the
 // previous iteration's solute populations around it.
 template <class S, int SR, int Q, bool SLIP>
-__global__ void __launch_bounds__(32 * LOC_BY, 4) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
+__global__ void __launch_bounds__(32 * LOC_BY, 4 * 8 / LOC_BY) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.chi) return;
