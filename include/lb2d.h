@@ -508,6 +508,58 @@ int lb_state_size(lb_ctx *ctx, size_t *bytes);
 int lb_save_state(lb_ctx *ctx, void *host, size_t bytes);
 int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes);
 
+/* ---- input-data and restart text files ------------------------------- */
+
+/* write_restart command (Sec. Commands, write_restart; the file layout is
+ * the input-data format of the read_data command): after every iteration
+ * whose step t is a multiple of Nf, lb_iteration writes the state as text
+ * files named "<file>.<t>" (one fluid), "<file>.<t>.fluid1" and
+ * "<file>.<t>.fluid2" (two fluids) and "<file>.<t>.solute" (solute).  A
+ * fluid file holds the sections relaxation_time (tau alpha), domain
+ * (Nx Ny: sites 0..Nx, 0..Ny), processors, inlet/outlet (wall x0 x1 label
+ * style arguments), boundary, field (force/acceleration as e1/e2 values,
+ * interforce, adhesiveforce), density (x y rho style; rho = -11 on solid
+ * sites) and momentum (x y f0 .. f8, the full populations, zero on solid
+ * sites); a solute file holds relaxation_time, inlet/outlet, reaction
+ * (surface kr Cs growth bmax b0 seed), field (intersolute), concentration
+ * (x y C [b]) and solute_modes (x y g_1 .. g_q).  Numbers are written with
+ * 17 significant digits.  Nf = 0 stops writing.  file is copied.  Errors:
+ * LB_E_ARG (Nf < 0, no name; a file that cannot be written is reported by
+ * lb_iteration), LB_E_UNSUPPORTED (a slab). */
+int lb_write_restart(lb_ctx *ctx, const char *file, int Nf);
+/* The same files for the current state, now, named "<file>" (one fluid),
+ * "<file>.fluid1"/".fluid2" and "<file>.solute".  Errors: LB_E_ORDER (no
+ * device state yet), LB_E_ARG (cannot write), LB_E_UNSUPPORTED (a slab). */
+int lb_write_data(lb_ctx *ctx, const char *file);
+/* read_data command (Sec. Commands, read_data): sets up the lattice from
+ * input-data files before the first iteration.  args: NULL or a comma- or
+ * space-separated subset of "fluids" (two fluids: read "<file>.fluid1" and
+ * "<file>.fluid2" instead of "<file>"), "solute" (also read
+ * "<file>.solute") and "equilibrium" (start from the equilibrium of the
+ * densities and velocities read instead of the populations).  The sections
+ * may come in any order but domain before processors, field after
+ * relaxation_time, processors before density and momentum, boundary before
+ * density, reaction before concentration.  A domain section (re)defines
+ * the lattice (as lb_lattice; its relaxation time from the file); the
+ * density section's solid sites replace the mask; openings listed are added
+ * (or, where an opening already lies at the same place, relabelled) and
+ * given their styles; force/acceleration items add to the body forces,
+ * interforce/adhesiveforce/intersolute/reaction items set them; the state
+ * read is applied when the device state is created (a later
+ * position0/momentum0/concentration0 replaces it).  Every site must be
+ * listed in density and, when present, momentum, concentration and
+ * solute_modes; a file without a momentum (solute_modes) section starts at
+ * the equilibrium of its densities (concentrations) at rest.  Errors:
+ * LB_E_ARG (unreadable file, a malformed or misplaced section or line, with
+ * the file and line in lb_last_error), LB_E_ORDER (after the first
+ * iteration; no domain section and no lattice), LB_E_UNSUPPORTED (a slab),
+ * and those of the commands it applies. */
+int lb_read_data(lb_ctx *ctx, const char *file, const char *args);
+/* The lattice as the commands (or read_data) have set it up: nodes nx x ny,
+ * fluid components, solute lattice (0 none, 4 or 9), processor grid.  Any
+ * output pointer may be NULL.  Errors: LB_E_ORDER (no lattice yet). */
+int lb_lattice_info(lb_ctx *ctx, int *nx, int *ny, int *ncomp, int *q, int *px, int *py);
+
 /* ---- batched lattices ------------------------------------------------ */
 
 /* Group n committed single-component contexts of one device and stream

@@ -477,6 +477,13 @@ int orc_set_reaction(orc_t *o, double kr, double Cs, double b0, double bmax,
 
 long orc_time(const orc_t *o) { return o->t; }
 
+/* the step counter (a run resumed from a restart file continues its count) */
+int orc_set_time(orc_t *o, long t) {
+  if (t < 0) return -1;
+  o->t = t;
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* inlet/outlet rules (inlet_momentum/outlet_momentum commands, App. A) */
 /* ------------------------------------------------------------------ */

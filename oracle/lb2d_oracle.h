@@ -95,6 +95,7 @@ int orc_set_reaction(orc_t *o, double kr, double Cs, double b0,
 
 int  orc_step(orc_t *o);
 long orc_time(const orc_t *o);
+int  orc_set_time(orc_t *o, long t);
 
 /* fields of the last iteration: density, physical momentum density
  * (j + F/2) and the equilibrium density of each component */

@@ -90,6 +90,7 @@ def _load():
         "orc_set_reaction": (I, [P, D, D, D, D, U64]),
         "orc_step": (I, [P]),
         "orc_time": (C.c_long, [P]),
+        "orc_set_time": (I, [P, C.c_long]),
         "orc_get_fields": (I, [P, I, dp, dp, dp, dp]),
         "orc_get_solute_C": (I, [P, dp]),
         "orc_get_thermo": (I, [P, dp]),
@@ -293,6 +294,10 @@ class Oracle:
     @property
     def t(self) -> int:
         return int(self._l.orc_time(self._h))
+
+    def set_t(self, t: int):
+        """Step counter (a run resumed from a restart file continues it)."""
+        _check(self._l.orc_set_time(self._h, t), "time")
 
     def fields(self, comp: int = 0):
         sh = (self.ny, self.nx)

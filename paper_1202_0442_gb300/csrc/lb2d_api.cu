@@ -20,20 +20,12 @@
 
 #include "lb2d.h"
 #include "lbbatch.h"
+#include "lbctx.h"
 #include "lbint.h"
 
 using namespace lbk;
 
 namespace {
-
-struct Opening {
-  int wall = 0, a0 = 0, a1 = 0, kind = 0;
-  std::string label[2];
-  int style[2] = {OPEN_NONE, OPEN_NONE};
-  double v[2] = {0, 0}, rho[2] = {1, 1};
-  int sstyle = SOL_NONE;
-  double C = 0, sv = 0;  // dirichlet C or flux C0; flux velocity
-};
 
 const double W9D[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                        1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -53,124 +45,13 @@ int wall_of(const char *s) {
 
 size_t storage_bytes(int st) { return st == ST_FP32 ? 4 : 2; }
 
-}  // namespace
-
-
-struct lb_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  uint64_t launches = 0;
-
-  // command state
-  bool have_lattice = false, have_style = false, have_region = false;
-  bool momentum_cmd = false, committed = false;
-  int nx = 0, ny = 0, nc = 1;
-  double tau[2] = {1, 1};
-  double alpha[2] = {4.0 / 9.0, 4.0 / 9.0};  // fluids command, density-ratio parameter
-  int qs = 0;
-  double taus = 1.0;
-  int storage = ST_FP32;
-  bool sr = false;
-  bool pm = false;  // LB_PRECISE_MOMENTUM
-  double rho_ref[2] = {1, 1};
-  float scale = 1.f, inv_scale = 1.f;
-  std::vector<uint8_t> solid, region;
-  // boundary_style: 0 noslip, 1 slip, 2 mixed (slipR), 3 hybrid (Rh per
-  // solid node and component, from the styled obstacle calls)
-  int bstyle = 0;
-  double slipR = 0.0;
-  std::vector<float> Rh[2];
-  float *Rmap = nullptr;
-  std::vector<double> paint_f[2], paint_C;
-  bool painted_f[2] = {false, false}, painted_C = false;
-  bool state_set[2] = {false, false}, solute_set = false;
-  double fave[2][2] = {{0, 0}, {0, 0}}, acc[2][2] = {{0, 0}, {0, 0}};
-  bool ads[2] = {false, false};
-  double Gads[2] = {0, 0}, ads_psi0[2] = {0, 0}, ads_rho0[2] = {0, 0};
-  bool sc = false;
-  double G = 0, psi0 = 0, sc_rho0 = 0;
-  std::vector<Opening> open;
-  bool react = false;
-  double kr = 0, Cs = 0, b0 = 0, bmax = 0;
-  bool inter = false;  // intersolute command
-  double isG = 0, ispsi0 = 0, isC0 = 0;
-  uint64_t seed = 0;
-  int nf = 0;
-  int nout = 0;  // output command: node fields every nout iterations (0: off)
-  // processors command: a px x py grid of processes; a context given a
-  // rank (lb_processor_rank) holds one y slab of the lattice: rows
-  // [sy0, sy0 + sny) and `halo` ghost rows on each side
-  int px = 1, py = 1;
-  int rank = -1;  // -1: the whole lattice
-  int halo = 0, sy0 = 0, sny = 0;
-
-  // device state
-  Geometry g{};
-  void *fbuf[2] = {nullptr, nullptr};
-  int cur = 0;
-  uint32_t *mask = nullptr;
-  float *fields = nullptr, *u = nullptr, *gbuf[2] = {nullptr, nullptr};
-  float *Cfield = nullptr, *db = nullptr, *Cpre = nullptr;
-  float *vstage = nullptr;  // lb_get_velocity_f32 staging (3 planes, kept)
-  double *b = nullptr, *removed = nullptr;
-  unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
-  uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
-  // host copy of the device mask words while the two are known to agree
-  // (lost once growth may have changed the device mask)
-  std::vector<uint32_t> mask_host;
-  bool mask_host_valid = false;
-  // caller-owned device buffers (lb_bind): f0, f1, g0, g1, fields, u
-  void *bound[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t bound_bytes[6] = {0, 0, 0, 0, 0, 0};
-  unsigned long long *nflips = nullptr;
-  double *partials = nullptr, *tout = nullptr;
-  unsigned int *tdone = nullptr;  // thermo blocks finished (reset by the last)
-  int tblocks = 0;
-  int64_t t = 0;
-  int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
-                         // 3 fused fluid-solute
-  int *errw = nullptr;   // device error word of the TMA kernel
-  long long wait_limit = -1;  // TMA kernel's wait limit in clock cycles (-1: its default)
-  int sms = 0;
-  bool fields_valid = false;
-  int64_t fields_step = -1;  // iteration whose end state the field planes hold
-  lb_thermo_t thermo{};
-  bool thermo_valid = false;
-
-  int fail(int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    err = buf;
-    return code;
-  }
-  int cuda_fail(cudaError_t e, const char *what) {
-    return fail(LB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
-  }
-};
-
-#define CK(call)                                                   \
-  do {                                                             \
-    cudaError_t e_ = (call);                                       \
-    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call);       \
-  } while (0)
-
-#define LAUNCH(expr)                                                              \
-  do {                                                                            \
-    int n_ = (expr);                                                              \
-    if (n_ < 0) return ctx->cuda_fail(cudaGetLastError(), "kernel launch");       \
-    ctx->launches += (uint64_t)n_;                                                \
-  } while (0)
-
-#define NEED_CTX()                              \
-  do {                                          \
-    if (!ctx) return LB_E_ARG;                  \
-  } while (0)
-
-namespace {
+// equilibrium population i at density rho and velocity (ux, uy) (FP64,
+// host side), with the density-ratio rest share of the fluids command
+double feq_host(int i, double rho, double ux, double uy, double alpha) {
+  const double usq = ux * ux + uy * uy, eu = EXD[i] * ux + EYD[i] * uy;
+  return alpha == 4.0 / 9.0 ? W9D[i] * rho * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * usq)
+                            : wshare(i, alpha) * rho + W9D[i] * rho * (3 * eu + 4.5 * eu * eu - 1.5 * usq);
+}
 
 int exchange_slabs(lb_ctx *const *ctxs, int n);  // slabs: halo rows (below)
 
@@ -325,7 +206,7 @@ size_t buffer_bytes(const lb_ctx *ctx, int k) {
 
 template <class T>
 int dalloc(lb_ctx *ctx, T **p, size_t n) {
-  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) ? n * sizeof(T) : 1);
+  cudaError_t e = cudaMalloc((void **)p, n > 0 ? n * sizeof(T) : 1);
   if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "cudaMalloc(%zu): %s", n * sizeof(T), cudaGetErrorString(e));
   e = cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
@@ -346,11 +227,6 @@ int dalloc_state(lb_ctx *ctx, T **p, size_t n, int k) {
   return LB_OK;
 }
 
-#define TRY(x)               \
-  do {                       \
-    int r_ = (x);            \
-    if (r_ != LB_OK) return r_; \
-  } while (0)
 
 int validate(lb_ctx *ctx) {
   const int nx = ctx->nx, ny = ctx->ny;
@@ -512,10 +388,14 @@ int commit(lb_ctx *ctx) {
   for (int c = 0; c < ctx->nc; c++) {
     if (!ctx->painted_f[c]) continue;
     std::vector<double> f = ctx->paint_f[c];
+    const std::vector<uint8_t> &base = ctx->paint_base[c];
     for (const Opening &o : ctx->open) {
       for (int a = o.a0; a <= o.a1; a++) {
         int x, y;
         node_of_open(ctx, o, a, x, y);
+        // an opening node that still holds the populations read by
+        // read_data keeps them (position0 does not reinitialise openings)
+        if (!base.empty() && base[(size_t)y * g.nx + x]) continue;
         double v = 0.0;
         if (o.style[c] == OPEN_UNIFORM) v = o.v[c];
         if (o.style[c] == OPEN_POISEUILLE) {
@@ -528,13 +408,8 @@ int commit(lb_ctx *ctx) {
         if (o.wall == 1) ux = -sgn * v;
         if (o.wall == 2) uy = sgn * v;
         if (o.wall == 3) uy = -sgn * v;
-        double r = o.rho[c], usq = ux * ux + uy * uy;
-        for (int i = 0; i < 9; i++) {
-          double eu = EXD[i] * ux + EYD[i] * uy;
-          f[(size_t)i * nn + (size_t)y * g.nx + x] =
-              ctx->alpha[c] == 4.0 / 9.0 ? W9D[i] * r * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * usq)
-                                         : wshare(i, ctx->alpha[c]) * r + W9D[i] * r * (3 * eu + 4.5 * eu * eu - 1.5 * usq);
-        }
+        for (int i = 0; i < 9; i++)
+          f[(size_t)i * nn + (size_t)y * g.nx + x] = feq_host(i, o.rho[c], ux, uy, ctx->alpha[c]);
       }
     }
     for (size_t n = 0; n < nn; n++) {
@@ -552,6 +427,21 @@ int commit(lb_ctx *ctx) {
   if (ctx->qs && ctx->painted_C) {
     int rc = lb_set_solute_equilibrium(ctx, ctx->paint_C.data(), nullptr, nullptr);
     if (rc != LB_OK) return rc;
+  }
+  // state read from input-data files (read_data command)
+  for (int c = 0; c < ctx->nc; c++) {
+    lb_ctx::ReadState &r = ctx->rf[c];
+    if (r.kind == 1) TRY(lb_set_populations(ctx, c + 1, r.a.data()));
+    if (r.kind == 2) TRY(lb_set_equilibrium(ctx, c + 1, r.a.data(), r.ux.data(), r.uy.data()));
+    r = lb_ctx::ReadState();
+  }
+  if (ctx->qs && ctx->rg.kind == 1) TRY(lb_set_solute_populations(ctx, ctx->rg.a.data()));
+  if (ctx->qs && ctx->rg.kind == 2)
+    TRY(lb_set_solute_equilibrium(ctx, ctx->rg.a.data(), ctx->rg.ux.data(), ctx->rg.uy.data()));
+  ctx->rg = lb_ctx::ReadState();
+  if (!ctx->rb.empty()) {
+    if (ctx->react) TRY(lb_set_precipitate(ctx, ctx->rb.data()));
+    std::vector<double>().swap(ctx->rb);
   }
   return LB_OK;
 }
@@ -860,9 +750,11 @@ int lb_lattice(lb_ctx *ctx, const char *style, int nx, int ny, double tau) {
   // allocated by the first command that paints
   for (int c = 0; c < 2; c++) {
     ctx->paint_f[c].clear();
+    ctx->paint_base[c].clear();
     ctx->painted_f[c] = false;
   }
   ctx->paint_C.clear();
+  ctx->paint_base_C.clear();
   return LB_OK;
 }
 
@@ -1230,11 +1122,32 @@ int lb_momentum0(lb_ctx *ctx, int mode, double value, int fluid) {
   if (!ctx->have_region) return ctx->fail(LB_E_ORDER, "momentum0 must follow position0");
   if (mode < 0 || mode > 8 || !fluid_ok(ctx, fluid)) return ctx->fail(LB_E_ARG, "bad mode or fluid");
   const size_t nn = ctx->region.size();
-  std::vector<double> &f = ctx->paint_f[fluid - 1];
-  if (f.empty()) f.assign(9 * nn, 0.0);
+  const int c = fluid - 1;
+  std::vector<double> &f = ctx->paint_f[c];
+  std::vector<uint8_t> &base = ctx->paint_base[c];
+  if (f.empty()) {
+    // after read_data the painting starts from the state read: only the
+    // nodes position0 marks are reinitialised (the first momentum0 that
+    // reaches a node clears the populations read there)
+    lb_ctx::ReadState &r = ctx->rf[c];
+    f.assign(9 * nn, 0.0);
+    base.clear();
+    if (r.kind) base.assign(nn, 1);
+    if (r.kind == 1) f = r.a;
+    if (r.kind == 2)
+      for (size_t n = 0; n < nn; n++)
+        for (int i = 0; i < 9; i++) f[(size_t)i * nn + n] = feq_host(i, r.a[n], r.ux[n], r.uy[n], ctx->alpha[c]);
+    r = lb_ctx::ReadState();
+  }
   for (size_t n = 0; n < nn; n++)
-    if (ctx->region[n]) f[(size_t)mode * nn + n] += value;
-  ctx->painted_f[fluid - 1] = true;
+    if (ctx->region[n]) {
+      if (!base.empty() && base[n]) {
+        for (int i = 0; i < 9; i++) f[(size_t)i * nn + n] = 0.0;
+        base[n] = 0;
+      }
+      f[(size_t)mode * nn + n] += value;
+    }
+  ctx->painted_f[c] = true;
   ctx->momentum_cmd = true;
   return LB_OK;
 }
@@ -1244,9 +1157,29 @@ int lb_concentration0(lb_ctx *ctx, double value) {
   TRY(paint_check(ctx));
   if (!ctx->have_region) return ctx->fail(LB_E_ORDER, "concentration0 must follow position0");
   if (!ctx->qs) return ctx->fail(LB_E_ORDER, "concentration0 needs the solute command");
-  if (ctx->paint_C.empty()) ctx->paint_C.assign(ctx->region.size(), 0.0);
-  for (size_t n = 0; n < ctx->region.size(); n++)
-    if (ctx->region[n]) ctx->paint_C[n] += value;
+  const size_t nn = ctx->region.size();
+  std::vector<uint8_t> &base = ctx->paint_base_C;
+  if (ctx->paint_C.empty()) {
+    // after read_data the painting starts from the concentrations read (the
+    // solute then starts at their equilibrium at rest)
+    lb_ctx::ReadState &r = ctx->rg;
+    ctx->paint_C.assign(nn, 0.0);
+    base.clear();
+    if (r.kind) base.assign(nn, 1);
+    if (r.kind == 1)
+      for (size_t n = 0; n < nn; n++)
+        for (int i = 0; i < ctx->qs; i++) ctx->paint_C[n] += r.a[(size_t)i * nn + n];
+    if (r.kind == 2) ctx->paint_C = r.a;
+    r = lb_ctx::ReadState();
+  }
+  for (size_t n = 0; n < nn; n++)
+    if (ctx->region[n]) {
+      if (!base.empty() && base[n]) {
+        ctx->paint_C[n] = 0.0;
+        base[n] = 0;
+      }
+      ctx->paint_C[n] += value;
+    }
   ctx->painted_C = true;
   return LB_OK;
 }
@@ -1446,10 +1379,12 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
   if (Nt < 0) return ctx->fail(LB_E_ARG, "Nt must be >= 0");
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   for (int c = 0; c < ctx->nc; c++)
-    if (!ctx->painted_f[c] && !ctx->state_set[c])
-      return ctx->fail(LB_E_ORDER, "fluid %d has no initial state (position0/momentum0 or lb_set_equilibrium)", c + 1);
-  if (ctx->qs && !ctx->painted_C && !ctx->solute_set)
-    return ctx->fail(LB_E_ORDER, "solute has no initial state (concentration0 or lb_set_solute_equilibrium)");
+    if (!ctx->painted_f[c] && !ctx->state_set[c] && !ctx->rf[c].kind)
+      return ctx->fail(LB_E_ORDER, "fluid %d has no initial state (position0/momentum0, read_data or "
+                       "lb_set_equilibrium)", c + 1);
+  if (ctx->qs && !ctx->painted_C && !ctx->solute_set && !ctx->rg.kind)
+    return ctx->fail(LB_E_ORDER, "solute has no initial state (concentration0, read_data or "
+                     "lb_set_solute_equilibrium)");
   TRY(commit(ctx));
   TRY(set_device(ctx));
   // a slab reads its ghost rows every iteration: with other slabs they are
@@ -1472,6 +1407,9 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
       ctx->fields_step = ctx->t;
       TRY(run_thermo(ctx));
     }
+    // write_restart: the state after this iteration, "<file>.<t>"
+    if (ctx->restart_nf > 0 && ctx->t % ctx->restart_nf == 0)
+      TRY(write_data_files(ctx, ctx->restart_file + "." + std::to_string((long long)ctx->t)));
   }
   return LB_OK;
 }

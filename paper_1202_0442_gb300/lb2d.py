@@ -123,6 +123,11 @@ SIGNATURES = {
     "lb_state_size": (I, [P, C.POINTER(C.c_size_t)]),
     "lb_save_state": (I, [P, P, SZ]),
     "lb_load_state": (I, [P, P, SZ]),
+    "lb_write_restart": (I, [P, S, I]),
+    "lb_write_data": (I, [P, S]),
+    "lb_read_data": (I, [P, S, S]),
+    "lb_lattice_info": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I),
+                            C.POINTER(I)]),
     "lb_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
     "lb_batch_destroy": (I, [P]),
     "lb_batch_iteration": (I, [P, I, I]),
@@ -480,6 +485,22 @@ class Lattice:
     def load_state(self, buf) -> None:
         ptr, n = _buffer(buf)
         self._ck(self._L.lb_load_state(self._h, C.c_void_p(ptr), n))
+
+    def write_restart(self, file: str, Nf: int) -> None:
+        """write_restart command: input-data text files "<file>.<t>" (plus
+        ".fluid1"/".fluid2", ".solute") every Nf iterations; 0 stops."""
+        self._ck(self._L.lb_write_restart(self._h, _b(file), Nf))
+
+    def write_data(self, file: str) -> None:
+        """The current state as input-data text files named after ``file``."""
+        self._ck(self._L.lb_write_data(self._h, _b(file)))
+
+    def read_data(self, file: str, *args: str) -> None:
+        """read_data command: args from "fluids", "solute", "equilibrium"."""
+        self._ck(self._L.lb_read_data(self._h, _b(file), _b(",".join(args)) if args else None))
+        v = [I() for _ in range(6)]
+        self._ck(self._L.lb_lattice_info(self._h, *[C.byref(x) for x in v]))
+        self.nx, self.ny, self.ncomp, self.q, _, self._py = (x.value for x in v)
 
     def launch_count(self) -> int:
         n = C.c_uint64()
