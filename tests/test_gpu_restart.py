@@ -7,8 +7,10 @@ write_restart commands, Sec. Commands), against the oracle's own reader.
   reader from the same file (FP32 storage: the populations to the FP32
   rounding of their deviations; after the run, rho and u to 1e-5).
 - The library writes its state (write_data / write_restart) for one fluid
-  with openings, two fluids with interforce and adhesion, and a solute with
-  surface reaction and growth (D2Q9 and D2Q4); the oracle's reader takes the
+  with openings, two fluids with interforce and adhesion, two fluids under
+  the hybrid boundary style (per-site styles per fluid), a channel under the
+  mixed style, and a solute with surface reaction and growth (D2Q9 and
+  D2Q4); the oracle's reader takes the
   files and must hold exactly the populations, solute modes, deposits and
   mask the library exports; both then continue and agree to 1e-5 (growth
   decisions equal).
@@ -111,6 +113,33 @@ def _reactive(q):
     return synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3, growth_seed=7)
 
 
+def _hybrid_two_fluids():
+    """hybrid boundary style: per-site coefficients per fluid (noslip/slip
+    for fluid 1, noslip/mixed 0.5 for fluid 2) with interforce"""
+    nx, ny = 64, 48
+    mask = synth.random_mask(nx, ny, 5, 0.15)
+    rng = np.random.default_rng(7)
+    R1 = rng.choice([0.0, 1.0], size=(ny, nx))
+    R2 = rng.choice([0.0, 0.5], size=(ny, nx))
+    r1 = np.where(mask, 0, synth.noise_field(nx, ny, 1, 0.6, 0.8))
+    r2 = np.where(mask, 0, synth.noise_field(nx, ny, 2, 0.2, 0.4))
+    return synth.Workload(name="hyb2", nx=nx, ny=ny, solid=mask, rho=[r1, r2], tau=(0.9, 1.2),
+                          aveforce=((1e-4, 0.0), (0.0, 1e-4)), interforce=(0.5, 0.0, 0.0),
+                          slip=[R1, R2], rho_ref=(0.7, 0.3))
+
+
+def _mixed_channel():
+    """mixed boundary style (R = 0.7) in a channel with dirichlet openings"""
+    nx, ny = 96, 26
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    solid[10:16, 40:46] = 1
+    return synth.Workload(name="mixch", nx=nx, ny=ny, solid=solid, rho=[np.where(solid, 0, 1.0)], tau=(0.7,),
+                          openings=[synth.Opening("xlo", 1, ny - 2, "inlet", [("dirichlet", 0.0, 1.002)]),
+                                    synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0.0, 1.0)])],
+                          slip=[0.7])
+
+
 def _args(w):
     a = []
     if w.ncomp == 2:
@@ -122,6 +151,8 @@ def _args(w):
 
 CASES = {"porous_openings": (_porous_open, 40, 30),
          "two_fluids_interforce_adhesion": (_two_fluids, 40, 20),
+         "hybrid_two_fluids": (_hybrid_two_fluids, 40, 30),
+         "mixed_channel_openings": (_mixed_channel, 60, 30),
          "reactive_q9": (lambda: _reactive(9), 120, 20),
          "reactive_q4": (lambda: _reactive(4), 120, 20)}
 
