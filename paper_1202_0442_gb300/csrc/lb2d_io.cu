@@ -297,7 +297,8 @@ int load(lb_ctx *ctx, const std::string &name, const char *const *names, int nna
     if (eol) *eol = '\0';
     Line ln;
     ln.no = no;
-    for (char *t = strtok(p, " \t\r"); t; t = strtok(nullptr, " \t\r")) ln.tok.push_back(t);
+    char *save = nullptr;
+    for (char *t = strtok_r(p, " \t\r", &save); t; t = strtok_r(nullptr, " \t\r", &save)) ln.tok.push_back(t);
     p = next;
     if (ln.tok.empty()) continue;
     bool head = false;
@@ -718,7 +719,8 @@ int lb_read_data(lb_ctx *ctx, const char *file, const char *args) {
       if (ch == ',') ch = ' ';
     std::vector<char> buf(a.begin(), a.end());
     buf.push_back('\0');
-    for (char *t = strtok(buf.data(), " \t"); t; t = strtok(nullptr, " \t")) {
+    char *save = nullptr;
+    for (char *t = strtok_r(buf.data(), " \t", &save); t; t = strtok_r(nullptr, " \t", &save)) {
       if (!strcmp(t, "fluids")) fluids = true;
       else if (!strcmp(t, "solute")) solute = true;
       else if (!strcmp(t, "equilibrium")) equilibrium = true;
