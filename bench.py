@@ -63,7 +63,7 @@ def kernel_source_hash() -> str:
     """Hash of the code (line comments and blank lines dropped) of the
     sources the streaming kernel is compiled from."""
     h = hashlib.sha256()
-    for name in ("k_fluid.cu", "lbcollide.cuh", "lbdev.cuh", "lbint.h", "lbsolute.cuh"):
+    for name in ("k_fluid.cu", "lbcollide.cuh", "lbdev.cuh", "lbint.h", "lbpdl.cuh", "lbsolute.cuh"):
         with open(os.path.join(ROOT, "paper_1202_0442_gb300", "csrc", name)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()

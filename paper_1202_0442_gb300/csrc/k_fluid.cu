@@ -31,6 +31,7 @@
 // of the mask-word arithmetic that otherwise dominated the streaming
 // kernel's instruction count.
 #include "lbcollide.cuh"
+#include "lbpdl.cuh"
 #include "lbsolute.cuh"
 
 namespace lbk {
@@ -174,6 +175,7 @@ __device__ __forceinline__ bool fluid_node(const FluidArgs &p, int x, int y, uin
 template <class S, int NC, bool ME, bool PM, int SR, bool SLIP>
 __global__ void __launch_bounds__(32 * LOC_BY, ((NC == 1 && !ME && !PM) ? (SLIP ? 6 : 8) : 4) * 8 / LOC_BY)
     k_fluid_local(const FluidArgs p) {
+  dep_wait();
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.chi) return;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, ((NC == 1 && !ME && !PM) ? (SLIP 
 // previous iteration's solute populations around it.
 template <class S, int SR, int Q, bool SLIP>
 __global__ void __launch_bounds__(32 * LOC_BY, 4 * 8 / LOC_BY) k_fluid_solute(const FluidArgs p, const SoluteArgs sp) {
+  dep_wait();
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = p.g.clo + blockIdx.y * LOC_BY + threadIdx.y;
   if (y >= p.g.chi) return;
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
   // (ty + 1, tx + 1) holds node (x0 + tx, y0 + ty) wrapped periodically.
   // Solid nodes are told apart by the mask bits, not by the stored value.
   __shared__ float sd[NC][SC_TY + 2][SC_TX + 2];
+  dep_wait();
   const Geometry &g = p.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = blockIdx.x * SC_TX, y0 = g.clo + blockIdx.y * SC_TY;
@@ -299,6 +303,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
 template <class S>
 __global__ void k_gradient(const GradArgs a) {
   // one thread per opening node of every gradient opening
+  dep_wait();
   const int k = blockIdx.y;
   const OpenDesc &o = a.op[k];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -354,8 +359,8 @@ __global__ void k_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry g, 
 template <class S, int NC, bool ME, bool PM, int SR>
 void launch_local(const FluidArgs &a, cudaStream_t s) {
   dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + LOC_BY - 1) / LOC_BY);
-  if (a.slip) k_fluid_local<S, NC, ME, PM, SR, true><<<grd, blk, 0, s>>>(a);
-  else k_fluid_local<S, NC, ME, PM, SR, false><<<grd, blk, 0, s>>>(a);
+  if (a.slip) launch_pdl(k_fluid_local<S, NC, ME, PM, SR, true>, grd, blk, 0, s, a);
+  else launch_pdl(k_fluid_local<S, NC, ME, PM, SR, false>, grd, blk, 0, s, a);
 }
 
 template <class S>
@@ -363,11 +368,11 @@ int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s)
   if (sc) {
     dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.chi - a.g.clo + SC_TY - 1) / SC_TY);
     if (a.slip) {
-      if (nc == 1) k_fluid_sc<S, 1, true><<<grd, blk, 0, s>>>(a);
-      else k_fluid_sc<S, 2, true><<<grd, blk, 0, s>>>(a);
+      if (nc == 1) launch_pdl(k_fluid_sc<S, 1, true>, grd, blk, 0, s, a);
+      else launch_pdl(k_fluid_sc<S, 2, true>, grd, blk, 0, s, a);
     } else {
-      if (nc == 1) k_fluid_sc<S, 1, false><<<grd, blk, 0, s>>>(a);
-      else k_fluid_sc<S, 2, false><<<grd, blk, 0, s>>>(a);
+      if (nc == 1) launch_pdl(k_fluid_sc<S, 1, false>, grd, blk, 0, s, a);
+      else launch_pdl(k_fluid_sc<S, 2, false>, grd, blk, 0, s, a);
     }
   } else {
     if (nc == 1) {
@@ -402,11 +407,11 @@ template <class S, int SR>
 int launch_fluid_solute_t(int q, const FluidArgs &a, const SoluteArgs &sa, cudaStream_t s) {
   dim3 blk(32, LOC_BY), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + LOC_BY - 1) / LOC_BY);
   if (a.slip) {
-    if (q == 4) k_fluid_solute<S, SR, 4, true><<<grd, blk, 0, s>>>(a, sa);
-    else k_fluid_solute<S, SR, 9, true><<<grd, blk, 0, s>>>(a, sa);
+    if (q == 4) launch_pdl(k_fluid_solute<S, SR, 4, true>, grd, blk, 0, s, a, sa);
+    else launch_pdl(k_fluid_solute<S, SR, 9, true>, grd, blk, 0, s, a, sa);
   } else {
-    if (q == 4) k_fluid_solute<S, SR, 4, false><<<grd, blk, 0, s>>>(a, sa);
-    else k_fluid_solute<S, SR, 9, false><<<grd, blk, 0, s>>>(a, sa);
+    if (q == 4) launch_pdl(k_fluid_solute<S, SR, 4, false>, grd, blk, 0, s, a, sa);
+    else launch_pdl(k_fluid_solute<S, SR, 9, false>, grd, blk, 0, s, a, sa);
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
@@ -436,9 +441,9 @@ int launch_gradient(int storage, const GradArgs &a, cudaStream_t s) {
   if (!a.nopen || maxlen <= 0) return 0;
   dim3 blk(128), grd((maxlen + 127) / 128, a.nopen);
   switch (storage) {
-    case ST_FP16: k_gradient<__half><<<grd, blk, 0, s>>>(a); break;
-    case ST_BF16: k_gradient<__nv_bfloat16><<<grd, blk, 0, s>>>(a); break;
-    default: k_gradient<float><<<grd, blk, 0, s>>>(a); break;
+    case ST_FP16: launch_pdl(k_gradient<__half>, grd, blk, 0, s, a); break;
+    case ST_BF16: launch_pdl(k_gradient<__nv_bfloat16>, grd, blk, 0, s, a); break;
+    default: launch_pdl(k_gradient<float>, grd, blk, 0, s, a); break;
   }
   return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }

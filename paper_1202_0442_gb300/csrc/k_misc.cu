@@ -19,6 +19,7 @@
 // FP32/FP16/BF16), equilibrium initialisation from rho and u, and field
 // export.
 #include "lbdev.cuh"
+#include "lbpdl.cuh"
 
 namespace lbk {
 
@@ -69,6 +70,7 @@ __device__ __forceinline__ void thermo_final(const double *partials, int nblocks
 // Quantities 0..8 come from FP32 planes and are summed per thread as FP32
 // pairs; 9..12 are FP64 arrays (reaction runs only); 13, 14 are counts.
 __global__ void __launch_bounds__(TB, THERMO_BLOCKS_PER_SM) k_thermo_partial(const ThermoArgs a) {
+  dep_wait();
   const Geometry &g = a.g;
   float hi[9], lo[9];
 #pragma unroll
@@ -342,8 +344,7 @@ int launch_copy_runs(const CopyRuns &r, cudaStream_t s) {
 }
 
 int launch_thermo(const ThermoArgs &a, int nblocks, cudaStream_t s) {
-  k_thermo_partial<<<nblocks, TB, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
+  return launch_pdl(k_thermo_partial, dim3(nblocks), dim3(TB), 0, s, a) == cudaSuccess ? 1 : -1;
 }
 
 int launch_import_pops(int storage, const double *src, void *dst, const uint32_t *mask,

@@ -28,6 +28,7 @@
 //   start with b0, and their fluid and solute mass is booked as removed.
 // The two growth kernels run back to back, so every decision sees the
 // state before any flip.
+#include "lbpdl.cuh"
 #include "lbsolute.cuh"
 
 namespace lbk {
@@ -38,6 +39,7 @@ namespace {
 // streaming and the opening rules (the C its collision will use)
 template <int Q>
 __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
+  dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const Geometry &g = p.g;
   const int y = g.clo + blockIdx.y * blockDim.y + threadIdx.y;
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(256) k_solute_pre(const SoluteArgs p) {
 
 template <int Q>
 __global__ void __launch_bounds__(256) k_solute(const SoluteArgs p) {
+  dep_wait();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const Geometry &g = p.g;
   const int y = g.clo + blockIdx.y * blockDim.y + threadIdx.y;
@@ -146,6 +149,7 @@ __device__ __forceinline__ void gather_grow_node(const GrowthArgs &a, int x, int
 
 // every solid node with a fluid neighbour in the rows [rlo, rhi)
 __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
+  dep_wait();
   const Geometry &g = a.g;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = a.rlo + blockIdx.y * 8 + threadIdx.y;
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(256) k_gather_grow(const GrowthArgs a) {
 // are independent of each other, so their order does not matter.
 template <class S>
 __global__ void __launch_bounds__(256) k_apply_flips(const GrowthArgs a) {
+  dep_wait();
   const Geometry &g = a.g;
   const unsigned int n = *a.fcount;
   for (unsigned int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -224,30 +229,26 @@ int launch_solute(int q, const SoluteArgs &a, cudaStream_t s) {
   dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.g.chi - a.g.clo + 7) / 8);
   int n = 0;
   if (a.inter) {
-    if (q == 4) k_solute_pre<4><<<grd, blk, 0, s>>>(a);
-    else k_solute_pre<9><<<grd, blk, 0, s>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return -1;
+    if ((q == 4 ? launch_pdl(k_solute_pre<4>, grd, blk, 0, s, a) : launch_pdl(k_solute_pre<9>, grd, blk, 0, s, a)) !=
+        cudaSuccess)
+      return -1;
     n++;
   }
-  if (q == 4) k_solute<4><<<grd, blk, 0, s>>>(a);
-  else k_solute<9><<<grd, blk, 0, s>>>(a);
-  return cudaGetLastError() == cudaSuccess ? n + 1 : -1;
+  const cudaError_t e = q == 4 ? launch_pdl(k_solute<4>, grd, blk, 0, s, a) : launch_pdl(k_solute<9>, grd, blk, 0, s, a);
+  return e == cudaSuccess ? n + 1 : -1;
 }
 
 int launch_growth(const GrowthArgs &a, cudaStream_t s) {
   dim3 blk(32, 8), grd((a.g.nx + 31) / 32, (a.rhi - a.rlo + 7) / 8);
-  k_gather_grow<<<grd, blk, 0, s>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return -1;
-  return 1;
+  return launch_pdl(k_gather_grow, grd, blk, 0, s, a) == cudaSuccess ? 1 : -1;
 }
 
 int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s) {
   switch (storage) {
-    case ST_FP16: k_apply_flips<__half><<<1, 256, 0, s>>>(a); break;
-    case ST_BF16: k_apply_flips<__nv_bfloat16><<<1, 256, 0, s>>>(a); break;
-    default: k_apply_flips<float><<<1, 256, 0, s>>>(a); break;
+    case ST_FP16: return launch_pdl(k_apply_flips<__half>, dim3(1), dim3(256), 0, s, a) == cudaSuccess ? 1 : -1;
+    case ST_BF16: return launch_pdl(k_apply_flips<__nv_bfloat16>, dim3(1), dim3(256), 0, s, a) == cudaSuccess ? 1 : -1;
+    default: return launch_pdl(k_apply_flips<float>, dim3(1), dim3(256), 0, s, a) == cudaSuccess ? 1 : -1;
   }
-  return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace lbk
