@@ -101,6 +101,30 @@ def test_momentum0_after_read_data_repaints_its_region_only():
     assert np.max(np.abs(lt.populations(1) - want)) < 1e-8
 
 
+def test_obstacle_after_read_data_overrides_the_sites_read():
+    """obstacle commands after read_data turn the sites they cover solid
+    (their populations read are dropped); the run then matches the oracle
+    read from the same file with the same sites made solid"""
+    lt = lb2d.Lattice(0)
+    lt.read_data(GOLDEN)
+    lt.boundary_style("noslip")
+    lt.obstacle_rect(2, 2, 1, 1)
+    lt.iteration(0)
+    o = oracle_from_data(GOLDEN)
+    solid = o.solid()
+    solid[1, 2] = 1
+    o.set_solid(solid)
+    f = o.f()
+    f[:, 1, 2] = 0.0
+    o.set_f(f)
+    assert np.array_equal(lt.mask() != 0, solid != 0)
+    assert np.max(np.abs(lt.populations(1) - o.f())) < 1e-8
+    lt.iteration(30)
+    o.step(30)
+    e_rho, e_u = _compare_flow(lt, o, 1)
+    assert e_rho < TOL32 and e_u < TOL32, (e_rho, e_u)
+
+
 def _porous_open():
     return synth.porous(128, 96, seed=2, rmin=4, rmax=10)
 
