@@ -182,3 +182,46 @@ def test_output_command_fields_without_thermo():
     assert e.value.code == lb2d.LB_E_ORDER
     with pytest.raises(lb2d.LBError):
         a.output(-1)
+
+
+def test_contexts_on_two_threads():
+    """Two contexts on two streams driven from two host threads at once (as
+    the end-to-end benchmark leg runs them): every snapshot upload,
+    iteration and velocity download gives the bits the same calls give
+    one after the other."""
+    import threading
+    w = synth.porous(256, 192, seed=4, rmin=4, rmax=10)
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    lts = [lb2d.from_workload(w, "fp32", stream=s.cuda_stream) for s in streams]
+    lts[1].iteration(7)  # a different state in each context
+    snaps = []
+    for lt in lts:
+        snaps.append(torch.empty(lt.state_size(), dtype=torch.uint8, pin_memory=True))
+        lt.save_state(snaps[-1])
+        lt.output(1)
+    want = []
+    for lt, snap in zip(lts, snaps):
+        lt.load_state(snap)
+        lt.iteration(3)
+        want.append([a.copy() for a in lt.velocity_f32()])
+    got = [[], []]
+
+    def run(i):
+        outs = tuple(torch.empty((w.ny, w.nx), dtype=torch.float32, pin_memory=True) for _ in range(3))
+        for _ in range(10):
+            lts[i].load_state(snaps[i])
+            lts[i].iteration(3)
+            lts[i].velocity_f32(outs)
+            got[i].append([o.numpy().copy() for o in outs])
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i in range(2):
+        assert len(got[i]) == 10
+        for rec in got[i]:
+            for a, b in zip(rec, want[i]):
+                assert np.array_equal(a, b)
+    assert not np.array_equal(want[0][1], want[1][1])
