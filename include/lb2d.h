@@ -397,6 +397,19 @@ int lb_set_kernel(lb_ctx *ctx, const char *name);
  * wait (a test of the give-up path).  Any time. */
 int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles);
 
+/* Checking aid in place of a memory sanitizer: with LB_DEBUG_POISON set,
+ * every iteration first fills the buffers it is about to write (the
+ * populations and solute populations of the next state, the deposit
+ * shares, the solvent-velocity and concentration planes, and on thermo or
+ * output steps the node-field planes) with NaN bit patterns.  A kernel
+ * that read a slot no kernel of the iteration wrote (a solid slot, a row
+ * padding lane, a plane it does not own) would carry the NaN into the fluid
+ * state, the exports or the thermo sums; with correct kernels the results
+ * equal those of a run without the flag bit for bit.  Costs a memset of
+ * those buffers per iteration.  flags: 0 or LB_DEBUG_POISON. */
+#define LB_DEBUG_POISON 0x1
+int lb_set_debug(lb_ctx *ctx, int flags);
+
 /* iteration command: advance Nt iterations.  The first call validates the
  * setup (LB_E_ARG with a message if it is inconsistent) and moves the
  * state to the GPU.  Returns LB_E_NAN if a thermo sum is not finite. */

@@ -493,6 +493,7 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
 }
 
 int run_thermo(lb_ctx *ctx) {
+  NvtxRange range("thermo");
   ThermoArgs ta{};
   ta.g = ctx->g;
   ta.mask = ctx->mask;
@@ -546,7 +547,26 @@ int run_thermo(lb_ctx *ctx) {
   return LB_OK;
 }
 
+// LB_DEBUG_POISON: NaN bit patterns (all ones: NaN in FP32, FP16 and
+// BF16) in every buffer the coming iteration writes
+int poison_outputs(lb_ctx *ctx, int nxt, bool fields) {
+  const Geometry &g = ctx->g;
+  const size_t plane = g.plane;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->fbuf[nxt], 0xff, (size_t)ctx->nc * 9 * plane * storage_bytes(ctx->storage), s));
+  if (ctx->qs) {
+    CK(cudaMemsetAsync(ctx->gbuf[nxt], 0xff, (size_t)ctx->qs * plane * 4, s));
+    CK(cudaMemsetAsync(ctx->u, 0xff, 2 * plane * 4, s));
+    if (ctx->react) CK(cudaMemsetAsync(ctx->db, 0xff, plane * 4, s));
+    if (ctx->inter) CK(cudaMemsetAsync(ctx->Cpre, 0xff, plane * 4, s));
+    if (fields) CK(cudaMemsetAsync(ctx->Cfield, 0xff, plane * 4, s));
+  }
+  if (fields) CK(cudaMemsetAsync(ctx->fields, 0xff, (size_t)ctx->nc * NFIELD * plane * 4, s));
+  return LB_OK;
+}
+
 int one_step(lb_ctx *ctx, bool fields) {
+  NvtxRange range("step");
   cudaStream_t s = ctx->stream;
   ctx->t += 1;
   if (ctx->react) ctx->mask_host_valid = false;  // growth may change the device mask
@@ -595,6 +615,7 @@ int one_step(lb_ctx *ctx, bool fields) {
     return ctx->fail(LB_E_UNSUPPORTED, "the fused kernel runs single-component lattices with a solute, "
                      "without interforce, intersolute or exact momentum pairs");
   const bool fused = fuse_ok && (ctx->kernel == 0 || ctx->kernel == 3);
+  if (ctx->debug & LB_DEBUG_POISON) TRY(poison_outputs(ctx, nxt, fields));
   if (fused) {
     // the solvent velocity stays in registers; the plane is written only
     // when the caller bound it
@@ -1360,6 +1381,13 @@ int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles) {
   return LB_OK;
 }
 
+int lb_set_debug(lb_ctx *ctx, int flags) {
+  NEED_CTX();
+  if (flags & ~LB_DEBUG_POISON) return ctx->fail(LB_E_ARG, "unknown debug flags 0x%x", flags);
+  ctx->debug = flags;
+  return LB_OK;
+}
+
 int lb_output(lb_ctx *ctx, int Nf) {
   NEED_CTX();
   if (Nf < 0) return ctx->fail(LB_E_ARG, "Nf must be >= 0");
@@ -1376,6 +1404,7 @@ int lb_thermo(lb_ctx *ctx, int Nf) {
 
 int lb_iteration(lb_ctx *ctx, int Nt) {
   NEED_CTX();
+  NvtxRange range("lb_iteration");
   if (Nt < 0) return ctx->fail(LB_E_ARG, "Nt must be >= 0");
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   for (int c = 0; c < ctx->nc; c++)
@@ -1777,6 +1806,7 @@ int lb_halo_pack(lb_ctx *ctx, int face, void *buf) { return halo_move(ctx, face,
 int lb_halo_unpack(lb_ctx *ctx, int face, const void *buf) { return halo_move(ctx, face, (void *)buf, false); }
 
 int lb_exchange(lb_ctx *const *ctxs, int n) {
+  NvtxRange range("lb_exchange");
   if (!ctxs || n < 1) return LB_E_ARG;
   for (int r = 0; r < n; r++)
     if (!ctxs[r]) return LB_E_ARG;
@@ -2160,6 +2190,7 @@ int lb_batch_launch_count(const lb_batch *b, uint64_t *out) {
 
 int lb_batch_iteration(lb_batch *b, int Nt, int use_graph) {
   if (!b) return LB_E_ARG;
+  NvtxRange range("lb_batch_iteration");
   if (Nt < 0) return b->fail(LB_E_ARG, "Nt must be >= 0");
   BCK(cudaSetDevice(b->device));
   int rc = sync_descs(b);

@@ -666,6 +666,7 @@ int apply_momentum_style(lb_ctx *ctx, const DataFile &d, const OpenLine &o) {
 }  // namespace
 
 int write_data_files(lb_ctx *ctx, const std::string &base) {
+  NvtxRange range("write_restart");
   if (ctx->rank >= 0) return ctx->fail(LB_E_UNSUPPORTED, "a slab writes no input-data file: gather the lattice first");
   if (!ctx->committed) return ctx->fail(LB_E_ORDER, "no device state yet");
   std::vector<uint8_t> mask((size_t)ctx->nx * ctx->ny);
@@ -709,6 +710,7 @@ int lb_write_restart(lb_ctx *ctx, const char *file, int Nf) {
 
 int lb_read_data(lb_ctx *ctx, const char *file, const char *args) {
   NEED_CTX();
+  NvtxRange range("read_data");
   if (!file || !*file) return ctx->fail(LB_E_ARG, "no file name");
   if (ctx->committed) return ctx->fail(LB_E_ORDER, "read_data must precede the first iteration");
   if (ctx->rank >= 0) return ctx->fail(LB_E_UNSUPPORTED, "read_data into a slab is not built");

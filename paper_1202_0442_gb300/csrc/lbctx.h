@@ -10,6 +10,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lb2d.h"
 #include "lbint.h"
@@ -101,6 +102,7 @@ struct lb_ctx {
   unsigned int *tdone = nullptr;  // thermo blocks finished (reset by the last)
   int tblocks = 0;
   int64_t t = 0;
+  int debug = 0;          // LB_DEBUG_* flags (lb_set_debug)
   int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
                          // 3 fused fluid-solute
   int *errw = nullptr;   // device error word of the TMA kernel
@@ -161,6 +163,17 @@ struct lb_ctx {
     int r_ = (x);            \
     if (r_ != LB_OK) return r_; \
   } while (0)
+
+// an NVTX range over a scope: the library's phases show up by name in
+// Nsight Systems timelines and can select kernels in Nsight Compute
+// (--nvtx --nvtx-include "lb_iteration/"); without a tool attached a push
+// or pop costs a pointer test
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // write the state of `ctx` as input-data text files named base (one
 // fluid), base.fluid1 / base.fluid2 (two) and base.solute (write_restart

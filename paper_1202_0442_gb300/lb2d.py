@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblb2d.so")
 
 LB_OK, LB_E_ORDER, LB_E_ARG, LB_E_UNSUPPORTED, LB_E_CUDA, LB_E_NAN, LB_E_NOMEM, LB_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+LB_DEBUG_POISON = 0x1
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LB_STOCHASTIC_ROUNDING = 0x100
 LB_PRECISE_MOMENTUM = 0x200
@@ -105,6 +106,7 @@ SIGNATURES = {
     "lb_adhesiveforce": (I, [P, D, D, D, I]),
     "lb_set_kernel": (I, [P, S]),
     "lb_set_wait_limit": (I, [P, C.c_int64]),
+    "lb_set_debug": (I, [P, I]),
     "lb_thermo": (I, [P, I]),
     "lb_output": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
@@ -372,6 +374,10 @@ class Lattice:
     # -- output and action -----------------------------------------------------
     def set_kernel(self, name: str = "auto"):
         self._ck(self._L.lb_set_kernel(self._h, _b(name)))
+
+    def set_debug(self, flags: int = 0):
+        """LB_DEBUG_POISON: NaN in every buffer an iteration writes, before it."""
+        self._ck(self._L.lb_set_debug(self._h, flags))
 
     def set_wait_limit(self, cycles: int = -1):
         """Clock-cycle limit of the TMA kernel's waits (-1: default)."""
