@@ -406,7 +406,9 @@ int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles);
  * padding lane, a plane it does not own) would carry the NaN into the fluid
  * state, the exports or the thermo sums; with correct kernels the results
  * equal those of a run without the flag bit for bit.  Costs a memset of
- * those buffers per iteration.  flags: 0 or LB_DEBUG_POISON. */
+ * those buffers per iteration; a batch with a poisoned member poisons its
+ * population buffers before every launch and runs without its graph.
+ * flags: 0 or LB_DEBUG_POISON. */
 #define LB_DEBUG_POISON 0x1
 int lb_set_debug(lb_ctx *ctx, int flags);
 

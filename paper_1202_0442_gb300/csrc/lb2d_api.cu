@@ -2069,9 +2069,32 @@ BatchLaunch launch_desc(lb_batch *b) {
   return L;
 }
 
+// LB_DEBUG_POISON on member contexts: NaN in the buffers the launch of
+// this parity writes (every member's next population buffer)
+int batch_poison(lb_batch *b, int parity) {
+  for (lb_ctx *c : b->ctxs) {
+    if (!(c->debug & LB_DEBUG_POISON)) continue;
+    const int out = 1 - ((c->cur + parity) & 1);
+    const cudaError_t e = cudaMemsetAsync(c->fbuf[out], 0xff, 9 * c->g.plane * storage_bytes(c->storage), b->stream);
+    if (e != cudaSuccess) return batch_cuda(b, e, "poison");
+  }
+  return LB_OK;
+}
+
+bool batch_poisoned(const lb_batch *b) {
+  for (const lb_ctx *c : b->ctxs)
+    if (c->debug & LB_DEBUG_POISON) return true;
+  return false;
+}
+
 int batch_direct(lb_batch *b, int parity0, int n) {
   BatchLaunch L = launch_desc(b);
+  const bool poison = batch_poisoned(b);
   for (int k = 0; k < n; k++) {
+    if (poison) {
+      const int rc = batch_poison(b, (parity0 + k) & 1);
+      if (rc != LB_OK) return rc;
+    }
     if (launch_batch(b->storage, L, (parity0 + k) & 1, b->stream) < 0)
       return batch_cuda(b, cudaGetLastError(), "batch launch");
     b->launches++;
@@ -2196,7 +2219,8 @@ int lb_batch_iteration(lb_batch *b, int Nt, int use_graph) {
   int rc = sync_descs(b);
   if (rc != LB_OK) return rc;
   int done = 0;
-  if (use_graph) {
+  // poisoned members run without the graph (the poisoning is not captured)
+  if (use_graph && !batch_poisoned(b)) {
     rc = ensure_graph(b);
     if (rc != LB_OK) return rc;
     if (Nt >= b->graph_steps) {

@@ -15,8 +15,8 @@ variant is reached: the streaming kernel (FP32, FP16, BF16; noslip, slip
 map, mixed; openings of every style incl. gradient), two components
 (mass-exact), Shan-Chen with one and two components, the fused fluid-solute
 kernel with reaction and growth (D2Q9, D2Q4), the separate solute kernel
-under a two-component fluid, intersolute, the TMA kernel and slabs with
-their halo exchange."""
+under a two-component fluid, intersolute, the TMA kernel, slabs with
+their halo exchange and the batched launch."""
 import copy
 
 import numpy as np
@@ -183,3 +183,29 @@ def test_debug_flag_errors():
         lt.set_debug(0x10)
     assert e.value.code == lb2d.LB_E_ARG
     lt.set_debug(0)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_poisoned_batch(storage):
+    """The batched launch over lattices of uneven sizes, poisoned (direct
+    launches) against unpoisoned (graph replays): bit for bit."""
+    ws = [synth.porous(nx, ny, seed=s, rmin=3, rmax=7) for s, (nx, ny) in enumerate([(64, 96), (96, 64), (160, 128)])]
+    for w in ws:
+        w.openings = []
+        w.aveforce = ((1e-5, 0.0),)
+    kw = {"h_max": 5e-3, "rounding": "stochastic"} if storage == "fp16" else {}
+    out = []
+    for poison in (False, True):
+        lats = [lb2d.from_workload(w, storage, **kw) for w in ws]
+        for lt in lats:
+            lt.thermo(1 << 30)
+            if poison:
+                lt.set_debug(lb2d.LB_DEBUG_POISON)
+        b = lb2d.Batch(lats)
+        b.iteration(45, use_graph=True)
+        torch.cuda.synchronize()
+        out.append([lt.populations(1) for lt in lats])
+        del b
+    for x, y in zip(*out):
+        assert np.array_equal(x, y)
+        assert np.all(np.isfinite(x))
