@@ -408,9 +408,18 @@ int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles);
  * equal those of a run without the flag bit for bit.  Costs a memset of
  * those buffers per iteration; a batch with a poisoned member poisons its
  * population buffers before every launch and runs without its graph.
- * flags: 0 or LB_DEBUG_POISON. */
+ * flags: any of LB_DEBUG_POISON and LB_DEBUG_GUARDS. */
 #define LB_DEBUG_POISON 0x1
+/* LB_DEBUG_GUARDS: every device buffer the library allocates after the
+ * flag is set (set it before the first iteration or state upload) gets a
+ * 256 KB zone of NaN bit patterns on each side.  A read past a buffer's
+ * end (or before its start) within that distance carries NaN into the
+ * results; lb_debug_check counts the guard bytes that no longer hold the
+ * pattern (a write out of bounds) into *bad.  Buffers bound with lb_bind
+ * have no guards. */
+#define LB_DEBUG_GUARDS 0x2
 int lb_set_debug(lb_ctx *ctx, int flags);
+int lb_debug_check(lb_ctx *ctx, int64_t *bad);
 
 /* iteration command: advance Nt iterations.  The first call validates the
  * setup (LB_E_ARG with a message if it is inconsistent) and moves the

@@ -204,10 +204,22 @@ size_t buffer_bytes(const lb_ctx *ctx, int k) {
   }
 }
 
+// LB_DEBUG_GUARDS: bytes of NaN pattern before and after each allocation
+constexpr size_t GUARD_BYTES = 256 << 10;
+
 template <class T>
 int dalloc(lb_ctx *ctx, T **p, size_t n) {
-  cudaError_t e = cudaMalloc((void **)p, n > 0 ? n * sizeof(T) : 1);
-  if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "cudaMalloc(%zu): %s", n * sizeof(T), cudaGetErrorString(e));
+  const size_t bytes = n > 0 ? n * sizeof(T) : 1;
+  const bool guard = (ctx->debug & LB_DEBUG_GUARDS) != 0;
+  void *raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, bytes + (guard ? 2 * GUARD_BYTES : 0));
+  if (e != cudaSuccess) return ctx->fail(LB_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  *p = (T *)((uint8_t *)raw + (guard ? GUARD_BYTES : 0));
+  if (guard) {
+    e = cudaMemsetAsync(raw, 0xff, bytes + 2 * GUARD_BYTES, ctx->stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
+    ctx->guarded.push_back({raw, (void *)*p, bytes});
+  }
   e = cudaMemsetAsync(*p, 0, n * sizeof(T), ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaMemsetAsync");
   return LB_OK;
@@ -735,7 +747,10 @@ int lb_destroy(lb_ctx *ctx) {
   for (void *p : ptrs) {
     bool own = p != nullptr;
     for (int k = 0; k < 6; k++) own = own && p != ctx->bound[k];
-    if (own) cudaFree(p);
+    if (!own) continue;
+    for (const lb_ctx::Guarded &gd : ctx->guarded)
+      if (gd.user == p) p = gd.raw;
+    cudaFree(p);
   }
   delete ctx;
   return LB_OK;
@@ -1383,8 +1398,26 @@ int lb_set_wait_limit(lb_ctx *ctx, int64_t cycles) {
 
 int lb_set_debug(lb_ctx *ctx, int flags) {
   NEED_CTX();
-  if (flags & ~LB_DEBUG_POISON) return ctx->fail(LB_E_ARG, "unknown debug flags 0x%x", flags);
+  if (flags & ~(LB_DEBUG_POISON | LB_DEBUG_GUARDS)) return ctx->fail(LB_E_ARG, "unknown debug flags 0x%x", flags);
   ctx->debug = flags;
+  return LB_OK;
+}
+
+int lb_debug_check(lb_ctx *ctx, int64_t *bad) {
+  NEED_CTX();
+  if (!bad) return ctx->fail(LB_E_ARG, "null output");
+  TRY(set_device(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<uint8_t> h(GUARD_BYTES);
+  int64_t n = 0;
+  for (const lb_ctx::Guarded &gd : ctx->guarded) {
+    for (int side = 0; side < 2; side++) {
+      const uint8_t *src = side ? (const uint8_t *)gd.user + gd.bytes : (const uint8_t *)gd.raw;
+      CK(cudaMemcpy(h.data(), src, GUARD_BYTES, cudaMemcpyDeviceToHost));
+      for (uint8_t v : h) n += v != 0xff;
+    }
+  }
+  *bad = n;
   return LB_OK;
 }
 

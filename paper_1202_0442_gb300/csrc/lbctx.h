@@ -103,6 +103,13 @@ struct lb_ctx {
   int tblocks = 0;
   int64_t t = 0;
   int debug = 0;          // LB_DEBUG_* flags (lb_set_debug)
+  // LB_DEBUG_GUARDS: allocations made with guard zones (raw block, the
+  // pointer handed out, its size)
+  struct Guarded {
+    void *raw, *user;
+    size_t bytes;
+  };
+  std::vector<Guarded> guarded;
   int kernel = 0;        // 0 auto (streaming), 1 streaming (k_fluid_local), 2 TMA pipeline,
                          // 3 fused fluid-solute
   int *errw = nullptr;   // device error word of the TMA kernel

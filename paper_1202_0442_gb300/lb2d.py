@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblb2d.so")
 
 LB_OK, LB_E_ORDER, LB_E_ARG, LB_E_UNSUPPORTED, LB_E_CUDA, LB_E_NAN, LB_E_NOMEM, LB_E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
-LB_DEBUG_POISON = 0x1
+LB_DEBUG_POISON, LB_DEBUG_GUARDS = 0x1, 0x2
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 LB_STOCHASTIC_ROUNDING = 0x100
 LB_PRECISE_MOMENTUM = 0x200
@@ -107,6 +107,7 @@ SIGNATURES = {
     "lb_set_kernel": (I, [P, S]),
     "lb_set_wait_limit": (I, [P, C.c_int64]),
     "lb_set_debug": (I, [P, I]),
+    "lb_debug_check": (I, [P, C.POINTER(C.c_int64)]),
     "lb_thermo": (I, [P, I]),
     "lb_output": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
@@ -376,8 +377,16 @@ class Lattice:
         self._ck(self._L.lb_set_kernel(self._h, _b(name)))
 
     def set_debug(self, flags: int = 0):
-        """LB_DEBUG_POISON: NaN in every buffer an iteration writes, before it."""
+        """LB_DEBUG_POISON: NaN in every buffer an iteration writes, before
+        it; LB_DEBUG_GUARDS: NaN guard zones around the buffers allocated
+        afterwards."""
         self._ck(self._L.lb_set_debug(self._h, flags))
+
+    def debug_check(self) -> int:
+        """Guard bytes overwritten so far (LB_DEBUG_GUARDS)."""
+        n = C.c_int64()
+        self._ck(self._L.lb_debug_check(self._h, C.byref(n)))
+        return int(n.value)
 
     def set_wait_limit(self, cycles: int = -1):
         """Clock-cycle limit of the TMA kernel's waits (-1: default)."""
@@ -582,12 +591,15 @@ def from_workload(w: "synth.Workload", storage: str = "fp32", h_max: float = 0.0
                   device: int = 0, stream: Optional[int] = None, thermo: int = 0,
                   rounding: str = "nearest", kernel: str = "auto", precise: bool = False,
                   bind: Optional[dict] = None, step: int = 0,
-                  slab: Optional[Tuple[int, int]] = None) -> Lattice:
+                  slab: Optional[Tuple[int, int]] = None, debug: int = 0) -> Lattice:
     """Issue the command sequence that sets up workload ``w``.  ``bind``:
     state buffer name -> caller-owned CUDA tensor (Lattice.bind); ``step``:
     iterations already done (a state that continues another run); ``slab``:
-    (py, rank) to hold one y slab of the lattice (processors command)."""
+    (py, rank) to hold one y slab of the lattice (processors command);
+    ``debug``: LB_DEBUG_* flags, set before any device buffer exists."""
     lt = Lattice(device, stream)
+    if debug:
+        lt.set_debug(debug)
     lt.lattice(w.nx, w.ny, w.tau[0])
     if slab is not None:
         lt.processors(1, slab[0])

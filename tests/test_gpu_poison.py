@@ -10,7 +10,10 @@ on thermo or output steps, the node-field planes.  A kernel that read a
 slot no kernel of the iteration wrote would carry NaN into the fluid state,
 the exports or the thermo sums.  Each workload below runs with and without
 the flag; populations, solute state, deposits, mask, Eq. (4) velocity and
-thermo records must be equal bit for bit and finite.  Every fluid kernel
+thermo records must be equal bit for bit and finite.  The poisoned runs
+also allocate every library buffer between zones of NaN patterns
+(LB_DEBUG_GUARDS): a read past a buffer's end would carry NaN in, and the
+zones must be intact at the end (no write out of bounds).  Every fluid kernel
 variant is reached: the streaming kernel (FP32, FP16, BF16; noslip, slip
 map, mixed; openings of every style incl. gradient), two components
 (mass-exact), Shan-Chen with one and two components, the fused fluid-solute
@@ -141,14 +144,15 @@ def test_poisoned_buffers_change_nothing(case):
     w = make()
     runs = []
     for poison in (False, True):
-        lt = lb2d.from_workload(w, storage, thermo=7, kernel=kernel or "auto", **kw)
-        if poison:
-            lt.set_debug(lb2d.LB_DEBUG_POISON)
+        dbg = (lb2d.LB_DEBUG_POISON | lb2d.LB_DEBUG_GUARDS) if poison else 0
+        lt = lb2d.from_workload(w, storage, thermo=7, kernel=kernel or "auto", debug=dbg, **kw)
         recs = []
         for k in range(steps // 10):
             lt.iteration(10)
             recs.append(lt.get_thermo())
         runs.append((_state(lt, w), recs))
+        if poison:
+            assert lt.debug_check() == 0
     (a, ra), (b, rb) = runs
     assert ra == rb
     for x, y in zip(a, b):
@@ -162,9 +166,8 @@ def test_poisoned_slabs():
     whole lattice: bit for bit."""
     w = _reactive(9)
     whole = lb2d.from_workload(w, thermo=9)
-    slabs = [lb2d.from_workload(w, thermo=9, slab=(3, r)) for r in range(3)]
-    for s in slabs:
-        s.set_debug(lb2d.LB_DEBUG_POISON)
+    slabs = [lb2d.from_workload(w, thermo=9, slab=(3, r), debug=lb2d.LB_DEBUG_POISON | lb2d.LB_DEBUG_GUARDS)
+             for r in range(3)]
     for _ in range(90):
         whole.iteration(1)
         for s in slabs:
@@ -175,6 +178,7 @@ def test_poisoned_slabs():
     for a, b in zip(zip(*[s.solute_state() for s in slabs]), whole.solute_state()):
         assert np.array_equal(cat(list(a)), b)
     assert np.array_equal(cat([s.mask() for s in slabs]), whole.mask())
+    assert all(s.debug_check() == 0 for s in slabs)
 
 
 def test_debug_flag_errors():
@@ -196,15 +200,16 @@ def test_poisoned_batch(storage):
     kw = {"h_max": 5e-3, "rounding": "stochastic"} if storage == "fp16" else {}
     out = []
     for poison in (False, True):
-        lats = [lb2d.from_workload(w, storage, **kw) for w in ws]
+        dbg = (lb2d.LB_DEBUG_POISON | lb2d.LB_DEBUG_GUARDS) if poison else 0
+        lats = [lb2d.from_workload(w, storage, debug=dbg, **kw) for w in ws]
         for lt in lats:
             lt.thermo(1 << 30)
-            if poison:
-                lt.set_debug(lb2d.LB_DEBUG_POISON)
         b = lb2d.Batch(lats)
         b.iteration(45, use_graph=True)
         torch.cuda.synchronize()
         out.append([lt.populations(1) for lt in lats])
+        if poison:
+            assert all(lt.debug_check() == 0 for lt in lats)
         del b
     for x, y in zip(*out):
         assert np.array_equal(x, y)
