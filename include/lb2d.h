@@ -547,9 +547,11 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes);
  * sites); a solute file holds relaxation_time, inlet/outlet, reaction
  * (surface kr Cs growth bmax b0 seed), field (intersolute), concentration
  * (x y C [b]) and solute_modes (x y g_1 .. g_q).  Numbers are written with
- * 17 significant digits.  Nf = 0 stops writing.  file is copied.  Errors:
- * LB_E_ARG (Nf < 0, no name; a file that cannot be written is reported by
- * lb_iteration), LB_E_UNSUPPORTED (a slab). */
+ * 17 significant digits.  As in the paper, the command precedes the
+ * iteration command (LB_E_ORDER once the device state exists, except
+ * Nf = 0, which stops writing).  file is copied.  Errors: LB_E_ARG (Nf < 0,
+ * no name; a file that cannot be written is reported by lb_iteration),
+ * LB_E_ORDER, LB_E_UNSUPPORTED (a slab). */
 int lb_write_restart(lb_ctx *ctx, const char *file, int Nf);
 /* The same files for the current state, now, named "<file>" (one fluid),
  * "<file>.fluid1"/".fluid2" and "<file>.solute".  Errors: LB_E_ORDER (no

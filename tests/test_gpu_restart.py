@@ -261,6 +261,10 @@ def test_write_restart_every_nf(tmp_path):
     a.write_restart("", 0)
     a.iteration(10)
     assert sorted(os.listdir(tmp_path)) == ["direct", "r.10", "r.20"]
+    # the command precedes the iteration command (write_data writes now)
+    with pytest.raises(lb2d.LBError) as e:
+        a.write_restart(str(tmp_path / "late"), 10)
+    assert e.value.code == lb2d.LB_E_ORDER
 
 
 def _bad(tmp_path, edit):
