@@ -206,8 +206,12 @@ int lb_solute(lb_ctx *ctx, double taus, int q);
  * density rho_ref[c] (one per component; NULL = 1.0); FP16 stores them
  * multiplied by the power of two 2^s with s the largest integer such that
  * h_max * 2^s <= 2^14, h_max being the largest |f_i - w_i rho_ref| the
- * run will see (<= 0 picks 0.25 * max rho_ref).  Arithmetic is FP32 in all
- * three.  Before the first lb_iteration only. */
+ * run will see (<= 0 picks 0.25 * max rho_ref); a deviation beyond the
+ * format's range (about 4 h_max) is stored as infinite by the stochastic
+ * and nearest roundings (the next thermo evaluation then returns
+ * LB_E_NAN; the mass-exact collision of two components clamps it), so
+ * h_max must bound the run.  Arithmetic is FP32 in all three.  Before the
+ * first lb_iteration only. */
 int lb_set_storage(lb_ctx *ctx, int storage, const double *rho_ref,
                    double h_max);
 
@@ -548,8 +552,8 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes);
  * (surface kr Cs growth bmax b0 seed), field (intersolute), concentration
  * (x y C [b]) and solute_modes (x y g_1 .. g_q).  Numbers are written with
  * 17 significant digits.  As in the paper, the command precedes the
- * iteration command (LB_E_ORDER once the device state exists, except
- * Nf = 0, which stops writing).  file is copied.  Errors: LB_E_ARG (Nf < 0,
+ * iteration command (LB_E_ORDER once an iteration has run, except Nf = 0,
+ * which stops writing).  file is copied.  Errors: LB_E_ARG (Nf < 0,
  * no name; a file that cannot be written is reported by lb_iteration),
  * LB_E_ORDER, LB_E_UNSUPPORTED (a slab). */
 int lb_write_restart(lb_ctx *ctx, const char *file, int Nf);

@@ -66,13 +66,16 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
   equilibrium_pairs(d, rho, ux, uy, mx, my, 1.0f / 9.0f, 1.0f / 36.0f, heq);
   if (L.sr) {
     // stochastic rounding as in the single-lattice kernels: one hash per
-    // node and launch, a linear congruential sequence per direction
+    // node and launch, a linear congruential step per pair of stores
     uint32_t r = rnd(seed, self, 0, 0);
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
+    for (int i = 0; i < 8; i += 2) {
       r = r * 1664525u + 1013904223u;
-      Store<S>::st_dither(fout, i * P + self, (h[i] + L.omega * (heq[i] - h[i])) * L.scale, r);
+      Store<S>::st2_dither(fout, i * P + self, (i + 1) * P + self, (h[i] + L.omega * (heq[i] - h[i])) * L.scale,
+                           (h[i + 1] + L.omega * (heq[i + 1] - h[i + 1])) * L.scale, r ^ (r >> 16));
     }
+    r = r * 1664525u + 1013904223u;
+    Store<S>::st_dither(fout, 8 * P + self, (h[8] + L.omega * (heq[8] - h[8])) * L.scale, r);
   } else {
 #pragma unroll
     for (int i = 0; i < 9; i++)

@@ -1469,6 +1469,7 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
       ctx->fields_step = ctx->t;
       TRY(run_thermo(ctx));
     }
+    ctx->iterated = true;
     // write_restart: the state after this iteration, "<file>.<t>"
     if (ctx->restart_nf > 0 && ctx->t % ctx->restart_nf == 0)
       TRY(write_data_files(ctx, ctx->restart_file + "." + std::to_string((long long)ctx->t)));

@@ -703,7 +703,7 @@ int lb_write_restart(lb_ctx *ctx, const char *file, int Nf) {
   if (Nf < 0) return ctx->fail(LB_E_ARG, "Nf must be >= 0");
   if (Nf > 0 && (!file || !*file)) return ctx->fail(LB_E_ARG, "no file name");
   if (Nf > 0 && ctx->rank >= 0) return ctx->fail(LB_E_UNSUPPORTED, "a slab writes no restart file");
-  if (Nf > 0 && ctx->committed)
+  if (Nf > 0 && ctx->iterated)
     return ctx->fail(LB_E_ORDER, "write_restart must precede the iteration command (lb_write_data writes now)");
   ctx->restart_nf = Nf;
   ctx->restart_file = Nf > 0 ? file : "";

@@ -129,21 +129,27 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
       equilibrium_pairs(drho[c], rho[c], uex[c], uey[c], mxt[c], myt[c], p.wa[c], p.wd[c], heq);
     }
     const float om = p.omega[c];
-    if (!ME && SR != 0) {
-      // SR 2: one hash per node and component, then a linear congruential
-      // sequence whose high bits dither each store
-      uint32_t r = SR == 2 ? rnd(p.sr_seed, hself, c, 0) : 0u;
+    if (!ME && SR == 2) {
+      // stochastic rounding: one hash per node and component, then a
+      // linear congruential sequence, one step per pair of stores, its high
+      // half folded into the low half (the paired conversion draws the
+      // first value's dither from the low bits); the ninth store takes the
+      // single conversion's high bits
+      uint32_t r = rnd(p.sr_seed, hself, c, 0);
+      const float sc = FOLD ? 1.0f : p.scale;
 #pragma unroll
-      for (int i = 0; i < 9; i++) {
-        const float v = h[c][i] + om * (heq[i] - h[c][i]);
-        if (SR == 2) {
-          r = r * 1664525u + 1013904223u;
-          if (FOLD) Store<S>::st_dither(out, i * P + self, v, r);
-          else Store<S>::st_dither(out, i * P + self, v * p.scale, r);
-        } else {
-          Store<S>::st(out, i * P + self, v, FOLD ? 1.0f : p.scale);
-        }
+      for (int i = 0; i < 8; i += 2) {
+        const float v0 = (h[c][i] + om * (heq[i] - h[c][i])) * sc;
+        const float v1 = (h[c][i + 1] + om * (heq[i + 1] - h[c][i + 1])) * sc;
+        r = r * 1664525u + 1013904223u;
+        Store<S>::st2_dither(out, i * P + self, (i + 1) * P + self, v0, v1, r ^ (r >> 16));
       }
+      r = r * 1664525u + 1013904223u;
+      Store<S>::st_dither(out, 8 * P + self, (h[c][8] + om * (heq[8] - h[c][8])) * sc, r);
+    } else if (!ME && SR == 1) {
+#pragma unroll
+      for (int i = 0; i < 9; i++)
+        Store<S>::st(out, i * P + self, h[c][i] + om * (heq[i] - h[c][i]), FOLD ? 1.0f : p.scale);
     } else if (!ME) {
       uint32_t r = p.sr_seed ? rnd(p.sr_seed, hself, c, 0) : 0u;
 #pragma unroll

@@ -36,6 +36,7 @@ struct lb_ctx {
   // command state
   bool have_lattice = false, have_style = false, have_region = false;
   bool momentum_cmd = false, committed = false;
+  bool iterated = false;  // an iteration has run (write_restart must come first)
   int nx = 0, ny = 0, nc = 1;
   double tau[2] = {1, 1};
   double alpha[2] = {4.0 / 9.0, 4.0 / 9.0};  // fluids command, density-ratio parameter

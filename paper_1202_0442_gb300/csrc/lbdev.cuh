@@ -64,6 +64,11 @@ template <> struct Store<float> {
     p[k] = v;
     return v;
   }
+  static __device__ __forceinline__ void st2_dither(float *p, size_t k0, size_t k1, float v0, float v1,
+                                                    uint32_t) {
+    p[k0] = v0;
+    p[k1] = v1;
+  }
 };
 // 16-bit stores take an optional 32-bit random word r: with r = 0 they
 // round to nearest even; otherwise r's low bits are added below the
@@ -102,6 +107,16 @@ template <> struct Store<__half> {
     p[k] = q;
     return __half2float(q) * inv;
   }
+  // two values (already scaled) rounded stochastically by one paired
+  // conversion (cvt.rs.f16x2.f32, sm_100 and later): bits 0-12 of r dither
+  // v0, bits 16-28 dither v1; v0 goes to slot k0, v1 to slot k1
+  static __device__ __forceinline__ void st2_dither(__half *p, size_t k0, size_t k1, float v0, float v1,
+                                                    uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v1), "f"(v0), "r"(r));
+    p[k0] = __ushort_as_half((unsigned short)(d & 0xffffu));
+    p[k1] = __ushort_as_half((unsigned short)(d >> 16));
+  }
 };
 template <> struct Store<__nv_bfloat16> {
   static constexpr bool kScaled = false;
@@ -134,6 +149,15 @@ template <> struct Store<__nv_bfloat16> {
                               : __float2bfloat16_rn(v);
     p[k] = q;
     return __bfloat162float(q);
+  }
+  // paired stochastic rounding (cvt.rs.bf16x2.f32): bits 0-15 of r dither
+  // v0, bits 16-31 dither v1
+  static __device__ __forceinline__ void st2_dither(__nv_bfloat16 *p, size_t k0, size_t k1, float v0, float v1,
+                                                    uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v1), "f"(v0), "r"(r));
+    p[k0] = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
+    p[k1] = __ushort_as_bfloat16((unsigned short)(d >> 16));
   }
 };
 

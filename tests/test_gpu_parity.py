@@ -532,9 +532,12 @@ def test_fused_fluid_solute_bitwise(q, storage, size):
     """The fused fluid-solute kernel (the default with a solute) gives the
     separate streaming and solute kernels' results bit for bit, growth
     included; 100 x 70 leaves padding lanes past nx in every row."""
+    # the pressure-driven recipe: with the velocity inlet, growth closing the
+    # channel makes the run diverge (|f - w rho_ref| 0.6 at iteration 50, 33
+    # at 150 in the FP64 oracle), beyond any 16-bit range
     w = synth.reactive(size[0], size[1], seed=3, ndiscs=4, rmin=4, rmax=7, q=q, kr=0.02, bmax=0.3,
-                       growth_seed=7)
-    kw = {"h_max": 2e-2, "rounding": "stochastic"} if storage != "fp32" else {}
+                       growth_seed=7, inlet="pressure")
+    kw = {"h_max": 4e-3, "rounding": "stochastic"} if storage != "fp32" else {}
     out = []
     for kern in ("streaming", "fused"):
         lt = lb2d.from_workload(w, storage, kernel=kern, thermo=50, **kw)

@@ -44,7 +44,7 @@ def _kw(storage, w=None):
     if storage == "fp32":
         return {}
     # deviations of two phase-separated components reach about 1/2
-    return {"h_max": 1.2 if (w is not None and w.ncomp == 2) else 2e-3, "rounding": "stochastic"}
+    return {"h_max": 1.2 if (w is not None and w.ncomp == 2) else 4e-3, "rounding": "stochastic"}
 
 
 def _run(w, py, steps, storage="fp32", via_buffers=False, check_every=None):
@@ -160,7 +160,10 @@ def test_reactive_growth_slabs(q, py, storage):
     out are its own; the mask and deposit rows travel with the halo.  The
     slabs' populations, solute, deposits, masks and every step's grown
     nodes equal the whole lattice's bit for bit."""
-    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3, growth_seed=7)
+    # pressure-driven (with the velocity inlet, growth closing the channel
+    # makes the run diverge beyond any 16-bit range)
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3, growth_seed=7,
+                       inlet="pressure")
     whole, slabs = _run(w, py, 120, storage=storage, check_every=40)
     for _ in range(20):
         whole.iteration(1)
