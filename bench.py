@@ -48,8 +48,8 @@ WORKLOAD = "porous 1024x1024 (random discs r 8-24 seed 1, porosity 0.7, Zou-He r
 BYTES_PER_FLUID_NODE = {"fp32": 72, "fp16": 36, "bf16": 36}
 # measured against the FP64 oracle on this workload after its stated 10 000
 # iterations (tests/long_parity.py); the target for 16-bit storage is 2e-3
-ACCURACY_16 = {"fp16": "rel. u 7.0e-4 after 10 000 iterations: meets 2e-3",
-               "bf16": "rel. u 6.1e-3 after 10 000 iterations: misses 2e-3 (8-bit significand)"}
+ACCURACY_16 = {"fp16": "rel. u 7.3e-4 after 10 000 iterations: meets 2e-3",
+               "bf16": "rel. u 6.4e-3 after 10 000 iterations: misses 2e-3 (8-bit significand)"}
 
 
 def peaks():
@@ -534,7 +534,7 @@ def variants(args, local, stream, flush, value_fp32):
             "state_bytes": int(2 * bpn * nodes),
             "accuracy": ("rel. u <= 3.8e-6 on 8 sampled lattices after 5000 iterations (exact momentum pairs): meets 1e-5"
                          if st == "fp32" else
-                         "rel. u 5.8e-4 to 2.6e-2 on 8 sampled lattices after 5000 iterations: "
+                         "rel. u up to 1.4e-2 on 8 sampled lattices after 5000 iterations: "
                          "misses 2e-3 on the slow ones")}
         del b, lats
     out["batched_fp16"]["speedup_vs_fp32_batched"] = (out["batched"]["ms_per_iteration_batched"]

@@ -72,7 +72,7 @@ __device__ __forceinline__ void batch_warp(const BatchLat &L, const S *fin, S *f
     for (int i = 0; i < 8; i += 2) {
       r = r * 1664525u + 1013904223u;
       Store<S>::st2_dither(fout, i * P + self, (i + 1) * P + self, (h[i] + L.omega * (heq[i] - h[i])) * L.scale,
-                           (h[i + 1] + L.omega * (heq[i + 1] - h[i + 1])) * L.scale, r ^ (r >> 16));
+                           (h[i + 1] + L.omega * (heq[i + 1] - h[i + 1])) * L.scale, r);
     }
     r = r * 1664525u + 1013904223u;
     Store<S>::st_dither(fout, 8 * P + self, (h[8] + L.omega * (heq[8] - h[8])) * L.scale, r);

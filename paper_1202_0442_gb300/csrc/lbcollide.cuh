@@ -131,10 +131,10 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
     const float om = p.omega[c];
     if (!ME && SR == 2) {
       // stochastic rounding: one hash per node and component, then a
-      // linear congruential sequence, one step per pair of stores, its high
-      // half folded into the low half (the paired conversion draws the
-      // first value's dither from the low bits); the ninth store takes the
-      // single conversion's high bits
+      // linear congruential sequence, one step per pair of stores (each
+      // state is uniform for a uniformly random start, so both dithers of
+      // the paired conversion are uniform: unbiased rounding); the ninth
+      // store takes the single conversion's high bits
       uint32_t r = rnd(p.sr_seed, hself, c, 0);
       const float sc = FOLD ? 1.0f : p.scale;
 #pragma unroll
@@ -142,7 +142,7 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
         const float v0 = (h[c][i] + om * (heq[i] - h[c][i])) * sc;
         const float v1 = (h[c][i + 1] + om * (heq[i + 1] - h[c][i + 1])) * sc;
         r = r * 1664525u + 1013904223u;
-        Store<S>::st2_dither(out, i * P + self, (i + 1) * P + self, v0, v1, r ^ (r >> 16));
+        Store<S>::st2_dither(out, i * P + self, (i + 1) * P + self, v0, v1, r);
       }
       r = r * 1664525u + 1013904223u;
       Store<S>::st_dither(out, 8 * P + self, (h[c][8] + om * (heq[8] - h[c][8])) * sc, r);
