@@ -543,7 +543,8 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes);
  * whose step t is a multiple of Nf, lb_iteration writes the state as text
  * files named "<file>.<t>" (one fluid), "<file>.<t>.fluid1" and
  * "<file>.<t>.fluid2" (two fluids) and "<file>.<t>.solute" (solute).  A
- * fluid file holds the sections relaxation_time (tau alpha), domain
+ * fluid file holds the sections relaxation_time (tau; with two fluids also
+ * the density-ratio alpha), domain
  * (Nx Ny: sites 0..Nx, 0..Ny), processors, inlet/outlet (wall x0 x1 label
  * style arguments), boundary, field (force/acceleration as e1/e2 values,
  * interforce, adhesiveforce), density (x y rho style; rho = -11 on solid

@@ -3,9 +3,9 @@
 
 TEST INFRASTRUCTURE ONLY (tests).  A plain reader written from the command
 descriptions, independent of the GPU library's reader: a fluid file holds
-the sections relaxation_time (tau [alpha]), domain (Nx Ny: sites 0..Nx,
-0..Ny), processors (px py), inlet/outlet (wall x0 x1 label style
-arguments), boundary (periodic, noslip, slip, mixed R, hybrid), field
+the sections relaxation_time (tau, and alpha for two components), domain
+(Nx Ny: sites 0..Nx, 0..Ny), processors (px py), inlet/outlet (wall x0 x1
+label style arguments), boundary (periodic, noslip, slip, mixed R, hybrid), field
 (force / acceleration as e<k> value pairs, interforce G psi0 rho0,
 adhesiveforce G psi0 rho0), density (x y rho style; rho = -11 marks a solid
 site) and momentum (x y f0 .. f8); a solute file holds relaxation_time,
@@ -211,7 +211,8 @@ def oracle_from_data(file, *args, b0=0.0, seed=0):
     for c, d in enumerate(D):
         if "tau" in d:
             o.set_tau(d["tau"], c)
-        if d.get("alpha") is not None:
+        # the density-ratio parameter applies to multicomponent runs only
+        if d.get("alpha") is not None and len(D) == 2:
             o.set_alpha(d["alpha"], c)
         o.set_aveforce(*d["force"], c)
         o.set_aveacceleration(*d["acceleration"], c)

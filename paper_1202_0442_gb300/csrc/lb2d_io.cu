@@ -3,7 +3,7 @@
 //
 // A fluid file holds nine sections, each a line with the section's name
 // followed by its data lines:
-//   relaxation_time  tau [alpha]
+//   relaxation_time  tau [alpha]      (alpha: two components only)
 //   domain           Nx Ny            (sites 0..Nx x 0..Ny)
 //   processors       px py
 //   inlet / outlet   wall x0 x1 label style arguments   (one line per opening)
@@ -142,7 +142,7 @@ int write_fluid(lb_ctx *ctx, int c, const std::string &name, const std::vector<u
   if (!o.f) return ctx->fail(LB_E_ARG, "cannot write '%s'", name.c_str());
   fprintf(o.f, "relaxation_time\n");
   o.num(ctx->tau[c]);
-  o.num(ctx->alpha[c]);
+  if (ctx->nc == 2) o.num(ctx->alpha[c]);  // the density-ratio parameter of multicomponent runs
   fprintf(o.f, "\n\ndomain\n%d %d\n\nprocessors\n%d %d\n\n", nx - 1, ny - 1, ctx->px, ctx->py);
   write_openings(o, ctx, 0, c, false);
   write_openings(o, ctx, 1, c, false);
@@ -756,10 +756,8 @@ int lb_read_data(lb_ctx *ctx, const char *file, const char *args) {
     if (ctx->nc != 1) return ctx->fail(LB_E_ARG, "two fluids are read with the argument fluids");
     if (!(tau0 > 0.5)) return ctx->fail(LB_E_ARG, "tau must exceed 1/2");
     ctx->tau[0] = ctx->tau[1] = tau0;
-    if (F[0].alpha >= 0) {
-      if (!(F[0].alpha < 1.0)) return ctx->fail(LB_E_ARG, "alpha must lie in [0, 1)");
-      ctx->alpha[0] = F[0].alpha;
-    }
+    // a density-ratio parameter belongs to multicomponent runs only: a
+    // single component keeps the weights of Eq. (2)
   }
   if (F[0].px > 0) TRY(lb_processors(ctx, F[0].px, F[0].py));
   // boundary style and the solid sites (the file's sites replace the mask)
