@@ -436,10 +436,8 @@ int launch_nbcode(const uint32_t *mask, uint16_t *nbc, const Geometry &g, cudaSt
 }
 
 int launch_gradient(int storage, const GradArgs &a, cudaStream_t s) {
-  int maxlen = 0;
-  for (int k = 0; k < a.nopen; k++) maxlen = max(maxlen, a.op[k].a1 - a.op[k].a0 + 1);
-  if (!a.nopen || maxlen <= 0) return 0;
-  dim3 blk(128), grd((maxlen + 127) / 128, a.nopen);
+  if (!a.nopen || a.maxlen <= 0) return 0;
+  dim3 blk(128), grd((a.maxlen + 127) / 128, a.nopen);
   switch (storage) {
     case ST_FP16: launch_pdl(k_gradient<__half>, grd, blk, 0, s, a); break;
     case ST_BF16: launch_pdl(k_gradient<__nv_bfloat16>, grd, blk, 0, s, a); break;

@@ -120,6 +120,11 @@ OpenDesc desc_of(const lb_ctx *ctx, const Opening &o) {
   return d;
 }
 
+// where the openings lie, for the membership tests in the kernels
+void fill_spans(const lb_ctx *ctx, OpenSpan *sp) {
+  for (size_t k = 0; k < ctx->open.size(); k++) sp[k] = {ctx->open[k].wall | ctx->open[k].a0 << 2, ctx->open[k].a1};
+}
+
 int paint_check(lb_ctx *ctx) {
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   if (ctx->committed)
@@ -347,11 +352,18 @@ int commit(lb_ctx *ctx) {
     TRY(dalloc(ctx, &ctx->flip, g.plane));
     TRY(dalloc(ctx, &ctx->flist, g.plane));
     TRY(dalloc(ctx, &ctx->fcount, 2));  // [0] running count, [1] last step's
+    if (ctx->react && ctx->rank < 0) {
+      TRY(dalloc(ctx, &ctx->slist, g.plane));
+      TRY(dalloc(ctx, &ctx->scount, 1));
+      TRY(dalloc(ctx, &ctx->gdone, 1));
+    }
   }
   TRY(dalloc(ctx, &ctx->b, g.plane));
   TRY(dalloc(ctx, &ctx->removed, (size_t)(ctx->nc + 1) * g.plane));
   TRY(dalloc(ctx, &ctx->nflips, 1));
   TRY(dalloc(ctx, &ctx->errw, 1));
+  TRY(dalloc(ctx, &ctx->d_open, MAX_OPEN));
+  TRY(dalloc(ctx, &ctx->d_grad, MAX_OPEN));
   CK(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->tblocks = thermo_blocks(g, ctx->sms);
   TRY(dalloc(ctx, &ctx->partials, (size_t)ctx->tblocks * NTHERMO));
@@ -368,6 +380,21 @@ int commit(lb_ctx *ctx) {
   LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream));
   ctx->mask_host = m;
   ctx->mask_host_valid = true;
+  if (ctx->slist) {
+    // blocks for the growth gather over the surface list: one entry per
+    // thread for the initial surface (the kernel strides over any more)
+    size_t nsurf = 0;
+    for (int y = 0; y < g.ny; y++)
+      for (int x = 0; x < g.nx; x++) {
+        if (!ctx->solid[(size_t)y * g.nx + x]) continue;
+        bool wet = false;
+        for (int dy = -1; dy <= 1 && !wet; dy++)
+          for (int dx = -1; dx <= 1 && !wet; dx++)
+            wet = !ctx->solid[(size_t)((y + dy + g.ny) % g.ny) * g.nx + (x + dx + g.nx) % g.nx];
+        nsurf += wet;
+      }
+    ctx->sblocks = (int)std::min<size_t>((nsurf + 255) / 256 + 1, (size_t)4 * ctx->sms);
+  }
 
   // hybrid boundary style: per-node reflection coefficients (0 on fluid
   // nodes, so nodes that grow solid later are noslip)
@@ -486,7 +513,8 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   a.psi0 = (float)ctx->psi0;
   a.sc_rho0 = (float)ctx->sc_rho0;
   a.nopen = (int)ctx->open.size();
-  for (int k = 0; k < a.nopen; k++) a.op[k] = desc_of(ctx, ctx->open[k]);
+  fill_spans(ctx, a.span);
+  a.op = ctx->d_open;
   a.fields = fields ? ctx->fields : nullptr;
   a.uout = ctx->qs ? ctx->u : nullptr;
   uint64_t z = (uint64_t)ctx->t * 0x9e3779b97f4a7c15ULL;
@@ -577,8 +605,31 @@ int poison_outputs(lb_ctx *ctx, int nxt, bool fields) {
   return LB_OK;
 }
 
+// the opening descriptors in device memory (all openings; the gradient
+// ones), uploaded in stream order when they differ from the last upload
+int sync_openings(lb_ctx *ctx) {
+  OpenDesc all[MAX_OPEN], grad[MAX_OPEN];
+  int na = 0, ng = 0;
+  for (const Opening &o : ctx->open) {
+    all[na] = desc_of(ctx, o);
+    bool gr = false;
+    for (int c = 0; c < ctx->nc; c++) gr |= o.style[c] == OPEN_GRADIENT;
+    if (gr) grad[ng++] = all[na];
+    na++;
+  }
+  auto upload = [&](const OpenDesc *d, int n, std::vector<OpenDesc> &held, OpenDesc *dst) -> int {
+    if ((size_t)n == held.size() && (n == 0 || !memcmp(d, held.data(), n * sizeof(OpenDesc)))) return LB_OK;
+    held.assign(d, d + n);
+    if (n) CK(cudaMemcpyAsync(dst, held.data(), n * sizeof(OpenDesc), cudaMemcpyHostToDevice, ctx->stream));
+    return LB_OK;
+  };
+  TRY(upload(all, na, ctx->h_open, ctx->d_open));
+  return upload(grad, ng, ctx->h_grad, ctx->d_grad);
+}
+
 int one_step(lb_ctx *ctx, bool fields) {
   NvtxRange range("step");
+  TRY(sync_openings(ctx));
   cudaStream_t s = ctx->stream;
   ctx->t += 1;
   if (ctx->react) ctx->mask_host_valid = false;  // growth may change the device mask
@@ -609,7 +660,8 @@ int one_step(lb_ctx *ctx, bool fields) {
     sa.db = ctx->db;
     sa.Cfield = fields ? ctx->Cfield : nullptr;
     sa.nopen = (int)ctx->open.size();
-    for (int k = 0; k < sa.nopen; k++) sa.op[k] = desc_of(ctx, ctx->open[k]);
+    fill_spans(ctx, sa.span);
+    sa.op = ctx->d_open;
     sa.D = (float)((ctx->taus - 0.5) / (ctx->qs == 4 ? 2.0 : 3.0));
     sa.inter = ctx->inter ? 1 : 0;
     sa.isG = (float)ctx->isG;
@@ -639,20 +691,16 @@ int one_step(lb_ctx *ctx, bool fields) {
     LAUNCH(launch_fluid(ctx->storage, ctx->nc, ctx->sc, mass_exact, fa, s));
   }
   // gradient openings
-  GradArgs ga{};
-  int ng = 0;
-  for (const Opening &o : ctx->open) {
-    bool grad = false;
-    for (int c = 0; c < ctx->nc; c++) grad |= o.style[c] == OPEN_GRADIENT;
-    if (grad) ga.op[ng++] = desc_of(ctx, o);
-  }
-  if (ng) {
+  if (!ctx->h_grad.empty()) {
+    GradArgs ga{};
     ga.g = ctx->g;
     ga.f = ctx->fbuf[nxt];
     ga.fields = fields ? ctx->fields : nullptr;
     ga.mask = ctx->mask;
     ga.nc = ctx->nc;
-    ga.nopen = ng;
+    ga.nopen = (int)ctx->h_grad.size();
+    ga.op = ctx->d_grad;
+    for (const OpenDesc &o : ctx->h_grad) ga.maxlen = std::max(ga.maxlen, o.a1 - o.a0 + 1);
     ga.inv_scale = ctx->inv_scale;
     ga.scale = ctx->scale;
     LAUNCH(launch_gradient(ctx->storage, ga, s));
@@ -679,7 +727,8 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.rhi = ctx->rank >= 0 ? ctx->g.yhi + 1 : ctx->g.ny;
       ga2.q = ctx->qs;
       ga2.nopen = sa.nopen;
-      for (int k = 0; k < sa.nopen; k++) ga2.op[k] = sa.op[k];
+      for (int k = 0; k < sa.nopen; k++) ga2.span[k] = sa.span[k];
+      ga2.op = sa.op;
       ga2.f = ctx->fbuf[nxt];
       ga2.f_prev = ctx->fbuf[ctx->cur];
       ga2.nc = ctx->nc;
@@ -689,8 +738,18 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.gpop = ctx->gbuf[nxt];
       ga2.removed = ctx->removed;
       ga2.nflips = ctx->nflips;
-      LAUNCH(launch_growth(ga2, s));
-      LAUNCH(launch_apply_flips(ctx->storage, ga2, s));
+      if (ctx->slist) {
+        ga2.slist = ctx->slist;
+        ga2.scount = ctx->scount;
+        ga2.sblocks = ctx->sblocks;
+        ga2.done = ctx->gdone;
+        if (!ctx->slist_valid) {
+          CK(cudaMemsetAsync(ctx->scount, 0, sizeof(unsigned int), s));
+          LAUNCH(launch_surface_list(ga2, s));
+          ctx->slist_valid = true;
+        }
+      }
+      LAUNCH(launch_growth(ctx->storage, ga2, s));
     }
   }
   ctx->cur = nxt;
@@ -743,7 +802,8 @@ int lb_destroy(lb_ctx *ctx) {
                   ctx->gbuf[0], ctx->gbuf[1], ctx->Cfield,   ctx->db,       ctx->b,
                   ctx->removed, ctx->flip,    ctx->nflips,   ctx->partials, ctx->tout, ctx->tdone,
                   ctx->errw,    ctx->Cpre,    ctx->Rmap,    ctx->flist,    ctx->fcount,
-                  ctx->vstage,  ctx->nbc};
+                  ctx->vstage,  ctx->nbc,     ctx->d_open,   ctx->d_grad,   ctx->slist,
+                  ctx->scount,  ctx->gdone};
   for (void *p : ptrs) {
     bool own = p != nullptr;
     for (int k = 0; k < 6; k++) own = own && p != ctx->bound[k];
@@ -1947,6 +2007,7 @@ int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
   if (!(ctx->mask_host_valid && !memcmp(mask_src, ctx->mask_host.data(), mbytes))) {
     CK(cudaMemcpyAsync(ctx->mask, mask_src, mbytes, cudaMemcpyHostToDevice, ctx->stream));
     LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
+    ctx->slist_valid = false;
     memcpy(ctx->mask_host.data(), mask_src, mbytes);
     ctx->mask_host_valid = true;
   }

@@ -248,7 +248,7 @@ __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
   if (!(x == 0 || gy == 0 || x == g.nx - 1 || gy == g.gny - 1)) return;
 #pragma unroll 1
   for (int k = 0; k < p.nopen; k++) {
-    if (!opening_has(p.op[k], x, gy, g.nx, g.gny)) continue;
+    if (!opening_has(p.span[k], x, gy, g.nx, g.gny)) continue;
 #pragma unroll
     for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, gy, p.rho_ref[c], sc);
     break;

@@ -54,6 +54,10 @@ struct lb_ctx {
   double slipR = 0.0;
   std::vector<float> Rh[2];
   float *Rmap = nullptr;
+  // opening descriptors the kernels read (all openings; the gradient
+  // ones), uploaded when they change, and the host copies last uploaded
+  lbk::OpenDesc *d_open = nullptr, *d_grad = nullptr;
+  std::vector<lbk::OpenDesc> h_open, h_grad;
   std::vector<double> paint_f[2], paint_C;
   // nodes whose painted values are still those read by read_data (cleared
   // by the first momentum0 / concentration0 that reaches them)
@@ -90,6 +94,11 @@ struct lb_ctx {
   float *vstage = nullptr;  // lb_get_velocity_f32 staging (3 planes, kept)
   double *b = nullptr, *removed = nullptr;
   unsigned int *flip = nullptr, *flist = nullptr, *fcount = nullptr;
+  // surface list of the growth gather (whole lattice with surface reaction):
+  // rebuilt at the next step whenever the device mask is replaced
+  unsigned int *slist = nullptr, *scount = nullptr, *gdone = nullptr;
+  bool slist_valid = false;
+  int sblocks = 0;
   uint16_t *nbc = nullptr;  // per-node neighbour codes of the streaming kernel
   // host copy of the device mask words while the two are known to agree
   // (lost once growth may have changed the device mask)

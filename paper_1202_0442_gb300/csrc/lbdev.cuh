@@ -321,12 +321,15 @@ __device__ __forceinline__ void zou_he(float (&h)[9], bool dirichlet, float un_i
   h[c8] = h[c6] + tdiff + a * (1.0f / 6.0f);
 }
 
-__device__ __forceinline__ bool opening_has(const OpenDesc &o, int x, int y, int nx, int ny) {
-  switch (o.wall) {
-    case 0: return x == 0 && y >= o.a0 && y <= o.a1;
-    case 1: return x == nx - 1 && y >= o.a0 && y <= o.a1;
-    case 2: return y == 0 && x >= o.a0 && x <= o.a1;
-    default: return y == ny - 1 && x >= o.a0 && x <= o.a1;
+__device__ __forceinline__ int span_wall(const OpenSpan &s) { return s.wa0 & 3; }
+
+__device__ __forceinline__ bool opening_has(const OpenSpan &s, int x, int y, int nx, int ny) {
+  const int a0 = s.wa0 >> 2;
+  switch (s.wa0 & 3) {
+    case 0: return x == 0 && y >= a0 && y <= s.a1;
+    case 1: return x == nx - 1 && y >= a0 && y <= s.a1;
+    case 2: return y == 0 && x >= a0 && x <= s.a1;
+    default: return y == ny - 1 && x >= a0 && x <= s.a1;
   }
 }
 

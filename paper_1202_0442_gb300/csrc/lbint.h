@@ -31,6 +31,15 @@ struct OpenDesc {
   float sv;      // velocity v of the flux style
 };
 
+// where an opening lies on the lattice border: wall | a0 << 2, and a1.
+// Kept in the launch parameters for the membership tests, which every
+// border node makes; the full descriptor (64 B) is read from device memory
+// only by the opening's own nodes.
+struct OpenSpan {
+  int wa0;
+  int a1;
+};
+
 struct Geometry {
   int nx, ny, pitch, mw;  // ny: rows held (a slab: its own rows and its
                           // ghost rows); mw = pitch / 32 mask words per row
@@ -74,7 +83,9 @@ struct FluidArgs {
   float Gads[2], ads_psi0[2], ads_rho0[2];
   float G, psi0, sc_rho0; // interforce
   int nopen;
-  OpenDesc op[MAX_OPEN];
+  OpenSpan span[MAX_OPEN];
+  const OpenDesc *op;     // [nopen] descriptors in device memory (the
+                          // launch parameters stay small: launch latency)
   float *fields;          // [nc][NFIELD][plane] or nullptr
   float *uout;            // [2][plane] solvent velocity or nullptr
   uint32_t sr_seed;       // 16-bit stores: 0 = round to nearest, else the
@@ -98,7 +109,9 @@ struct GradArgs {
   const uint32_t *mask;
   int nc;
   int nopen;
-  OpenDesc op[MAX_OPEN];
+  const OpenDesc *op;     // [nopen] descriptors in device memory (the
+                          // launch parameters stay small: launch latency)
+  int maxlen;             // nodes of the longest of these openings
   float inv_scale, scale;
 };
 
@@ -117,7 +130,9 @@ struct SoluteArgs {
   float *db;              // deposit share per fluid node
   float *Cfield;          // or nullptr
   int nopen;
-  OpenDesc op[MAX_OPEN];
+  OpenSpan span[MAX_OPEN];
+  const OpenDesc *op;     // [nopen] descriptors in device memory (the
+                          // launch parameters stay small: launch latency)
   float D;                // diffusion coefficient (tau_s - 1/2)/2 or /3
   // intersolute: concentrations after streaming and the opening rules,
   // written by a first pass (Cpre_out) and read by the update (Cpre)
@@ -143,9 +158,17 @@ struct GrowthArgs {
   int rlo, rhi;           // rows whose solid nodes gather and decide (a
                           // slab: its own rows and one ghost row each side;
                           // only own-row nodes are turned solid)
+  unsigned int *slist;    // whole lattice: the solid nodes that had a fluid
+  unsigned int *scount;   // neighbour when listed (plane offsets, *scount of
+                          // them; flipped nodes are appended), or nullptr:
+                          // the rows [rlo, rhi) are scanned
+  int sblocks;            // blocks of the launch over the list
+  unsigned int *done;     // CTAs of that launch finished (0 between launches)
   int q;
   int nopen;
-  OpenDesc op[MAX_OPEN];
+  OpenSpan span[MAX_OPEN];
+  const OpenDesc *op;     // [nopen] descriptors in device memory (the
+                          // launch parameters stay small: launch latency)
   // flip application
   void *f;                // fluid populations after the step [nc][9][plane]
   void *f_prev;           // the other population buffer
@@ -201,8 +224,9 @@ bool tma_supported(int storage, const Geometry &g);
 int launch_fluid_tma(int storage, const FluidArgs &a, int *err, long long limit, cudaStream_t s, int sms);
 // one solute iteration (two kernels with intersolute: concentrations, then the update)
 int launch_solute(int q, const SoluteArgs &a, cudaStream_t s);
-int launch_growth(const GrowthArgs &a, cudaStream_t s);
-int launch_apply_flips(int storage, const GrowthArgs &a, cudaStream_t s);
+int launch_surface_list(const GrowthArgs &a, cudaStream_t s);
+// a growth step (gather, decisions and flips): one or two launches
+int launch_growth(int storage, const GrowthArgs &a, cudaStream_t s);
 // thermo grid: one block per row, at most THERMO_BLOCKS_PER_SM per SM
 constexpr int THERMO_BLOCKS_PER_SM = 4;
 int thermo_blocks(const Geometry &g, int sms);

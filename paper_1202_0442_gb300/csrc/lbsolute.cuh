@@ -15,10 +15,10 @@ template <int Q> __device__ __forceinline__ constexpr int sopp(int i) { return Q
 template <int Q> __device__ __forceinline__ constexpr float sw(int i) { return Q == 4 ? 0.25f : W9(i); }
 
 // which opening (if any) holds node (x, y)
-__device__ __forceinline__ int opening_of(const OpenDesc *op, int nopen, int x, int y, int nx, int ny) {
+__device__ __forceinline__ int opening_of(const OpenSpan *sp, int nopen, int x, int y, int nx, int ny) {
   if (!(x == 0 || y == 0 || x == nx - 1 || y == ny - 1)) return -1;
   for (int k = 0; k < nopen; k++)
-    if (opening_has(op[k], x, y, nx, ny)) return k;
+    if (opening_has(sp[k], x, y, nx, ny)) return k;
   return -1;
 }
 
@@ -80,11 +80,11 @@ template <int Q>
 __device__ float solute_streamed_C(const SoluteArgs &p, int x, int y) {
   const Geometry &g = p.g;
   if (solid_at(p.mask, g.mw, x, y)) return 0.f;
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
+  const int k = p.nopen ? opening_of(p.span, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
   float gt[Q], Cw;
   int nU;
   uint32_t U, cross;
-  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, solute_bits(p, x, y), gt, Cw, nU, U, cross);
+  solute_pull<Q>(p, x, y, k >= 0 ? span_wall(p.span[k]) : -1, solute_bits(p, x, y), gt, Cw, nU, U, cross);
   float C = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; i++) C += gt[i];
@@ -166,11 +166,11 @@ __device__ __forceinline__ void solute_node(const SoluteArgs &p, int x, int y, u
                                             float uy) {
   const Geometry &g = p.g;
   const size_t self = (size_t)y * g.pitch + x;
-  const int k = p.nopen ? opening_of(p.op, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
+  const int k = p.nopen ? opening_of(p.span, p.nopen, x, grow(g, y), g.nx, g.gny) : -1;
   float gt[Q], Cw, Cflux = 0.f;
   int nU;
   uint32_t U, cross;
-  solute_pull<Q>(p, x, y, k >= 0 ? p.op[k].wall : -1, bits, gt, Cw, nU, U, cross);
+  solute_pull<Q>(p, x, y, k >= 0 ? span_wall(p.span[k]) : -1, bits, gt, Cw, nU, U, cross);
   bool flux = false;
   if (k >= 0) flux = solute_openings<Q>(p, p.op[k], x, y, gt, cross, Cflux);
   float C = 0.f;
