@@ -262,15 +262,22 @@ template <class S>
 __global__ void __launch_bounds__(256) k_grow_list(const GrowthArgs a) {
   dep_wait();
   const Geometry &g = a.g;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  unsigned int k = blockIdx.x * blockDim.x + threadIdx.x;
+  // the thread's first entry is loaded beside the count, not after it (the
+  // list has room for every node slot, so the slot exists)
+  unsigned int self = k < (unsigned int)g.plane ? a.slist[k] : 0u;
   const unsigned int n = *a.scount;
-  for (unsigned int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const unsigned int self = a.slist[k];
+  const bool wrote = k < n;
+  while (k < n) {
     const int y = (int)(self / (unsigned int)g.pitch), x = (int)(self - (unsigned int)y * (unsigned int)g.pitch);
     if (a.q == 4) gather_grow_node<4>(a, x, y);
     else gather_grow_node<9>(a, x, y);
+    k += stride;
+    if (k < n) self = a.slist[k];
   }
   __shared__ unsigned int ticket;
-  __threadfence();
+  if (wrote) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(a.done, 1u);
   __syncthreads();

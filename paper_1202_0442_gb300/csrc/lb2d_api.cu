@@ -125,6 +125,16 @@ void fill_spans(const lb_ctx *ctx, OpenSpan *sp) {
   for (size_t k = 0; k < ctx->open.size(); k++) sp[k] = {ctx->open[k].wall | ctx->open[k].a0 << 2, ctx->open[k].a1};
 }
 
+// the openings' fluid rules for the fluid kernels (the values as desc_of
+// rounds them)
+void fill_rules(const lb_ctx *ctx, OpenRule *r) {
+  for (size_t k = 0; k < ctx->open.size(); k++) {
+    const OpenDesc d = desc_of(ctx, ctx->open[k]);
+    r[k].bits = d.style[0] | d.style[1] << 3 | d.kind << 6;
+    for (int c = 0; c < 2; c++) r[k].val[c] = d.style[c] == OPEN_DIRICHLET ? d.drho[c] : d.v[c];
+  }
+}
+
 int paint_check(lb_ctx *ctx) {
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
   if (ctx->committed)
@@ -514,7 +524,7 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   a.sc_rho0 = (float)ctx->sc_rho0;
   a.nopen = (int)ctx->open.size();
   fill_spans(ctx, a.span);
-  a.op = ctx->d_open;
+  fill_rules(ctx, a.rule);
   a.fields = fields ? ctx->fields : nullptr;
   a.uout = ctx->qs ? ctx->u : nullptr;
   uint64_t z = (uint64_t)ctx->t * 0x9e3779b97f4a7c15ULL;
@@ -728,7 +738,6 @@ int one_step(lb_ctx *ctx, bool fields) {
       ga2.q = ctx->qs;
       ga2.nopen = sa.nopen;
       for (int k = 0; k < sa.nopen; k++) ga2.span[k] = sa.span[k];
-      ga2.op = sa.op;
       ga2.f = ctx->fbuf[nxt];
       ga2.f_prev = ctx->fbuf[ctx->cur];
       ga2.nc = ctx->nc;

@@ -250,7 +250,7 @@ __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
   for (int k = 0; k < p.nopen; k++) {
     if (!opening_has(p.span[k], x, gy, g.nx, g.gny)) continue;
 #pragma unroll
-    for (int c = 0; c < NC; c++) apply_opening(p.op[k], c, h[c], x, gy, p.rho_ref[c], sc);
+    for (int c = 0; c < NC; c++) apply_opening(p.span[k], p.rule[k], c, h[c], x, gy, p.rho_ref[c], sc);
     break;
   }
 }

@@ -340,22 +340,24 @@ __device__ __forceinline__ float poiseuille(float vmax, int a0, int a1, int c) {
   return 4.0f * vmax / (L * L) * (0.25f * L * L - d * d);
 }
 
-// apply the velocity/dirichlet rule of opening o to component c's h; sc:
-// the units h is in (the rule is homogeneous of degree one in h, drho and
-// rho_ref, so scaled storage units take sc = 2^s)
-__device__ __forceinline__ void apply_opening(const OpenDesc &o, int c, float (&h)[9],
+// apply the velocity/dirichlet rule r of the opening at s to component c's
+// h; sc: the units h is in (the rule is homogeneous of degree one in h, drho
+// and rho_ref, so scaled storage units take sc = 2^s)
+__device__ __forceinline__ void apply_opening(const OpenSpan &s, const OpenRule &r, int c, float (&h)[9],
                                               int x, int y, float rho_ref, float sc = 1.0f) {
-  const int st = o.style[c];
+  const int st = (r.bits >> (3 * c)) & 7;
   if (st != OPEN_POISEUILLE && st != OPEN_UNIFORM && st != OPEN_DIRICHLET) return;
   const bool dir = (st == OPEN_DIRICHLET);
-  float un = 0.0f;
+  const int wall = span_wall(s);
+  float un = 0.0f, dr = 0.0f;
   if (!dir) {
-    const int coord = (o.wall <= 1) ? y : x;
-    const float v = (st == OPEN_UNIFORM) ? o.v[c] : poiseuille(o.v[c], o.a0, o.a1, coord);
-    un = (o.kind == 0) ? v : -v;
+    const int coord = (wall <= 1) ? y : x;
+    const float v = (st == OPEN_UNIFORM) ? r.val[c] : poiseuille(r.val[c], s.wa0 >> 2, s.a1, coord);
+    un = ((r.bits >> 6) & 1) == 0 ? v : -v;
+  } else {
+    dr = r.val[c];
   }
-  const float dr = o.drho[c];
-  switch (o.wall) {
+  switch (wall) {
     case 0: zou_he<0>(h, dir, un, dr * sc, rho_ref * sc); break;
     case 1: zou_he<1>(h, dir, un, dr * sc, rho_ref * sc); break;
     case 2: zou_he<2>(h, dir, un, dr * sc, rho_ref * sc); break;

@@ -40,6 +40,16 @@ struct OpenSpan {
   int a1;
 };
 
+// the fluid rule of an opening, in the launch parameters of the fluid
+// kernels (its own nodes read it in every iteration; from the constant bank
+// it costs no registers): styles and kind packed, and one value per
+// component, the speed (uniform) or v_max (poiseuille), or for dirichlet the
+// density minus rho_ref (a velocity rule does not use that difference)
+struct OpenRule {
+  int bits;      // style[0] | style[1] << 3 | kind << 6
+  float val[2];
+};
+
 struct Geometry {
   int nx, ny, pitch, mw;  // ny: rows held (a slab: its own rows and its
                           // ghost rows); mw = pitch / 32 mask words per row
@@ -84,8 +94,7 @@ struct FluidArgs {
   float G, psi0, sc_rho0; // interforce
   int nopen;
   OpenSpan span[MAX_OPEN];
-  const OpenDesc *op;     // [nopen] descriptors in device memory (the
-                          // launch parameters stay small: launch latency)
+  OpenRule rule[MAX_OPEN];
   float *fields;          // [nc][NFIELD][plane] or nullptr
   float *uout;            // [2][plane] solvent velocity or nullptr
   uint32_t sr_seed;       // 16-bit stores: 0 = round to nearest, else the
@@ -167,8 +176,6 @@ struct GrowthArgs {
   int q;
   int nopen;
   OpenSpan span[MAX_OPEN];
-  const OpenDesc *op;     // [nopen] descriptors in device memory (the
-                          // launch parameters stay small: launch latency)
   // flip application
   void *f;                // fluid populations after the step [nc][9][plane]
   void *f_prev;           // the other population buffer

@@ -859,6 +859,35 @@ def test_snapshot_resume_with_growth():
     assert plain.state_size() < a.state_size() // 2
 
 
+def test_snapshot_of_other_geometry_into_running_lattice():
+    """Growth after a snapshot whose mask differs from the running lattice's
+    (another geometry of the same size, taken after its own growth events):
+    the lattice that had grown its own surface before the load continues
+    bit for bit like a fresh lattice that loaded the same snapshot, and
+    both go back to their own step count (the surface the growth gather
+    visits is the loaded mask's, not the one the lattice had)."""
+    kw = dict(ndiscs=4, rmin=4, rmax=8, q=9, kr=0.02, bmax=0.3, growth_seed=7)
+    other = lb2d.from_workload(synth.reactive(128, 64, seed=5, **kw), thermo=20)
+    other.iteration(120)
+    buf = np.zeros(other.state_size(), np.uint8)
+    other.save_state(buf)
+    w = synth.reactive(128, 64, seed=3, **kw)
+    a = lb2d.from_workload(w, thermo=20)
+    a.iteration(140)
+    assert a.get_thermo()["flips"] > 0
+    assert not np.array_equal(a.mask(), other.mask())
+    a.load_state(buf)
+    b = lb2d.from_workload(w, thermo=20)
+    b.load_state(buf)
+    for lt in (a, b):
+        lt.iteration(160)
+    assert np.array_equal(a.mask(), b.mask())
+    assert np.array_equal(a.populations(), b.populations())
+    assert all(np.array_equal(x, y) for x, y in zip(a.solute_state(), b.solute_state()))
+    assert a.get_thermo() == b.get_thermo()
+    assert a.get_thermo()["flips"] > other.get_thermo()["flips"]
+
+
 @pytest.mark.parametrize("nx,ny", [(1, 24), (3, 5), (33, 2), (31, 17)])
 def test_degenerate_and_ragged_sizes(nx, ny):
     """Lattices narrower than a warp, one node wide or two high (periodic
