@@ -561,7 +561,7 @@ def variants(args, local, stream, flush, value_fp32):
     ms = float(t.mean())
     out["reactive_1024x512_q9"] = {
         "workload": "1024 x 512 channel, 40 discs, velocity inlet 0.02, D2Q9 solute, reaction and growth",
-        "kernels": "k_fluid_solute<9> (fluid and solute fused) + k_gather_grow + k_apply_flips",
+        "kernels": "k_fluid_solute<9> (fluid and solute fused) + k_grow_list (gather, decisions and flips over the surface list)",
         "value": w4.nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
         # 72 B fluid + 72 B D2Q9 solute; the fused kernel keeps the solvent
         # velocity (16 B of the unfused path) in registers
