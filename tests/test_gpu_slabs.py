@@ -178,6 +178,32 @@ def test_reactive_growth_slabs(q, py, storage):
     assert tw["flips"] > 0 and tw["flips"] == sum(s.get_thermo()["flips"] for s in slabs)
 
 
+def test_growth_surface_list_equals_row_scan_full_size():
+    """The growth step over the surface list (a whole lattice: gather,
+    decisions and flips in one launch) against the scan of every row with
+    the separate flip kernel (the same lattice held as one slab, processors
+    1 x 1), on the full 1024 x 512 reactive channel: every step's grown
+    nodes, then populations, solute state, deposits, mask and thermo bit
+    for bit after 300 iterations with growth events."""
+    w = synth.reactive(seed=1, kr=0.02, bmax=0.3, growth_seed=7, inlet="pressure")
+    whole = lb2d.from_workload(w, thermo=50)
+    one = lb2d.from_workload(w, thermo=50, slab=(1, 0))
+    grown = 0
+    for _ in range(300):
+        whole.iteration(1)
+        one.iteration(1)
+        fw = whole.flips()
+        assert np.array_equal(fw, np.sort(one.flips()))
+        grown += len(fw)
+    assert grown > 0
+    assert np.array_equal(whole.mask(), one.mask())
+    assert np.array_equal(whole.populations(1), one.populations(1))
+    for a, b in zip(whole.solute_state(), one.solute_state()):
+        assert np.array_equal(a, b)
+    assert whole.get_thermo() == one.get_thermo()
+    assert whole.get_thermo()["flips"] == grown
+
+
 def test_halo_messages_through_buffers():
     """The exchange through packed device buffers (the messages a
     multi-GPU run sends over NCCL) gives the same bits."""
