@@ -261,7 +261,9 @@ int lb_obstacle_mask_hybrid(lb_ctx *ctx, const uint8_t *mask, const double *R);
  * spanning a0..a1 along it (y for x-walls, x for y-walls).  label1 names
  * it for fluid 1 (and the solute), label2 for fluid 2 (NULL with one
  * component).  Openings on one wall may not overlap; two walls may not
- * both have an opening on a shared corner node. */
+ * both have an opening on a shared corner node.  At most 8 openings per
+ * lattice (LB_E_UNSUPPORTED beyond: where each lies and its fluid rule
+ * travel in the kernels' launch parameters). */
 int lb_inlet(lb_ctx *ctx, const char *wall, int a0, int a1,
              const char *label1, const char *label2);
 int lb_outlet(lb_ctx *ctx, const char *wall, int a0, int a1,

@@ -163,6 +163,38 @@ def test_reversed_openings():
         assert rel_rho(lt, o, w) < TOL32
 
 
+def _eight_openings(n=8):
+    """A channel (solid rows y = 0 and y = 41) with four inlets of mixed
+    styles along x = 0 and four outlets along x = 39, ten nodes each."""
+    nx, ny = 40, 42
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    ins = [("uniform", 0.02, 1.0), ("poiseuille", 0.03, 1.0), ("dirichlet", 0.0, 1.002), ("uniform", 0.01, 1.0)]
+    outs = [("dirichlet", 0.0, 1.0), ("dirichlet", 0.0, 1.0005), ("uniform", 0.015, 1.0), ("poiseuille", 0.02, 1.0)]
+    ops = [synth.Opening("xlo", 1 + 10 * k, 10 + 10 * k, "inlet", [ins[k]]) for k in range(4)]
+    ops += [synth.Opening("xhi", 1 + 10 * k, 10 + 10 * k, "outlet", [outs[k]]) for k in range(4)]
+    if n > 8:
+        ops.append(synth.Opening("ylo", 18, 22, "inlet", [("uniform", 0.01, 1.0)]))
+    return synth.Workload(name="open8", nx=nx, ny=ny, solid=solid, rho=[np.where(solid, 0, 1.0)], tau=(0.8,),
+                          openings=ops)
+
+
+def test_eight_openings():
+    """Eight openings, the most a lattice takes (each one's place and fluid
+    rule sit in the kernels' launch parameters, every slot used here), four
+    inlet and four outlet styles side by side, against the oracle; a ninth
+    opening is refused."""
+    w = _eight_openings()
+    lt, o = run_pair(w, 300)
+    assert rel_rho(lt, o, w) < TOL32
+    assert rel_u(lt, o) < TOL32
+    e, _ = pop_err(lt, o)
+    assert e < TOL32, e
+    with pytest.raises(lb2d.LBError) as ei:
+        lb2d.from_workload(_eight_openings(9))
+    assert ei.value.code == lb2d.LB_E_UNSUPPORTED
+
+
 def test_porous_config2_small():
     """Config-2 recipe at 128 x 128 (dirichlet 1.001 / 1.0, discs, periodic
     y), 400 iterations."""
