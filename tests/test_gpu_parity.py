@@ -195,6 +195,30 @@ def test_eight_openings():
     assert ei.value.code == lb2d.LB_E_UNSUPPORTED
 
 
+@pytest.mark.parametrize("q", [4, 9])
+def test_eight_openings_with_solute(q):
+    """The eight openings carrying a solute (its rules read the openings'
+    descriptors from device memory): dirichlet, flux and adiabatic styles
+    mixed over the four inlets and four outlets, solute and fluid against
+    the oracle."""
+    w = _eight_openings()
+    sol_in = [("dirichlet", 1.0), ("flux", 0.8, 0.02), ("dirichlet", 0.6), ("flux", 1.2, 0.01)]
+    sol_out = [("adiabatic", 0.0), ("dirichlet", 0.2), ("adiabatic", 0.0), ("flux", 0.5, 0.6)]
+    for k, op in enumerate(w.openings):
+        op.solute = sol_in[k] if k < 4 else sol_out[k - 4]
+    w.solute_q, w.taus = q, 0.75
+    w.C = np.where(w.solid, 0.0, 0.5)
+    lt, o = run_pair(w, 300)
+    assert rel_rho(lt, o, w) < TOL32
+    assert rel_u(lt, o) < TOL32
+    _, Cg, _ = lt.solute_state(g=False, b=False)
+    Co = o.solute_C()
+    fl = o.solid() == 0
+    assert np.max(np.abs(Cg[fl] - Co[fl])) / np.max(np.abs(Co[fl])) < TOL32
+    errs, _, _ = thermo_err(lt, o, ["solute"])
+    assert errs["solute"] < 1e-6, errs
+
+
 def test_porous_config2_small():
     """Config-2 recipe at 128 x 128 (dirichlet 1.001 / 1.0, discs, periodic
     y), 400 iterations."""
