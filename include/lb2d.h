@@ -435,6 +435,22 @@ int lb_iteration(lb_ctx *ctx, int Nt);
 /* Thermo record of the last thermo evaluation. */
 int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out);
 
+/* Thermo evaluations that do not stop the host (no counterpart in the
+ * paper, whose thermo command prints at once).  By default (on = 0) every
+ * thermo evaluation copies its record to the host and waits for it, so
+ * lb_iteration returns LB_E_NAN or LB_E_TIMEOUT from the iteration that
+ * found it.  With on = 1 the record is copied, in stream order, to
+ * page-locked host memory of the context (allocated by the first such
+ * call) and read later, without the host waiting for the GPU to catch up:
+ * by the next thermo evaluation before it runs (the record is then a
+ * thermo interval old), by lb_get_thermo and lb_thermo_static, and by
+ * lb_thermo_deferred(ctx, 0).  Those calls then return the record's
+ * LB_E_NAN or LB_E_TIMEOUT: the error of a thermo step reaches the caller
+ * with the next of them, after the iterations queued since have run.  The
+ * records and the thermo kernel are the same in both modes, bit for bit.
+ * LB_E_ARG unless on is 0 or 1. */
+int lb_thermo_deferred(lb_ctx *ctx, int on);
+
 /* Recompute the thermo record of the context's last thermo evaluation
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that cannot let the library allocate device memory -- when a

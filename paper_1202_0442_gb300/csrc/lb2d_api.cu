@@ -542,26 +542,9 @@ FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   return a;
 }
 
-int run_thermo(lb_ctx *ctx) {
-  NvtxRange range("thermo");
-  ThermoArgs ta{};
-  ta.g = ctx->g;
-  ta.mask = ctx->mask;
-  ta.fields = ctx->fields;
-  ta.nc = ctx->nc;
-  ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
-  ta.b = ctx->react ? ctx->b : nullptr;
-  ta.removed = ctx->react ? ctx->removed : nullptr;
-  ta.partials = ctx->partials;
-  ta.out = ctx->tout;
-  ta.done = ctx->tdone;
-  ta.nflips = ctx->nflips;
-  ta.errw = ctx->errw;
-  LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
-  // one record: the sums, the flip count (64 bits), the TMA error word
-  double rec[NTHERMO + 2];
-  CK(cudaMemcpyAsync(rec, ctx->tout, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+// the thermo record of step `step` (the sums, the flip count, the TMA
+// error word) into ctx->thermo; its LB_E_TIMEOUT or LB_E_NAN
+int decode_thermo(lb_ctx *ctx, const double *rec, int64_t step) {
   const double *h = rec;
   unsigned long long nfl = 0;
   memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
@@ -570,11 +553,11 @@ int run_thermo(lb_ctx *ctx) {
     // reported once: the word is cleared for the iterations that follow
     CK(cudaMemsetAsync(ctx->errw, 0, sizeof(int), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
+    return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)step);
   }
   lb_thermo_t &T = ctx->thermo;
   memset(&T, 0, sizeof T);
-  T.step = ctx->t;
+  T.step = step;
   T.nsolid = (int64_t)llround(h[13]);
   T.nfluid = (int64_t)llround(h[14]);
   for (int c = 0; c < ctx->nc; c++) {
@@ -593,8 +576,59 @@ int run_thermo(lb_ctx *ctx) {
   T.flips = (int64_t)nfl;
   ctx->thermo_valid = true;
   for (int q = 0; q < NTHERMO; q++)
-    if (!std::isfinite(h[q])) return ctx->fail(LB_E_NAN, "thermo sum %d is not finite at step %lld", q, (long long)ctx->t);
+    if (!std::isfinite(h[q])) return ctx->fail(LB_E_NAN, "thermo sum %d is not finite at step %lld", q, (long long)step);
   return LB_OK;
+}
+
+// deferred records: read the oldest one waiting (after its copy has landed)
+int read_deferred(lb_ctx *ctx) {
+  const int slot = ctx->tq[0];
+  ctx->tq[0] = ctx->tq[1];
+  ctx->tq_n--;
+  CK(cudaEventSynchronize(ctx->trec_ev[slot]));
+  return decode_thermo(ctx, ctx->trec_host + (size_t)slot * (NTHERMO + 2), ctx->trec_step[slot]);
+}
+
+// ... every one waiting, in step order
+int read_all_deferred(lb_ctx *ctx) {
+  while (ctx->tq_n) TRY(read_deferred(ctx));
+  return LB_OK;
+}
+
+int run_thermo(lb_ctx *ctx) {
+  NvtxRange range("thermo");
+  ThermoArgs ta{};
+  ta.g = ctx->g;
+  ta.mask = ctx->mask;
+  ta.fields = ctx->fields;
+  ta.nc = ctx->nc;
+  ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
+  ta.b = ctx->react ? ctx->b : nullptr;
+  ta.removed = ctx->react ? ctx->removed : nullptr;
+  ta.partials = ctx->partials;
+  ta.out = ctx->tout;
+  ta.done = ctx->tdone;
+  ta.nflips = ctx->nflips;
+  ta.errw = ctx->errw;
+  // deferred records of earlier thermo evaluations are read first (at
+  // least one thermo interval old, their copies have long landed); their
+  // errors are this call's
+  if (ctx->tdefer) TRY(read_all_deferred(ctx));
+  LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
+  if (ctx->tdefer) {
+    const int slot = ctx->tq_next;
+    ctx->tq_next ^= 1;
+    CK(cudaMemcpyAsync(ctx->trec_host + (size_t)slot * (NTHERMO + 2), ctx->tout, (NTHERMO + 2) * sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->trec_ev[slot], ctx->stream));
+    ctx->trec_step[slot] = ctx->t;
+    ctx->tq[ctx->tq_n++] = slot;
+    return LB_OK;
+  }
+  double rec[NTHERMO + 2];
+  CK(cudaMemcpyAsync(rec, ctx->tout, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return decode_thermo(ctx, rec, ctx->t);
 }
 
 // LB_DEBUG_POISON: NaN bit patterns (all ones: NaN in FP32, FP16 and
@@ -821,6 +855,9 @@ int lb_destroy(lb_ctx *ctx) {
       if (gd.user == p) p = gd.raw;
     cudaFree(p);
   }
+  for (int k = 0; k < 2; k++)
+    if (ctx->trec_ev[k]) cudaEventDestroy(ctx->trec_ev[k]);
+  if (ctx->trec_host) cudaFreeHost(ctx->trec_host);
   delete ctx;
   return LB_OK;
 }
@@ -1504,6 +1541,22 @@ int lb_thermo(lb_ctx *ctx, int Nf) {
   return LB_OK;
 }
 
+int lb_thermo_deferred(lb_ctx *ctx, int on) {
+  NEED_CTX();
+  if (on != 0 && on != 1) return ctx->fail(LB_E_ARG, "on must be 0 or 1");
+  if (on && !ctx->trec_host) {
+    TRY(set_device(ctx));
+    CK(cudaHostAlloc((void **)&ctx->trec_host, 2 * (NTHERMO + 2) * sizeof(double), cudaHostAllocDefault));
+    for (int k = 0; k < 2; k++) CK(cudaEventCreateWithFlags(&ctx->trec_ev[k], cudaEventDisableTiming));
+  }
+  if (!on && ctx->tq_n) {
+    TRY(set_device(ctx));
+    TRY(read_all_deferred(ctx));
+  }
+  ctx->tdefer = on != 0;
+  return LB_OK;
+}
+
 int lb_iteration(lb_ctx *ctx, int Nt) {
   NEED_CTX();
   NvtxRange range("lb_iteration");
@@ -1549,6 +1602,10 @@ int lb_iteration(lb_ctx *ctx, int Nt) {
 int lb_get_thermo(lb_ctx *ctx, lb_thermo_t *out) {
   NEED_CTX();
   if (!out) return ctx->fail(LB_E_ARG, "null output");
+  if (ctx->tq_n) {
+    TRY(set_device(ctx));
+    TRY(read_all_deferred(ctx));
+  }
   if (!ctx->thermo_valid) return ctx->fail(LB_E_ORDER, "no thermo record yet: call lb_iteration first");
   *out = ctx->thermo;
   return LB_OK;
@@ -2494,6 +2551,10 @@ std::mutex g_thermo_scratch_mu;
 extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
   NEED_CTX();
   if (!out) return ctx->fail(LB_E_ARG, "null output");
+  if (ctx->tq_n) {
+    TRY(set_device(ctx));
+    TRY(read_all_deferred(ctx));
+  }
   if (!ctx->fields_valid || !ctx->thermo_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
   // the field planes must describe the live state: written by the last
   // iteration executed, with no state replaced and no step count set since

@@ -129,6 +129,14 @@ struct lb_ctx {
   int64_t fields_step = -1;  // iteration whose end state the field planes hold
   lb_thermo_t thermo{};
   bool thermo_valid = false;
+  // lb_thermo_deferred: records copied to page-locked host memory in stream
+  // order (two slots, an event after each copy) and read, oldest first,
+  // when a call needs them
+  bool tdefer = false;
+  double *trec_host = nullptr;  // [2][NTHERMO + 2]
+  cudaEvent_t trec_ev[2] = {nullptr, nullptr};
+  int64_t trec_step[2] = {0, 0};
+  int tq[2] = {0, 0}, tq_n = 0, tq_next = 0;
 
   // read_data command: the state read from input-data files, applied when
   // the device state is created (kind 1: populations a; kind 2: the

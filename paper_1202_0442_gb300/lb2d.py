@@ -109,6 +109,7 @@ SIGNATURES = {
     "lb_set_debug": (I, [P, I]),
     "lb_debug_check": (I, [P, C.POINTER(C.c_int64)]),
     "lb_thermo": (I, [P, I]),
+    "lb_thermo_deferred": (I, [P, I]),
     "lb_output": (I, [P, I]),
     "lb_iteration": (I, [P, I]),
     "lb_get_thermo": (I, [P, C.POINTER(Thermo)]),
@@ -398,6 +399,11 @@ class Lattice:
 
     def thermo(self, Nf: int):
         self._ck(self._L.lb_thermo(self._h, Nf))
+
+    def thermo_deferred(self, on: bool = True):
+        """Thermo records read by the next thermo evaluation or get_thermo
+        instead of waited for at each thermo step (lb_thermo_deferred)."""
+        self._ck(self._L.lb_thermo_deferred(self._h, 1 if on else 0))
 
     def iteration(self, Nt: int):
         self._ck(self._L.lb_iteration(self._h, Nt))

@@ -988,6 +988,46 @@ def test_nan_is_reported():
     assert ei.value.code == lb2d.LB_E_NAN
 
 
+def test_deferred_thermo_records_match():
+    """Deferred thermo records (read when a call needs them; the host does
+    not wait at a thermo step) equal the waited-for records bit for bit: on
+    a reactive lattice with growth, thermo every 7 iterations, after calls
+    of mixed lengths (one thermo step, several, none), and after switching
+    back."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, kr=0.02, bmax=0.3, growth_seed=7)
+    a = lb2d.from_workload(w, thermo=7)
+    b = lb2d.from_workload(w, thermo=7)
+    b.thermo_deferred(True)
+    for n in (7, 1, 6, 3, 14, 1, 1, 30, 2, 150):
+        a.iteration(n)
+        b.iteration(n)
+        assert a.get_thermo() == b.get_thermo()
+    assert a.get_thermo()["flips"] > 0
+    assert np.array_equal(a.populations(), b.populations())
+    b.thermo_deferred(False)
+    a.iteration(7)
+    b.iteration(7)
+    assert a.get_thermo() == b.get_thermo()
+
+
+def test_deferred_thermo_reports_nan_at_next_call():
+    """A non-finite thermo sum found by a deferred record is returned by the
+    next call that reads it: lb_get_thermo, or the next thermo evaluation
+    (here the last iteration of the next lb_iteration call)."""
+    w = synth.channel(32, 16, 1.0, 0.0)
+    for reader in ("get_thermo", "iteration"):
+        lt = lb2d.from_workload(w)
+        lt.thermo_deferred(True)
+        f = lt.populations()
+        f[3, 5, 7] = np.nan
+        lt.set_populations(f)
+        lt.iteration(3)
+        with pytest.raises(lb2d.LBError) as ei:
+            lt.get_thermo() if reader == "get_thermo" else lt.iteration(1)
+        assert ei.value.code == lb2d.LB_E_NAN
+    assert lt._L.lb_thermo_deferred(lt._h, 2) == lb2d.LB_E_ARG
+
+
 def test_order_and_argument_errors():
     E = lb2d.LBError
     lt = lb2d.Lattice()

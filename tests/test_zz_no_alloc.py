@@ -77,3 +77,18 @@ def test_static_thermo_refuses_fields_of_another_state():
     assert ref["step"] == 28
     for _ in range(2):
         _same(lt.thermo_static(), ref)
+
+
+def test_static_thermo_reads_deferred_record_first():
+    """With deferred thermo records the call reads the record still waiting
+    in host memory before it checks and recomputes: called first after the
+    iteration, it still equals lb_get_thermo's record."""
+    w = synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=9, kr=0.02, bmax=0.3)
+    lt = lb2d.from_workload(w)
+    lt.thermo_deferred(True)
+    for steps in (30, 17):
+        lt.iteration(steps)
+        first = lt.thermo_static()
+        _same(first, lt.get_thermo())
+        assert first["step"] == 30 if steps == 30 else first["step"] == 47
+
