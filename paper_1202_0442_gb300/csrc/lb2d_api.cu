@@ -7,8 +7,12 @@
 // state on the host, moves it to the GPU at the first call that needs
 // device memory, and then drives each iteration as a fixed sequence of
 // kernel launches on the caller's stream:
-//   fluid (k_fluid_local or k_fluid_sc) -> gradient openings -> solute ->
-//   precipitation gather + growth decisions -> flips -> [thermo]
+//   fluid (k_fluid_local, k_fluid_sc or the fused k_fluid_solute) ->
+//   gradient openings -> solute -> growth (gather, decisions and flips) ->
+//   [thermo]
+// Slabs and their halo exchange are in lb2d_slab.cu, snapshots in
+// lb2d_state.cu, batched lattices in lb2d_batch.cu, the allocation-free
+// thermo call in lb2d_static.cu, the input-data text files in lb2d_io.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -19,6 +23,7 @@
 #include <vector>
 
 #include "lb2d.h"
+#include "lbapi.h"
 #include "lbbatch.h"
 #include "lbctx.h"
 #include "lbint.h"
@@ -26,13 +31,6 @@
 using namespace lbk;
 
 namespace {
-
-const double W9D[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                       1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-const int EXD[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-const int EYD[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-const int EX4D[4] = {1, 0, -1, 0};
-const int EY4D[4] = {0, 1, 0, -1};
 
 int wall_of(const char *s) {
   if (!s) return -1;
@@ -43,7 +41,11 @@ int wall_of(const char *s) {
   return -1;
 }
 
+}  // namespace
+
 size_t storage_bytes(int st) { return st == ST_FP32 ? 4 : 2; }
+
+namespace {
 
 // equilibrium population i at density rho and velocity (ux, uy) (FP64,
 // host side), with the density-ratio rest share of the fluids command
@@ -53,13 +55,15 @@ double feq_host(int i, double rho, double ux, double uy, double alpha) {
                             : wshare(i, alpha) * rho + W9D[i] * rho * (3 * eu + 4.5 * eu * eu - 1.5 * usq);
 }
 
-int exchange_slabs(lb_ctx *const *ctxs, int n);  // slabs: halo rows (below)
+}  // namespace
 
 int set_device(lb_ctx *ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaSetDevice");
   return LB_OK;
 }
+
+namespace {
 
 bool fluid_ok(lb_ctx *ctx, int fluid) { return fluid >= 1 && fluid <= ctx->nc; }
 
@@ -321,6 +325,8 @@ int validate(lb_ctx *ctx) {
 }
 
 // allocate the device state and upload geometry and the painted state
+}  // namespace
+
 int commit(lb_ctx *ctx) {
   if (ctx->committed) return LB_OK;
   if (!ctx->have_lattice) return ctx->fail(LB_E_ORDER, "lattice must come first");
@@ -495,6 +501,8 @@ int commit(lb_ctx *ctx) {
   return LB_OK;
 }
 
+namespace {
+
 FluidArgs fluid_args(lb_ctx *ctx, bool fields) {
   FluidArgs a{};
   a.g = ctx->g;
@@ -590,10 +598,14 @@ int read_deferred(lb_ctx *ctx) {
 }
 
 // ... every one waiting, in step order
+}  // namespace
+
 int read_all_deferred(lb_ctx *ctx) {
   while (ctx->tq_n) TRY(read_deferred(ctx));
   return LB_OK;
 }
+
+namespace {
 
 int run_thermo(lb_ctx *ctx) {
   NvtxRange range("thermo");
@@ -1820,820 +1832,3 @@ int lb_get_flips(lb_ctx *ctx, int64_t *idx, int cap, int *count) {
 
 
 }  // extern "C"
-
-// ======================================================================
-// slabs (processors command): the halo rows between neighbouring slabs
-// ======================================================================
-
-namespace {
-
-struct Run {
-  uint8_t *p;
-  size_t bytes;
-};
-
-// The rows of the current state buffers across face `face` of a slab (0:
-// its low-y side, 1: its high-y side): the rows it sends (ghost = false:
-// its first or last `halo` own rows) or the ghost rows it receives into
-// (ghost = true), one run per population plane.  With one ghost row only
-// the populations the pull takes across the face travel (e_y = +1 for data
-// moving towards +y, e_y = -1 for data moving towards -y); with two ghost
-// rows every population does.
-void face_runs(lb_ctx *ctx, int face, bool ghost, std::vector<Run> &runs) {
-  runs.clear();
-  const Geometry &g = ctx->g;
-  const int H = ctx->halo;
-  const size_t r0 = (size_t)(face == 0 ? (ghost ? 0 : g.ylo) : (ghost ? g.yhi : g.yhi - H));
-  const int dir = ((face == 1) != ghost) ? 1 : -1;  // e_y of the data crossing
-  const size_t row = (size_t)g.pitch, sb = storage_bytes(ctx->storage);
-  for (int c = 0; c < ctx->nc; c++)
-    for (int q = 0; q < 9; q++)
-      if (H > 1 || EYD[q] == dir)
-        runs.push_back({(uint8_t *)ctx->fbuf[ctx->cur] + (((size_t)c * 9 + q) * g.plane + r0 * row) * sb, H * row * sb});
-  for (int q = 0; q < ctx->qs; q++) {
-    const int ey = ctx->qs == 4 ? EY4D[q] : EYD[q];
-    if (H > 1 || ey == dir)
-      runs.push_back({(uint8_t *)ctx->gbuf[ctx->cur] + ((size_t)q * g.plane + r0 * row) * 4, H * row * 4});
-  }
-  if (ctx->react) {
-    // growth changes the mask and the deposits: their rows travel too
-    runs.push_back({(uint8_t *)(ctx->mask + r0 * g.mw), H * (size_t)g.mw * 4});
-    runs.push_back({(uint8_t *)(ctx->b + r0 * row), H * row * 8});
-  }
-}
-
-// after ghost rows of a slab with surface reaction changed (face 0, 1 or
-// -1 both), the neighbour codes of the rows whose 3 x 3 neighbourhood
-// reaches them
-int refresh_codes(lb_ctx *ctx, int face) {
-  if (!ctx->react) return LB_OK;
-  const Geometry &g = ctx->g;
-  if (face != 1) LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream, 0, g.ylo + 1));
-  if (face != 0) LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, g, ctx->stream, g.yhi - 1, g.ny));
-  return LB_OK;
-}
-
-// device-to-device copies src[k] -> dst[k] of bytes[k], MAX_RUNS per launch
-int copy_runs(lb_ctx *ctx, const std::vector<const void *> &src, const std::vector<void *> &dst,
-              const std::vector<size_t> &bytes) {
-  for (size_t k0 = 0; k0 < src.size(); k0 += MAX_RUNS) {
-    CopyRuns r{};
-    r.n = (int)std::min(src.size() - k0, (size_t)MAX_RUNS);
-    for (int k = 0; k < r.n; k++) {
-      r.src[k] = src[k0 + k];
-      r.dst[k] = dst[k0 + k];
-      r.bytes[k] = (unsigned)bytes[k0 + k];
-    }
-    LAUNCH(launch_copy_runs(r, ctx->stream));
-  }
-  return LB_OK;
-}
-
-int slab_check(lb_ctx *ctx) {
-  if (ctx->rank < 0) return ctx->fail(LB_E_ORDER, "not a slab: call lb_processors(1, py) and lb_processor_rank first");
-  if (!ctx->committed) return ctx->fail(LB_E_ORDER, "the slab has no device state yet: set its initial state first");
-  return LB_OK;
-}
-
-// every slab's first and last own rows into its neighbours' ghost rows
-// (periodic in y: slab py - 1 and slab 0 are neighbours)
-int exchange_slabs(lb_ctx *const *ctxs, int n) {
-  std::vector<const void *> src;
-  std::vector<void *> dst;
-  std::vector<size_t> bytes;
-  std::vector<Run> a, b;
-  for (int r = 0; r < n; r++) {
-    for (int face = 0; face < 2; face++) {
-      lb_ctx *to = ctxs[face == 1 ? (r + 1) % n : (r + n - 1) % n];
-      face_runs(ctxs[r], face, false, a);
-      face_runs(to, 1 - face, true, b);
-      for (size_t k = 0; k < a.size(); k++) {
-        src.push_back(a[k].p);
-        dst.push_back(b[k].p);
-        bytes.push_back(a[k].bytes);
-      }
-    }
-  }
-  TRY(copy_runs(ctxs[0], src, dst, bytes));
-  for (int r = 0; r < n; r++) TRY(refresh_codes(ctxs[r], -1));
-  return LB_OK;
-}
-
-// offset of each run in a packed halo message (16-byte aligned)
-size_t pad16(size_t n) { return (n + 15) / 16 * 16; }
-
-}  // namespace
-
-extern "C" {
-
-int lb_halo_size(lb_ctx *ctx, size_t *bytes) {
-  NEED_CTX();
-  if (!bytes) return ctx->fail(LB_E_ARG, "null output");
-  TRY(slab_check(ctx));
-  std::vector<Run> runs;
-  face_runs(ctx, 1, false, runs);
-  size_t n = 0;
-  for (const Run &r : runs) n += pad16(r.bytes);
-  *bytes = n;
-  return LB_OK;
-}
-
-static int halo_move(lb_ctx *ctx, int face, void *buf, bool pack) {
-  NEED_CTX();
-  TRY(slab_check(ctx));
-  if (face != 0 && face != 1) return ctx->fail(LB_E_ARG, "face must be 0 (low y) or 1 (high y)");
-  if (!buf || (uintptr_t)buf % 16) return ctx->fail(LB_E_ARG, "halo buffer must be a 16-byte aligned device pointer");
-  TRY(set_device(ctx));
-  std::vector<Run> runs;
-  face_runs(ctx, face, !pack, runs);
-  std::vector<const void *> src;
-  std::vector<void *> dst;
-  std::vector<size_t> bytes;
-  size_t off = 0;
-  for (const Run &r : runs) {
-    uint8_t *b = (uint8_t *)buf + off;
-    src.push_back(pack ? (const void *)r.p : (const void *)b);
-    dst.push_back(pack ? (void *)b : (void *)r.p);
-    bytes.push_back(r.bytes);
-    off += pad16(r.bytes);
-  }
-  TRY(copy_runs(ctx, src, dst, bytes));
-  return pack ? LB_OK : refresh_codes(ctx, face);
-}
-
-int lb_halo_pack(lb_ctx *ctx, int face, void *buf) { return halo_move(ctx, face, buf, true); }
-
-int lb_halo_unpack(lb_ctx *ctx, int face, const void *buf) { return halo_move(ctx, face, (void *)buf, false); }
-
-int lb_exchange(lb_ctx *const *ctxs, int n) {
-  NvtxRange range("lb_exchange");
-  if (!ctxs || n < 1) return LB_E_ARG;
-  for (int r = 0; r < n; r++)
-    if (!ctxs[r]) return LB_E_ARG;
-  lb_ctx *c0 = ctxs[0];
-  for (int r = 0; r < n; r++) {
-    lb_ctx *c = ctxs[r];
-    TRY(slab_check(c));
-    if (c->rank != r || c->py != n)
-      return c->fail(LB_E_ARG, "lb_exchange takes the %d slabs of one lattice in rank order", c->py);
-    if (c->nx != c0->nx || c->ny != c0->ny || c->nc != c0->nc || c->qs != c0->qs || c->storage != c0->storage ||
-        c->halo != c0->halo || c->cur != c0->cur || c->t != c0->t)
-      return c->fail(LB_E_ARG, "slab %d does not belong to the same lattice and step as slab 0", r);
-    if (c->device != c0->device || c->stream != c0->stream)
-      return c->fail(LB_E_UNSUPPORTED, "lb_exchange moves rows within one device and stream; "
-                     "across devices use lb_halo_pack/lb_halo_unpack");
-  }
-  TRY(set_device(c0));
-  return exchange_slabs(ctxs, n);
-}
-
-}  // extern "C"
-
-extern "C" {
-
-// snapshot layout: header, populations (current buffer), mask, solute
-// populations, and with surface_reaction the precipitate, removed tallies
-// and flip count (without it they stay zero and are not part of the state)
-struct SnapHeader {
-  uint64_t magic, nx, ny, nc, qs, storage, t;
-};
-static const uint64_t SNAP_MAGIC = 0x4c42324453543031ULL;  // "LB2DST01"
-
-static void snap_parts(lb_ctx *ctx, std::vector<std::pair<void *, size_t>> &parts) {
-  const Geometry &g = ctx->g;
-  parts.clear();
-  parts.push_back({ctx->fbuf[ctx->cur], (size_t)ctx->nc * 9 * g.plane * storage_bytes(ctx->storage)});
-  parts.push_back({ctx->mask, (size_t)g.ny * g.mw * 4});
-  if (ctx->qs) parts.push_back({ctx->gbuf[ctx->cur], (size_t)ctx->qs * g.plane * 4});
-  if (ctx->react) {
-    parts.push_back({ctx->b, g.plane * 8});
-    parts.push_back({ctx->removed, (size_t)(ctx->nc + 1) * g.plane * 8});
-    parts.push_back({ctx->nflips, 8});
-  }
-}
-
-int lb_state_size(lb_ctx *ctx, size_t *bytes) {
-  NEED_CTX();
-  if (!bytes) return ctx->fail(LB_E_ARG, "null output");
-  TRY(commit(ctx));
-  std::vector<std::pair<void *, size_t>> parts;
-  snap_parts(ctx, parts);
-  size_t n = sizeof(SnapHeader);
-  for (auto &p : parts) n += p.second;
-  *bytes = n;
-  return LB_OK;
-}
-
-int lb_save_state(lb_ctx *ctx, void *host, size_t bytes) {
-  NEED_CTX();
-  size_t need = 0;
-  TRY(lb_state_size(ctx, &need));
-  if (!host || bytes != need) return ctx->fail(LB_E_ARG, "snapshot buffer must be %zu bytes", need);
-  TRY(set_device(ctx));
-  SnapHeader h{SNAP_MAGIC, (uint64_t)ctx->nx, (uint64_t)ctx->ny, (uint64_t)ctx->nc, (uint64_t)ctx->qs,
-               (uint64_t)ctx->storage, (uint64_t)ctx->t};
-  memcpy(host, &h, sizeof h);
-  std::vector<std::pair<void *, size_t>> parts;
-  snap_parts(ctx, parts);
-  size_t off = sizeof h;
-  for (auto &p : parts) {
-    CK(cudaMemcpyAsync((uint8_t *)host + off, p.first, p.second, cudaMemcpyDeviceToHost, ctx->stream));
-    off += p.second;
-  }
-  CK(cudaStreamSynchronize(ctx->stream));
-  return LB_OK;
-}
-
-int lb_load_state(lb_ctx *ctx, const void *host, size_t bytes) {
-  NEED_CTX();
-  ctx->fields_step = -1;  // the live state no longer matches the field planes
-  size_t need = 0;
-  TRY(lb_state_size(ctx, &need));
-  if (!host || bytes != need) return ctx->fail(LB_E_ARG, "snapshot must be %zu bytes", need);
-  SnapHeader h;
-  memcpy(&h, host, sizeof h);
-  if (h.magic != SNAP_MAGIC || h.nx != (uint64_t)ctx->nx || h.ny != (uint64_t)ctx->ny ||
-      h.nc != (uint64_t)ctx->nc || h.qs != (uint64_t)ctx->qs || h.storage != (uint64_t)ctx->storage)
-    return ctx->fail(LB_E_ARG, "snapshot does not match this lattice");
-  TRY(set_device(ctx));
-  std::vector<std::pair<void *, size_t>> parts;
-  snap_parts(ctx, parts);
-  size_t off = sizeof h;
-  const uint8_t *mask_src = nullptr;
-  for (auto &p : parts) {
-    if (p.first == (void *)ctx->mask)
-      mask_src = (const uint8_t *)host + off;  // below, once the other copies are queued
-    else
-      CK(cudaMemcpyAsync(p.first, (const uint8_t *)host + off, p.second, cudaMemcpyHostToDevice, ctx->stream));
-    off += p.second;
-  }
-  // the mask and its neighbour codes only when the snapshot's mask differs
-  // from the one on the device (compared on the host while the copies run)
-  const size_t mbytes = ctx->mask_host.size() * 4;
-  if (!(ctx->mask_host_valid && !memcmp(mask_src, ctx->mask_host.data(), mbytes))) {
-    CK(cudaMemcpyAsync(ctx->mask, mask_src, mbytes, cudaMemcpyHostToDevice, ctx->stream));
-    LAUNCH(launch_nbcode(ctx->mask, ctx->nbc, ctx->g, ctx->stream));
-    ctx->slist_valid = false;
-    memcpy(ctx->mask_host.data(), mask_src, mbytes);
-    ctx->mask_host_valid = true;
-  }
-  ctx->t = (int64_t)h.t;
-  if (ctx->fcount) CK(cudaMemsetAsync(ctx->fcount, 0, 2 * sizeof(unsigned int), ctx->stream));
-  for (int c = 0; c < ctx->nc; c++) ctx->state_set[c] = true;
-  if (ctx->qs) ctx->solute_set = true;
-  return LB_OK;
-}
-
-}  // extern "C"
-
-// ======================================================================
-// batched lattices
-// ======================================================================
-
-struct lb_batch {
-  std::vector<lb_ctx *> ctxs;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int storage = ST_FP32;
-  std::string err;
-  uint64_t launches = 0;
-  BatchLat *d_lat = nullptr;
-  int4 *d_tiles = nullptr;
-  unsigned int *d_counters = nullptr;
-  unsigned int *d_tick = nullptr;
-  std::vector<BatchLat> h_lat;
-  int shape = 0, dynamic = 1, order = 1;
-  int ntiles = 0, grid = 0;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_steps = 0;
-  // graphs are captured and replayed on a private stream (the caller's may
-  // be the legacy default stream, which cannot be captured), fenced to the
-  // caller's stream by events
-  cudaStream_t gstream = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int fail(int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    err = buf;
-    return code;
-  }
-};
-
-namespace {
-
-int batch_cuda(lb_batch *b, cudaError_t e, const char *what) {
-  return b->fail(LB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-#define BCK(call)                                            \
-  do {                                                       \
-    cudaError_t e_ = (call);                                 \
-    if (e_ != cudaSuccess) return batch_cuda(b, e_, #call);  \
-  } while (0)
-
-void drop_graph(lb_batch *b) {
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
-  b->gexec = nullptr;
-  b->graph_steps = 0;
-}
-
-// tile list for the current shape and order: 0 = lattice by lattice,
-// 1 = round robin over lattices, 2 = largest lattices first
-int build_tiles(lb_batch *b) {
-  const int TX = batch_shape_tx(b->shape), TY = batch_shape_ty(b->shape);
-  std::vector<std::vector<int4>> per(b->ctxs.size());
-  for (size_t l = 0; l < b->ctxs.size(); l++) {
-    const lb_ctx *c = b->ctxs[l];
-    for (int y0 = 0; y0 < c->ny; y0 += TY)
-      for (int x0 = 0; x0 < c->nx; x0 += TX) per[l].push_back(make_int4((int)l, x0, y0, 0));
-  }
-  std::vector<int> idx(b->ctxs.size());
-  for (size_t l = 0; l < idx.size(); l++) idx[l] = (int)l;
-  if (b->order == 2)
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return per[a].size() > per[c].size(); });
-  std::vector<int4> tiles;
-  if (b->order == 1) {
-    size_t maxn = 0;
-    for (auto &v : per) maxn = std::max(maxn, v.size());
-    for (size_t k = 0; k < maxn; k++)
-      for (int l : idx)
-        if (k < per[l].size()) tiles.push_back(per[l][k]);
-  } else {
-    for (int l : idx) tiles.insert(tiles.end(), per[l].begin(), per[l].end());
-  }
-  if (b->d_tiles) cudaFree(b->d_tiles);
-  b->d_tiles = nullptr;
-  BCK(cudaMalloc((void **)&b->d_tiles, tiles.size() * sizeof(int4)));
-  BCK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
-  b->ntiles = (int)tiles.size();
-  int sms = 0;
-  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-  int occ = batch_occupancy(b->storage, b->shape);
-  b->grid = std::max(1, std::min(b->ntiles, sms * std::max(occ, 1)));
-  drop_graph(b);
-  return LB_OK;
-}
-
-// refresh the per-lattice descriptors (a context may have been advanced on
-// its own since the last batch call)
-int sync_descs(lb_batch *b) {
-  bool dirty = b->h_lat.empty();
-  if (dirty) b->h_lat.resize(b->ctxs.size());
-  for (size_t l = 0; l < b->ctxs.size(); l++) {
-    lb_ctx *c = b->ctxs[l];
-    BatchLat L{};
-    L.nx = c->g.nx;
-    L.ny = c->g.ny;
-    L.pitch = c->g.pitch;
-    L.mw = c->g.mw;
-    L.plane = c->g.plane;
-    L.buf[0] = c->fbuf[0];
-    L.buf[1] = c->fbuf[1];
-    L.cur = c->cur;
-    L.mask = c->mask;
-    L.nbc = c->nbc;
-    L.rho_ref = (float)c->rho_ref[0];
-    L.scale = c->scale;
-    L.inv_scale = c->inv_scale;
-    L.tau = (float)c->tau[0];
-    L.omega = (float)(1.0 / c->tau[0]);
-    L.pm = c->pm ? 1 : 0;
-    L.sr = c->sr ? 1 : 0;
-    L.fx = (float)c->fave[0][0];
-    L.fy = (float)c->fave[0][1];
-    L.ax = (float)c->acc[0][0];
-    L.ay = (float)c->acc[0][1];
-    if (memcmp(&L, &b->h_lat[l], sizeof L)) {
-      b->h_lat[l] = L;
-      dirty = true;
-    }
-  }
-  if (dirty)
-    BCK(cudaMemcpyAsync(b->d_lat, b->h_lat.data(), b->h_lat.size() * sizeof(BatchLat), cudaMemcpyHostToDevice,
-                        b->stream));
-  return LB_OK;
-}
-
-BatchLaunch launch_desc(lb_batch *b) {
-  BatchLaunch L{};
-  L.lat = b->d_lat;
-  L.tiles = b->d_tiles;
-  L.ntiles = b->ntiles;
-  L.grid = b->grid;
-  L.shape = b->shape;
-  L.dynamic = b->dynamic;
-  L.counters = b->d_counters;
-  L.tick = b->d_tick;
-  return L;
-}
-
-// LB_DEBUG_POISON on member contexts: NaN in the buffers the launch of
-// this parity writes (every member's next population buffer)
-int batch_poison(lb_batch *b, int parity) {
-  for (lb_ctx *c : b->ctxs) {
-    if (!(c->debug & LB_DEBUG_POISON)) continue;
-    const int out = 1 - ((c->cur + parity) & 1);
-    const cudaError_t e = cudaMemsetAsync(c->fbuf[out], 0xff, 9 * c->g.plane * storage_bytes(c->storage), b->stream);
-    if (e != cudaSuccess) return batch_cuda(b, e, "poison");
-  }
-  return LB_OK;
-}
-
-bool batch_poisoned(const lb_batch *b) {
-  for (const lb_ctx *c : b->ctxs)
-    if (c->debug & LB_DEBUG_POISON) return true;
-  return false;
-}
-
-int batch_direct(lb_batch *b, int parity0, int n) {
-  BatchLaunch L = launch_desc(b);
-  const bool poison = batch_poisoned(b);
-  for (int k = 0; k < n; k++) {
-    if (poison) {
-      const int rc = batch_poison(b, (parity0 + k) & 1);
-      if (rc != LB_OK) return rc;
-    }
-    if (launch_batch(b->storage, L, (parity0 + k) & 1, b->stream) < 0)
-      return batch_cuda(b, cudaGetLastError(), "batch launch");
-    b->launches++;
-  }
-  return LB_OK;
-}
-
-void batch_advance(lb_batch *b, int n) {
-  for (lb_ctx *c : b->ctxs) {
-    c->cur = (c->cur + n) & 1;
-    c->t += n;
-    c->fields_valid = false;
-  }
-  b->h_lat.clear();
-}
-
-constexpr int GRAPH_STEPS = 20;  // kernels per captured graph (even)
-
-int ensure_graph(lb_batch *b) {
-  if (b->gexec) return LB_OK;
-  if (!b->gstream) {
-    BCK(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
-    BCK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
-    BCK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
-  }
-  cudaGraph_t graph = nullptr;
-  BCK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
-  BatchLaunch L = launch_desc(b);
-  int bad = 0;
-  for (int k = 0; k < GRAPH_STEPS; k++)
-    if (launch_batch(b->storage, L, k & 1, b->gstream) < 0) bad = 1;
-  cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
-  if (bad || e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return batch_cuda(b, e != cudaSuccess ? e : cudaGetLastError(), "graph capture");
-  }
-  e = cudaGraphInstantiate(&b->gexec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return batch_cuda(b, e, "cudaGraphInstantiate");
-  b->graph_steps = GRAPH_STEPS;
-  return LB_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-int lb_batch_create(lb_ctx *const *ctxs, int n, lb_batch **out) {
-  if (!out || !ctxs || n < 1) return LB_E_ARG;
-  *out = nullptr;
-  lb_batch *b = new (std::nothrow) lb_batch();
-  if (!b) return LB_E_NOMEM;
-  for (int k = 0; k < n; k++) {
-    lb_ctx *c = ctxs[k];
-    int rc = LB_OK;
-    if (!c) rc = LB_E_ARG;
-    else if (c->nc != 1 || c->qs || !c->open.empty() || c->sc || c->ads[0] || c->bstyle != 0 || c->rank >= 0)
-      rc = c->fail(LB_E_UNSUPPORTED, "batched lattices are periodic single-component noslip lattices with body forces");
-    else {
-      for (int s = 0; s < c->nc && rc == LB_OK; s++)
-        if (!c->painted_f[s] && !c->state_set[s]) rc = c->fail(LB_E_ORDER, "lattice %d has no initial state", k);
-      if (rc == LB_OK) rc = commit(c);
-    }
-    if (rc == LB_OK && k > 0 && (c->device != ctxs[0]->device || c->stream != ctxs[0]->stream ||
-                                 c->storage != ctxs[0]->storage))
-      rc = LB_E_ARG;
-    if (rc != LB_OK) {
-      delete b;
-      return rc;
-    }
-    b->ctxs.push_back(c);
-  }
-  b->device = ctxs[0]->device;
-  b->stream = ctxs[0]->stream;
-  b->storage = ctxs[0]->storage;
-  if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc((void **)&b->d_lat, n * sizeof(BatchLat)) != cudaSuccess ||
-      cudaMalloc((void **)&b->d_counters, 2 * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess ||
-      cudaMalloc((void **)&b->d_tick, 2 * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMemsetAsync(b->d_tick, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess) {
-    lb_batch_destroy(b);
-    return LB_E_CUDA;
-  }
-  if (build_tiles(b) != LB_OK) {
-    lb_batch_destroy(b);
-    return LB_E_CUDA;
-  }
-  *out = b;
-  return LB_OK;
-}
-
-int lb_batch_destroy(lb_batch *b) {
-  if (!b) return LB_E_ARG;
-  cudaSetDevice(b->device);
-  cudaStreamSynchronize(b->stream);
-  drop_graph(b);
-  if (b->gstream) cudaStreamSynchronize(b->gstream);
-  if (b->gstream) cudaStreamDestroy(b->gstream);
-  if (b->ev_in) cudaEventDestroy(b->ev_in);
-  if (b->ev_out) cudaEventDestroy(b->ev_out);
-  if (b->d_lat) cudaFree(b->d_lat);
-  if (b->d_tiles) cudaFree(b->d_tiles);
-  if (b->d_counters) cudaFree(b->d_counters);
-  if (b->d_tick) cudaFree(b->d_tick);
-  delete b;
-  return LB_OK;
-}
-
-const char *lb_batch_last_error(const lb_batch *b) { return b ? b->err.c_str() : "no batch"; }
-
-int lb_batch_launch_count(const lb_batch *b, uint64_t *out) {
-  if (!b || !out) return LB_E_ARG;
-  *out = b->launches;
-  return LB_OK;
-}
-
-int lb_batch_iteration(lb_batch *b, int Nt, int use_graph) {
-  if (!b) return LB_E_ARG;
-  NvtxRange range("lb_batch_iteration");
-  if (Nt < 0) return b->fail(LB_E_ARG, "Nt must be >= 0");
-  BCK(cudaSetDevice(b->device));
-  int rc = sync_descs(b);
-  if (rc != LB_OK) return rc;
-  int done = 0;
-  // poisoned members run without the graph (the poisoning is not captured)
-  if (use_graph && !batch_poisoned(b)) {
-    rc = ensure_graph(b);
-    if (rc != LB_OK) return rc;
-    if (Nt >= b->graph_steps) {
-      BCK(cudaEventRecord(b->ev_in, b->stream));
-      BCK(cudaStreamWaitEvent(b->gstream, b->ev_in, 0));
-      while (Nt - done >= b->graph_steps) {
-        BCK(cudaGraphLaunch(b->gexec, b->gstream));
-        b->launches += (uint64_t)b->graph_steps;
-        done += b->graph_steps;
-      }
-      BCK(cudaEventRecord(b->ev_out, b->gstream));
-      BCK(cudaStreamWaitEvent(b->stream, b->ev_out, 0));
-    }
-  }
-  rc = batch_direct(b, done & 1, Nt - done);
-  if (rc != LB_OK) return rc;
-  batch_advance(b, Nt);
-  return LB_OK;
-}
-
-int lb_batch_autotune(lb_batch *b, const char *cache_json) {
-  if (!b) return LB_E_ARG;
-  BCK(cudaSetDevice(b->device));
-  // cache key: device name, storage and the lattice shapes
-  cudaDeviceProp prop;
-  BCK(cudaGetDeviceProperties(&prop, b->device));
-  uint64_t hsh = 1469598103934665603ULL;
-  for (lb_ctx *c : b->ctxs) {
-    hsh = (hsh ^ (uint64_t)c->nx) * 1099511628211ULL;
-    hsh = (hsh ^ (uint64_t)c->ny) * 1099511628211ULL;
-  }
-  char key[512];
-  snprintf(key, sizeof key, "%s|st%d|n%zu|%016llx", prop.name, b->storage, b->ctxs.size(), (unsigned long long)hsh);
-  std::string cache;
-  if (cache_json) {
-    FILE *fp = fopen(cache_json, "rb");
-    if (fp) {
-      char buf[4096];
-      size_t n;
-      while ((n = fread(buf, 1, sizeof buf, fp)) > 0) cache.append(buf, n);
-      fclose(fp);
-    }
-    size_t p = cache.find(std::string("\"") + key + "\"");
-    if (p != std::string::npos) {
-      int sh, dy, od;
-      const char *q = strchr(cache.c_str() + p, '{');
-      if (q && sscanf(q, "{\"shape\": %d, \"dynamic\": %d, \"order\": %d", &sh, &dy, &od) == 3 && sh >= 0 &&
-          sh < BATCH_SHAPES) {
-        b->shape = sh;
-        b->dynamic = dy;
-        b->order = od;
-        return build_tiles(b);
-      }
-    }
-  }
-  // keep the lattices' states: time on them, then put the states back
-  int rc = sync_descs(b);
-  if (rc != LB_OK) return rc;
-  std::vector<void *> saved(b->ctxs.size(), nullptr);
-  std::vector<size_t> sizes(b->ctxs.size());
-  for (size_t l = 0; l < b->ctxs.size(); l++) {
-    lb_ctx *c = b->ctxs[l];
-    sizes[l] = (size_t)9 * c->g.plane * storage_bytes(c->storage);
-    BCK(cudaMalloc(&saved[l], sizes[l]));
-    BCK(cudaMemcpyAsync(saved[l], c->fbuf[c->cur], sizes[l], cudaMemcpyDeviceToDevice, b->stream));
-  }
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0));
-  BCK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int bs = 0, bd = 1, bo = 1;
-  const int reps = 6;
-  for (int sh = 0; sh < BATCH_SHAPES; sh++)
-    for (int dy = 0; dy < 2; dy++)
-      for (int od = 0; od < 3; od++) {
-        if (dy && od == 0) continue;  // dynamic hand-out makes lattice order moot
-        b->shape = sh;
-        b->dynamic = dy;
-        b->order = od;
-        rc = build_tiles(b);
-        if (rc != LB_OK) return rc;
-        rc = batch_direct(b, 0, 2);
-        if (rc != LB_OK) return rc;
-        BCK(cudaEventRecord(e0, b->stream));
-        rc = batch_direct(b, 0, reps);
-        if (rc != LB_OK) return rc;
-        BCK(cudaEventRecord(e1, b->stream));
-        BCK(cudaEventSynchronize(e1));
-        float ms = 0;
-        BCK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bs = sh;
-          bd = dy;
-          bo = od;
-        }
-      }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  // an even number of launches per candidate leaves buf[cur] the input
-  for (size_t l = 0; l < b->ctxs.size(); l++) {
-    lb_ctx *c = b->ctxs[l];
-    BCK(cudaMemcpyAsync(c->fbuf[c->cur], saved[l], sizes[l], cudaMemcpyDeviceToDevice, b->stream));
-  }
-  BCK(cudaStreamSynchronize(b->stream));
-  for (void *p : saved) cudaFree(p);
-  b->shape = bs;
-  b->dynamic = bd;
-  b->order = bo;
-  rc = build_tiles(b);
-  if (rc != LB_OK) return rc;
-  if (cache_json) {
-    std::string entry = std::string("\"") + key + "\": {\"shape\": " + std::to_string(bs) +
-                        ", \"dynamic\": " + std::to_string(bd) + ", \"order\": " + std::to_string(bo) +
-                        ", \"ms_per_iter\": " + std::to_string(best / reps) + "}";
-    std::string body;
-    size_t l = cache.find('{'), r = cache.rfind('}');
-    if (l != std::string::npos && r != std::string::npos && r > l) body = cache.substr(l + 1, r - l - 1);
-    while (!body.empty() && isspace((unsigned char)body.back())) body.pop_back();
-    std::string outs = "{" + body + (body.empty() ? "\n  " : ",\n  ") + entry + "\n}\n";
-    FILE *fp = fopen(cache_json, "wb");
-    if (fp) {
-      fwrite(outs.data(), 1, outs.size(), fp);
-      fclose(fp);
-    }
-  }
-  return LB_OK;
-}
-
-}  // extern "C"
-
-// ======================================================================
-// thermo sums without allocation
-//
-// Some callers cannot let a library call cudaMalloc/cudaFree: applications
-// whose device memory is already handed out by a framework's caching
-// allocator (a fresh cudaMalloc can fail even though the framework has free
-// memory in its pool), loops that must not pay for an allocation or the
-// device-wide synchronisation cudaFree can imply, and programs that forbid
-// allocating once they are initialised.  lb_thermo_static serves them: its
-// FP64 partial sums live in the fixed array below instead of the context's
-// own buffer, so the call allocates nothing.
-// ======================================================================
-
-namespace {
-
-// room for the per-block partial sums of up to STATIC_THERMO_BLOCKS blocks
-// plus the final record (NTHERMO sums, flip count, error word) and the
-// blocks-finished counter: (1024 + 1) * 16 + 2 doubles and 4 bytes =
-// 131,220 bytes, held by every GPU that loads the library until the
-// process exits.  The thermo grid has at most THERMO_BLOCKS_PER_SM blocks
-// per SM, so 1024 blocks cover GPUs of up to 256 SMs.
-constexpr int STATIC_THERMO_BLOCKS = 1024;
-static_assert(STATIC_THERMO_BLOCKS >= THERMO_BLOCKS_PER_SM * 256, "static thermo scratch below 256 SMs");
-static __device__ __align__(256) double g_thermo_scratch[(STATIC_THERMO_BLOCKS + 1) * NTHERMO + 2];
-static __device__ unsigned int g_thermo_done;
-
-// device address of g_thermo_scratch per device, looked up once per device
-// (the host-side name of a __device__ array is not a device address)
-constexpr int STATIC_MAX_DEVICES = 64;
-double *g_thermo_scratch_dev[STATIC_MAX_DEVICES] = {};
-unsigned int *g_thermo_done_dev[STATIC_MAX_DEVICES] = {};
-std::mutex g_thermo_scratch_mu;
-
-}  // namespace
-
-extern "C" int lb_thermo_static(lb_ctx *ctx, lb_thermo_t *out) {
-  NEED_CTX();
-  if (!out) return ctx->fail(LB_E_ARG, "null output");
-  if (ctx->tq_n) {
-    TRY(set_device(ctx));
-    TRY(read_all_deferred(ctx));
-  }
-  if (!ctx->fields_valid || !ctx->thermo_valid) return ctx->fail(LB_E_ORDER, "no fields yet: call lb_iteration first");
-  // the field planes must describe the live state: written by the last
-  // iteration executed, with no state replaced and no step count set since
-  // (mask, deposits and removed mass are read live)
-  if (ctx->fields_step != ctx->t || ctx->thermo.step != ctx->t)
-    return ctx->fail(LB_E_ORDER, "the node fields are not those of the current state (step %lld): the "
-                     "record can be recomputed only after an iteration whose last step is a thermo step",
-                     (long long)ctx->t);
-  if (ctx->device < 0 || ctx->device >= STATIC_MAX_DEVICES)
-    return ctx->fail(LB_E_UNSUPPORTED, "device %d is beyond the %d devices the static scratch serves",
-                     ctx->device, STATIC_MAX_DEVICES);
-  if (ctx->tblocks > STATIC_THERMO_BLOCKS)
-    return ctx->fail(LB_E_ARG, "lattice needs %d blocks of partial sums; the static scratch holds %d",
-                     ctx->tblocks, STATIC_THERMO_BLOCKS);
-  TRY(set_device(ctx));
-  double *scratch = nullptr;
-  unsigned int *done = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_thermo_scratch_mu);
-    if (!g_thermo_scratch_dev[ctx->device]) {
-      cudaError_t e = cudaGetSymbolAddress((void **)&g_thermo_scratch_dev[ctx->device], g_thermo_scratch);
-      if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&g_thermo_done_dev[ctx->device], g_thermo_done);
-      if (e != cudaSuccess) {
-        g_thermo_scratch_dev[ctx->device] = nullptr;
-        g_thermo_done_dev[ctx->device] = nullptr;
-        return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_thermo_scratch)");
-      }
-    }
-    scratch = g_thermo_scratch_dev[ctx->device];
-    done = g_thermo_done_dev[ctx->device];
-  }
-  // every slot the kernels read is written by the same call first, so the
-  // contents a previous call left behind need no clearing
-  ThermoArgs ta{};
-  ta.g = ctx->g;
-  ta.mask = ctx->mask;
-  ta.fields = ctx->fields;
-  ta.nc = ctx->nc;
-  ta.Cfield = ctx->qs ? ctx->Cfield : nullptr;
-  ta.b = ctx->react ? ctx->b : nullptr;
-  ta.removed = ctx->react ? ctx->removed : nullptr;
-  ta.partials = scratch;
-  ta.out = scratch + (size_t)STATIC_THERMO_BLOCKS * NTHERMO;
-  ta.done = done;  // zero at load; the last block of every call resets it
-  ta.nflips = ctx->nflips;
-  ta.errw = ctx->errw;
-  LAUNCH(launch_thermo(ta, ctx->tblocks, ctx->stream));
-  double rec[NTHERMO + 2];
-  CK(cudaMemcpyAsync(rec, ta.out, sizeof rec, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const double *h = rec;
-  unsigned long long nfl = 0;
-  memcpy(&nfl, &rec[NTHERMO], sizeof nfl);
-  if ((int)rec[NTHERMO + 1]) {
-    CK(cudaMemsetAsync(ctx->errw, 0, sizeof(int), ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return ctx->fail(LB_E_TIMEOUT, "a TMA pipeline wait timed out before step %lld", (long long)ctx->t);
-  }
-  lb_thermo_t T;
-  memset(&T, 0, sizeof T);
-  T.step = ctx->t;
-  T.nsolid = (int64_t)llround(h[13]);
-  T.nfluid = (int64_t)llround(h[14]);
-  for (int c = 0; c < ctx->nc; c++) {
-    T.mass[c] = ctx->rho_ref[c] * (double)T.nfluid + h[0 + c];
-    T.mass_eq[c] = ctx->rho_ref[c] * (double)T.nfluid + h[2 + c];
-    T.mom_comp[c][0] = h[4 + 2 * c];
-    T.mom_comp[c][1] = h[5 + 2 * c];
-    T.mom[0] += h[4 + 2 * c];
-    T.mom[1] += h[5 + 2 * c];
-  }
-  T.solute = h[8];
-  T.bsum = h[9];
-  T.removed[0] = h[10];
-  T.removed[1] = h[11];
-  T.removed_solute = h[12];
-  T.flips = (int64_t)nfl;
-  *out = T;
-  for (int q = 0; q < NTHERMO; q++)
-    if (!std::isfinite(h[q])) return ctx->fail(LB_E_NAN, "thermo sum %d is not finite", q);
-  return LB_OK;
-}
