@@ -346,7 +346,10 @@ int lb_aveacceleration_xy(lb_ctx *ctx, double ax, double ay, int fluid);
 /* interforce command: one component F = -G psi(x) sum_i w_i psi(x+e_i) e_i
  * with psi = psi0 exp(-rho0/rho); two components F_s = -G rho_s(x)
  * sum_i w_i rho_sbar(x+e_i) e_i (psi0, rho0 ignored).  psi = 0 on solid
- * nodes.  Not combined with inlet/outlet openings (LB_E_UNSUPPORTED). */
+ * nodes.  With inlet/outlet openings the densities are those after the
+ * opening rules of the same iteration, and the sums wrap periodically
+ * across every wall, as the domain's boundaries do; not built for slabs
+ * (LB_E_UNSUPPORTED at the first iteration). */
 int lb_interforce(lb_ctx *ctx, double G, double psi0, double rho0);
 
 /* adhesiveforce command: F = -G psi(x) sum_i w_i s(x+e_i) e_i, s = 1 on

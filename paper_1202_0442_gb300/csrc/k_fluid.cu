@@ -13,8 +13,10 @@
 //   taken from registers: one pass for single-component runs with a solute
 //   and no intersolute.
 // k_fluid_sc: the same plus interforce, which needs the densities of the
-//   eight neighbours after this step's streaming.  Each CTA pulls the
-//   populations of its tile and of a one-node ring around it, stages
+//   eight neighbours after this step's streaming and opening rules (the sums
+//   wrap periodically across every wall, openings or not).  Each CTA pulls
+//   the populations of its tile and of a one-node ring around it, applies
+//   the opening rules of the nodes that have one, stages
 //   rho - rho_ref in shared memory, and reads the neighbours from there; the
 //   ring's extra loads hit L1/L2, the HBM traffic stays nine loads and nine
 //   stores per node.
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(32 * LOC_BY, 4 * 8 / LOC_BY) k_fluid_solute(co
 // barrier waits on fewer warps; the ring costs 33 % more pulls, from L1/L2)
 constexpr int SC_TX = 32, SC_TY = 8;
 
-template <class S, int NC, bool SLIP>
+template <class S, int NC, bool SLIP, bool OPEN>
 __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p) {
   // rho - rho_ref of every component for the tile and a one-node ring; slot
   // (ty + 1, tx + 1) holds node (x0 + tx, y0 + ty) wrapped periodically.
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
       pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, x, y, bits, p.inv_scale, h[c]);
       if (SLIP && (bits & DIAG_BITS))
         slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, x, y, bits, p.inv_scale, h[c]);
+      if (OPEN) apply_opening_c(p, c, x, y, h[c]);
 #pragma unroll
       for (int i = 0; i < 9; i++) d += h[c][i];
     }
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(SC_TX *SC_TY, 4) k_fluid_sc(const FluidArgs p)
         pull9<S>((const S *)p.fin + (size_t)c * 9 * g.plane, g, hx, hy, hb, p.inv_scale, hh);
         if (SLIP && (hb & DIAG_BITS))
           slip_fix<S>(p, c, (const S *)p.fin + (size_t)c * 9 * g.plane, hx, hy, hb, p.inv_scale, hh);
+        if (OPEN) apply_opening_c(p, c, hx, hy, hh);
 #pragma unroll
         for (int i = 0; i < 9; i++) d += hh[i];
       }
@@ -367,12 +371,15 @@ template <class S>
 int launch_fluid_t(int nc, bool sc, bool me, const FluidArgs &a, cudaStream_t s) {
   if (sc) {
     dim3 blk(SC_TX, SC_TY), grd((a.g.nx + SC_TX - 1) / SC_TX, (a.g.chi - a.g.clo + SC_TY - 1) / SC_TY);
+    // openings take their own instantiations: their rules would cost the
+    // kernel without openings registers (spills in the two-component one)
+    const bool op = a.nopen > 0;
     if (a.slip) {
-      if (nc == 1) launch_pdl(k_fluid_sc<S, 1, true>, grd, blk, 0, s, a);
-      else launch_pdl(k_fluid_sc<S, 2, true>, grd, blk, 0, s, a);
+      if (nc == 1) launch_pdl(op ? k_fluid_sc<S, 1, true, true> : k_fluid_sc<S, 1, true, false>, grd, blk, 0, s, a);
+      else launch_pdl(op ? k_fluid_sc<S, 2, true, true> : k_fluid_sc<S, 2, true, false>, grd, blk, 0, s, a);
     } else {
-      if (nc == 1) launch_pdl(k_fluid_sc<S, 1, false>, grd, blk, 0, s, a);
-      else launch_pdl(k_fluid_sc<S, 2, false>, grd, blk, 0, s, a);
+      if (nc == 1) launch_pdl(op ? k_fluid_sc<S, 1, false, true> : k_fluid_sc<S, 1, false, false>, grd, blk, 0, s, a);
+      else launch_pdl(op ? k_fluid_sc<S, 2, false, true> : k_fluid_sc<S, 2, false, false>, grd, blk, 0, s, a);
     }
   } else {
     if (nc == 1) {

@@ -261,8 +261,8 @@ int dalloc_state(lb_ctx *ctx, T **p, size_t n, int k) {
 
 int validate(lb_ctx *ctx) {
   const int nx = ctx->nx, ny = ctx->ny;
-  if (ctx->sc && !ctx->open.empty())
-    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built");
+  if (ctx->sc && !ctx->open.empty() && ctx->rank >= 0)
+    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built for slabs");
   for (const Opening &o : ctx->open) {
     for (int c = 0; c < ctx->nc; c++) {
       // without a momentum style the fluid stays periodic across the
@@ -1481,8 +1481,8 @@ int lb_interforce(lb_ctx *ctx, double G, double psi0, double rho0) {
   ctx->G = G;
   ctx->psi0 = psi0;
   ctx->sc_rho0 = rho0;
-  if (ctx->committed && ctx->sc && !ctx->open.empty())
-    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built");
+  if (ctx->committed && ctx->sc && !ctx->open.empty() && ctx->rank >= 0)
+    return ctx->fail(LB_E_UNSUPPORTED, "interforce with inlet/outlet openings is not built for slabs");
   return LB_OK;
 }
 

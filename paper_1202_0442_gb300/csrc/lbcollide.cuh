@@ -240,6 +240,22 @@ __device__ __forceinline__ void collide_store(const FluidArgs &p, int x, int y, 
   }
 }
 
+// component c's opening rule at node (x, y) if an opening holds it (the
+// rule of a component reads only that component's populations, so the
+// interforce kernel applies it per component, to its own node and to the
+// ring nodes whose densities it stages); h in unscaled units
+__device__ __forceinline__ void apply_opening_c(const FluidArgs &p, int c, int x, int y, float (&h)[9]) {
+  const Geometry &g = p.g;
+  const int gy = grow(g, y);
+  if (!(x == 0 || gy == 0 || x == g.nx - 1 || gy == g.gny - 1)) return;
+#pragma unroll 1
+  for (int k = 0; k < p.nopen; k++) {
+    if (!opening_has(p.span[k], x, gy, g.nx, g.gny)) continue;
+    apply_opening(p.span[k], p.rule[k], c, h, x, gy, p.rho_ref[c]);
+    return;
+  }
+}
+
 template <int NC>
 __device__ __forceinline__ void apply_openings(const FluidArgs &p, int x, int y,
                                                float (&h)[NC][9], float sc = 1.0f) {

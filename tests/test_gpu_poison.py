@@ -16,7 +16,7 @@ also allocate every library buffer between zones of NaN patterns
 zones must be intact at the end (no write out of bounds).  Every fluid kernel
 variant is reached: the streaming kernel (FP32, FP16, BF16; noslip, slip
 map, mixed; openings of every style incl. gradient), two components
-(mass-exact), Shan-Chen with one and two components, the fused fluid-solute
+(mass-exact), Shan-Chen with one and two components (and with openings), the fused fluid-solute
 kernel with reaction and growth (D2Q9, D2Q4), the separate solute kernel
 under a two-component fluid, intersolute, the TMA kernel, slabs with
 their halo exchange and the batched launch."""
@@ -102,6 +102,17 @@ def _intersolute():
                           aveforce=((1e-5, 0.0),), solute_q=4, taus=0.8, C=C, intersolute=(-0.05, 1.0, 0.3))
 
 
+def _sc_openings():
+    nx, ny = 48, 30
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = solid[-1, :] = 1
+    ops = [synth.Opening("xlo", 1, ny - 2, "inlet", [("uniform", 0.02, 0.7), ("dirichlet", 0.0, 0.41)]),
+           synth.Opening("xhi", 1, ny - 2, "outlet", [("dirichlet", 0.0, 0.7), ("uniform", 0.01, 0.4)])]
+    return synth.Workload(name="sco", nx=nx, ny=ny, solid=solid,
+                          rho=[np.where(solid, 0, 0.7), np.where(solid, 0, 0.4)], tau=(0.8, 1.1),
+                          alpha=(4 / 9, 4 / 9), rho_ref=(0.7, 0.4), openings=ops, interforce=(0.3, 0.0, 0.0))
+
+
 def _reactive(q):
     return synth.reactive(128, 64, seed=3, ndiscs=4, rmin=4, rmax=8, q=q, kr=0.02, bmax=0.3, growth_seed=7)
 
@@ -119,6 +130,7 @@ CASES = {
     "shan_chen_one": (_sc_one, "fp32", {}, None, 30),
     "shan_chen_two_fp32": (lambda: synth.shan_chen2(128), "fp32", {}, None, 30),
     "shan_chen_two_fp16": (lambda: synth.shan_chen2(128), "fp16", {"h_max": 1.2, "rounding": "stochastic"}, None, 30),
+    "shan_chen_two_openings": (_sc_openings, "fp32", {}, None, 30),
     "reactive_q9_fused": (lambda: _reactive(9), "fp32", {}, None, 150),
     "reactive_q4_fused": (lambda: _reactive(4), "fp32", {}, None, 150),
     "reactive_q9_separate": (lambda: _reactive(9), "fp32", {}, "streaming", 150),
