@@ -508,6 +508,31 @@ def test_poiseuille_opening_profile():
     assert np.isclose(v.max(), vmax * (1 - 1 / L ** 2) if L % 2 == 0 else vmax, rtol=1e-12)
 
 
+@pytest.mark.parametrize("nc", [1, 2])
+def test_interforce_beside_openings_keeps_a_uniform_rest_state(nc):
+    """Interforce beside inlet/outlet openings (the sums wrap periodically
+    across the open walls, as the domain's boundaries do): a uniform fluid
+    at rest, periodic in y, between dirichlet openings that hold its own
+    density feels no force at any node and stays at rest.  Sums that took
+    the neighbours beyond an open wall as psi = 0 would push the opening
+    columns and set the fluid moving."""
+    nx, ny = 24, 12
+    if nc == 1:
+        rho, G, ref, mom = [np.full((ny, nx), 200.0)], (-120.0, 4.0, 200.0), (200.0,), [("dirichlet", 0.0, 200.0)]
+    else:
+        rho = [np.full((ny, nx), 0.7), np.full((ny, nx), 0.4)]
+        G, ref, mom = (0.9, 0.0, 0.0), (0.7, 0.4), [("dirichlet", 0.0, 0.7), ("dirichlet", 0.0, 0.4)]
+    w = synth.Workload(name="screst", nx=nx, ny=ny, solid=np.zeros((ny, nx), np.uint8), rho=rho,
+                       tau=(0.9,) * nc, alpha=(4 / 9,) * nc, interforce=G, rho_ref=ref,
+                       openings=[synth.Opening("xlo", 0, ny - 1, "inlet", mom),
+                                 synth.Opening("xhi", 0, ny - 1, "outlet", mom)])
+    o = oracle_from_workload(w)
+    f0 = [o.f(c).copy() for c in range(nc)]
+    o.step(40)
+    for c in range(nc):
+        assert np.allclose(o.f(c), f0[c], rtol=1e-13, atol=0), np.max(np.abs(o.f(c) - f0[c]))
+
+
 def test_pressure_driven_channel():
     """dirichlet inlet/outlet on a walled channel: at steady state the mass
     flux is the same through every column, the profile is parabolic and the
