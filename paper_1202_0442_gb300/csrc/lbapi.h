@@ -1,6 +1,7 @@
-// lbapi.h -- functions of the library's host side that its files share
-// (lb2d_api.cu defines them; the slab, snapshot, batch and allocation-free
-// thermo files use them).
+// lbapi.h -- what the files of the library's host side share: the host
+// direction tables and five functions (lb2d_api.cu defines four of them,
+// lb2d_slab.cu exchange_slabs, which lb_iteration calls for a lattice held
+// as one slab).
 #pragma once
 
 #include <cstddef>
